@@ -492,3 +492,49 @@ def test_growth_draws_within_a_block_are_independent(oracle):
     exp = m * prob * prob
     z = (both - exp) / np.sqrt(m * prob * prob * (1 - prob * prob))
     assert abs(z) < 5, (both, exp, single, m)
+
+
+# --------------------------------------------------------------------------
+# R1 counter layout, evaluated with the independent engine
+# --------------------------------------------------------------------------
+def test_seeding_counter_layout(oracle, torch_philox):
+    p = dict(nx=13, ny=7, nz=5, cd=0.2, target_solid_fraction=0.5, seed=0x1234567890ABCDEF)
+    t_seed = oracle.targets(p)[1]
+    n = 13 * 7 * 5
+    k0, k1 = p["seed"] & 0xFFFFFFFF, p["seed"] >> 32
+    rows = [((g & 0xFFFFFFFF), g >> 32, 0xFFFFFFFF, 0x100, k0, k1) for g in range((n + 3) // 4)]
+    blocks = torch_philox(rows)
+    want = [v for v in range(n) if blocks[v >> 2][v & 3] < t_seed]
+    assert list(oracle.seed_candidates(p)) == want
+
+
+def test_growth_counter_layout(oracle, torch_philox):
+    # One step from isolated seeds: the claimed set is exactly the targets
+    # whose draw (word d&3 of block (a, 0, t, 0x200 | d>>2)) is below the
+    # class threshold.
+    dirs, cls = oracle.directions()
+    checked = 0
+    for seed in range(40):
+        p = dict(nx=16, ny=15, nz=14, cd=0.003, g_face=0.03, g_edge=0.02, g_corner=0.01,
+                 spacing_s=7, target_solid_fraction=0.9, seed=seed * 0x9E3779B97F4A7C15 % 2**64)
+        seeds = _seeds_phase(oracle, p)
+        if not seeds.any():
+            continue
+        nt, _, t_ref = oracle.targets(p)
+        c0 = int(seeds.sum())
+        thr = [oracle.threshold(t_ref[k], nt, c0) for k in range(3)]
+        k0, k1 = p["seed"] & 0xFFFFFFFF, p["seed"] >> 32
+        want = seeds.copy()
+        for a in np.flatnonzero(seeds.ravel()):
+            z, y, x = a // (16 * 15), (a // 16) % 15, a % 16
+            blocks = torch_philox([(int(a), 0, 0, 0x200 | b, k0, k1) for b in range(7)])
+            for d in range(26):
+                xx, yy, zz = x + dirs[d][0], y + dirs[d][1], z + dirs[d][2]
+                if not (0 <= xx < 16 and 0 <= yy < 15 and 0 <= zz < 14):
+                    continue
+                if blocks[d >> 2][d & 3] < thr[cls[d]]:
+                    want[zz, yy, xx] = True
+        r = oracle.run(dict(p, max_steps=1))
+        assert np.array_equal(r.phase.astype(bool), want)
+        checked += 1
+    assert checked > 20
