@@ -1,0 +1,279 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 LIETS QSGS generator.
+
+One step = one full realization of the 400^3 workload (cd = 1e-4, spacing
+s = 30, face/edge/corner G_ref = 0.01/0.0025/0.000625, solid fraction 0.80):
+seeding, spacing, front construction, growth to the exact target.  The
+metric is nodes/s = voxels generated per second of device time, summed over
+ranks (each rank generates its own realizations: weak scaling, no
+collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+on a bounded sample of the same workload (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_11734_gb300 import workloads  # noqa: E402
+
+METRIC = "nodes/s"
+WORKLOAD = "single_400"
+L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2: written between timed steps
+CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
+REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
+BYTES_PER_FRONT_VOXEL = 40       # k_grow: 4 B front entry + 9 row words of 4 B
+BYTES_PER_CLAIM = 8              # k_grow: atomicOr into grid and claim grid
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help=">= 1")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def cpu_baseline(edge: int):
+    from oracle import oracle as O
+    p = dict(workloads.single_400(), nx=edge, ny=edge, nz=edge)
+    O.lib()
+    t0 = time.perf_counter()
+    O.run(p)
+    dt = time.perf_counter() - t0
+    return {"value": edge**3 / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"one full realization of the 400^3 parameters on a {edge}^3 box "
+                      f"({dt:.1f} s, single-threaded C oracle)"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    p = dict(workloads.single_400(), nx=REF_SAMPLE_EDGE, ny=REF_SAMPLE_EDGE, nz=REF_SAMPLE_EDGE)
+    O.lib()
+    for _ in range(a.warmup):
+        O.run(p)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        O.run(p)
+        times.append(time.perf_counter() - t0)
+    n = REF_SAMPLE_EDGE**3
+    value = n * len(times) / sum(times)
+    sample = (f"one full realization of the 400^3 parameters on a {REF_SAMPLE_EDGE}^3 box "
+              "per step (single-threaded C oracle)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_edge": REF_SAMPLE_EDGE},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+def main():
+    a = parse()
+    a.e2e_steps = max(1, a.e2e_steps)
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    from paper_2602_11734_gb300 import build, qsgs as Q
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    Q.load_library()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    p = dict(workloads.single_400(), seed=1 + rank)
+    n_vox = p["nx"] * p["ny"] * p["nz"]
+    g = Q.Generator(p, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = g.stream
+
+    for _ in range(max(3, a.warmup)):
+        g.seed()
+        st = g.grow()
+    assert st.status == Q.QSGS_OK, st
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    sampler = ClockSampler(gpu_id)
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    launches0 = g.query().launches
+    launches_timed = 0
+    for k in range(a.steps):
+        with torch.cuda.stream(s):
+            flush.fill_(k)  # evict L2 between timed steps (not timed)
+        torch.cuda.synchronize()
+        l0 = g.query().launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.seed()
+        st = g.grow()
+        e1.record(s)
+        e1.synchronize()
+        launches_timed += g.query().launches - l0
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    del launches0
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n_vox * a.steps * world / (total_ms / 1000.0)
+
+    # Kernel-level pass with the library's event profiler (not timed above).
+    g.set_profiling(True)
+    g.seed()
+    st_prof = g.grow()
+    prof = g.profile()
+    g.set_profiling(False)
+    grow_launches, grow_ms = prof["grow"]
+    claims = st_prof.solid_count - st_prof.n_seeds
+    alg_bytes = BYTES_PER_FRONT_VOXEL * st_prof.sum_front + BYTES_PER_CLAIM * claims
+    pk, pk_kind = peaks()
+    achieved = alg_bytes / (grow_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_grow",
+                "peak_kind": pk_kind, "launches": grow_launches,
+                "mean_launch_ms": grow_ms / max(1, grow_launches),
+                "phases_ms": {k: round(v[1], 4) for k, v in prof.items()}}
+
+    # End to end through the C ABI with host buffers: create, seed, grow and
+    # copy the uint8 phase map to pinned host memory, every step.
+    host = torch.empty(n_vox, dtype=torch.uint8, pin_memory=True)
+    ws = torch.empty(g.nbytes, dtype=torch.uint8, device=dev)
+    e2e_times = []
+    for k in range(a.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = Q.qsgs_create(p, ws.data_ptr(), ws.numel(), s.cuda_stream)
+        Q.qsgs_seed(h)
+        rc, _ = Q.qsgs_grow_until(h, 0)
+        Q.qsgs_fetch(h, host.data_ptr(), n_vox, Q.QSGS_FMT_U8, False)
+        Q.qsgs_destroy(h)
+        t1 = time.perf_counter()
+        if k:
+            e2e_times.append(t1 - t0)
+    e2e = {"value": n_vox * world / statistics.mean(e2e_times), "unit": METRIC,
+           "h2d_bytes_per_step": ctypes.sizeof(Q.QsgsParams), "d2h_bytes_per_step": n_vox}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(CPU_SAMPLE_EDGE)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": 400, "ny": 400, "nz": 400, "cd": p["cd"],
+                       "spacing_s": p["spacing_s"], "g_face": p["g_face"], "g_edge": p["g_edge"],
+                       "g_corner": p["g_corner"], "solid_fraction": p["target_solid_fraction"],
+                       "growth_steps": st.steps, "seeds": st.n_seeds,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_timed, "clocks": clocks,
+        }), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * qsgs.h -- C ABI of the GB300 LIETS QSGS porous-media generator.
+ *
+ * The library generates one solid phase on a 3-D voxel grid by the
+ * list-indexed explicit time-stepping (LIETS) form of the Quartet Structure
+ * Generation Set of arXiv 2602.11734 (Wang & Al Kobaisi):
+ *   - Bernoulli seeding with probability c_d                (Sec. 2.1 step 2)
+ *   - seed spacing s by diamond (L1-ball) exclusion          (Sec. 2.3, Fig. 1 D)
+ *   - the active front: solids with a void 26-neighbour      (Sec. 2.3 step 2)
+ *   - front-only directional growth, 6 face / 12 edge /
+ *     8 corner directions                                   (Sec. 2.3 step 3, Algorithm 3)
+ *   - the volume-fraction law of the growth probabilities    (Eq. 1)
+ *   - the front update prune(A U New)                        (Sec. 2.3 step 4)
+ * with an exact final solid count (the last step keeps the lowest-index
+ * claims only).  All arithmetic is integer: draws are 32-bit Philox4x32-10
+ * words keyed by the realization seed, and probabilities p enter as
+ * thresholds floor(p 2^32).  Results are bit-identical for any launch order.
+ *
+ * Conventions
+ *   - Voxel v = x + nx (y + ny z), x fastest; N = nx ny nz must be < 2^32.
+ *   - Pointers marked "device" are CUDA device pointers of the current
+ *     device; "host" pointers are ordinary host memory.
+ *   - Ownership: the caller allocates and frees the device workspace, every
+ *     output buffer and the CUDA stream.  A handle owns only host-side
+ *     metadata; creating or destroying one allocates or frees no device
+ *     memory.  Work is enqueued on the caller's stream.
+ *   - Errors: every function returns an int.  0 (QSGS_OK) is success;
+ *     positive values are run statuses; negative values are errors.  No C++
+ *     exception crosses this interface.  qsgs_strerror() names every code.
+ *   - Thread safety: a handle must not be used from two host threads at
+ *     once; distinct handles are independent.
+ */
+#ifndef QSGS_H
+#define QSGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (>= 0) ---------------------------------------------- */
+#define QSGS_OK 0          /* done: the solid count equals the target       */
+#define QSGS_STALLED 1     /* no growth attempt can succeed any more         */
+#define QSGS_MAX_STEPS 2   /* the total step limit (params.max_steps) hit    */
+#define QSGS_RUNNING 3     /* this call's step budget is used up; call again */
+
+/* ---- error codes (< 0) ------------------------------------------------ */
+#define QSGS_ERR_INVALID -1   /* bad parameter or argument                   */
+#define QSGS_ERR_WORKSPACE -2 /* workspace missing, misaligned or too small  */
+#define QSGS_ERR_CUDA -3      /* a CUDA runtime call failed                  */
+#define QSGS_ERR_TIMEOUT -4   /* a bounded device-side wait gave up          */
+#define QSGS_ERR_STATE -5     /* call out of order (e.g. grow before seed)   */
+#define QSGS_ERR_NOMEM -6     /* host allocation failed                      */
+
+/* ---- fetch formats ---------------------------------------------------- */
+#define QSGS_FMT_U8 0     /* uint8[N], 1 = solid, 0 = void, x fastest        */
+#define QSGS_FMT_PACKED 1 /* uint32[nz*ny*W], W = ceil(nx/32): bit (x & 31)
+                             of word (y + ny z) W + (x >> 5); bits at
+                             x >= nx are 0                                   */
+
+/* Generation parameters (the problem statement of Sec. 2.1 and Sec. 3.2).
+ *   nx, ny, nz   grid dimensions, each >= 1, product < 2^32
+ *   cd           seed (core) probability c_d in [0, 1]
+ *   g_face       reference growth probability G_ref of the 6 face directions
+ *   g_edge       ... of the 12 edge directions
+ *   g_corner     ... of the 8 corner directions            (each in [0, 1])
+ *   spacing_s    minimum L1 distance between seeds (0 or 1: no spacing)
+ *   target_solid_fraction  phi_s in [0, 1], used when target_count == 0:
+ *                Nt = floor(phi_s N + 0.5)
+ *   target_count Nt directly (<= N); 0 = derive from the fraction
+ *   seed         64-bit key of the realization's random numbers
+ *   max_steps    total growth-step limit; 0 = none (2^32 - 1)          */
+typedef struct qsgs_params {
+  uint32_t nx, ny, nz;
+  double cd;
+  double g_face, g_edge, g_corner;
+  uint32_t spacing_s;
+  double target_solid_fraction;
+  uint64_t target_count;
+  uint64_t seed;
+  uint32_t max_steps;
+} qsgs_params;
+
+/* Run statistics.
+ *   solid_count  current solid voxels c
+ *   target_count Nt
+ *   front_size   |A|, the current active front
+ *   n_candidates Bernoulli candidates drawn by qsgs_seed
+ *   n_seeds      seeds placed (after spacing and the cap at Nt)
+ *   sum_front    sum over executed steps of |A_t| (growth work done)
+ *   steps        growth steps executed
+ *   status       QSGS_RUNNING while more steps can run, else the final
+ *                status (QSGS_OK / QSGS_STALLED / QSGS_MAX_STEPS)           */
+typedef struct qsgs_stats {
+  uint64_t solid_count;
+  uint64_t target_count;
+  uint64_t front_size;
+  uint64_t n_candidates;
+  uint64_t n_seeds;
+  uint64_t sum_front;
+  uint32_t steps;
+  int32_t status;
+  uint64_t launches; /* kernels this handle has launched since creation  */
+} qsgs_stats;
+
+/* One kernel class of the optional event profiler (qsgs_profile).
+ *   name      "seed", "grow", "step_ctl", "trim", "front" or "fetch"
+ *   launches  kernels of that class timed so far
+ *   total_ms  their summed CUDA-event durations on the handle's stream  */
+typedef struct qsgs_profile_entry {
+  char name[16];
+  uint64_t launches;
+  double total_ms;
+} qsgs_profile_entry;
+
+typedef struct qsgs_handle qsgs_handle;
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int qsgs_version(void);
+
+/* Text of a status or error code; never NULL. */
+const char* qsgs_strerror(int code);
+
+/* Validates params and returns 0 with *nt, *t_seed, t_ref[0..2] set to the
+ * integer forms of Nt, floor(cd 2^32) and floor(G 2^32) (face, edge,
+ * corner), or QSGS_ERR_INVALID.  Host only; touches no device. */
+int qsgs_check_params(const qsgs_params* params, uint64_t* nt, uint64_t* t_seed,
+                      uint64_t t_ref[3]);
+
+/* Device workspace bytes needed for params (0 if params are invalid).  The
+ * workspace holds the run state, two bit grids of nz*ny*ceil(nx/32) words,
+ * the front list (N words) and, when spacing_s >= 2, the spacing scratch.
+ * Host only. */
+size_t qsgs_workspace_bytes(const qsgs_params* params);
+
+/* Binds a realization to a caller-allocated device workspace.
+ *   params          host, copied
+ *   dev_workspace   device, >= qsgs_workspace_bytes(params) bytes, 256-byte
+ *                   aligned; owned by the caller and must outlive the handle
+ *   bytes           its size
+ *   cuda_stream     a cudaStream_t (NULL = the legacy default stream); all
+ *                   work of this handle is enqueued on it
+ *   out             host; receives the handle
+ * Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_NOMEM or
+ * QSGS_ERR_CUDA.  Enqueues the workspace initialisation (no host wait). */
+int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                qsgs_handle** out);
+
+/* Seeding, spacing, the seed cap and the initial front (Sec. 2.1 step 2,
+ * Sec. 2.3 steps 1-2).  Asynchronous on the handle's stream.  May be
+ * called again to restart the realization from scratch.
+ * Returns QSGS_OK or QSGS_ERR_CUDA. */
+int qsgs_seed(qsgs_handle* h);
+
+/* Runs growth steps (Sec. 2.3 steps 3-5 with Eq. 1) until the target is
+ * reached, growth stalls, params.max_steps is hit, or max_steps further
+ * steps have run in this call (0 = no per-call limit).  Blocks until the
+ * stream has finished them and fills *out (may be NULL).
+ * Returns the status (QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING)
+ * or QSGS_ERR_STATE (not seeded), QSGS_ERR_CUDA, QSGS_ERR_TIMEOUT. */
+int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out);
+
+/* Copies the phase map out.
+ *   dst            host or device buffer (dst_is_device says which)
+ *   bytes          its size: >= N for QSGS_FMT_U8, >= 4 nz ny W for
+ *                  QSGS_FMT_PACKED
+ *   fmt            QSGS_FMT_U8 or QSGS_FMT_PACKED
+ * Blocks until the copy is complete.  Returns QSGS_OK, QSGS_ERR_INVALID
+ * (fmt or size), QSGS_ERR_STATE or QSGS_ERR_CUDA.  A U8 fetch to the host
+ * stages through the front-list area of the workspace, so it is only
+ * allowed when the realization has finished (status != QSGS_RUNNING). */
+int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_device);
+
+/* Synchronises the handle's stream and fills *out.  Returns QSGS_OK,
+ * QSGS_ERR_CUDA or QSGS_ERR_TIMEOUT (a device wait gave up). */
+int qsgs_query(qsgs_handle* h, qsgs_stats* out);
+
+/* Turns the event profiler on (enable != 0) or off and clears its totals.
+ * While on, every kernel launch of the handle is bracketed by CUDA events
+ * on its stream; totals are collected at each host synchronisation.  Adds
+ * a small per-launch cost, so timed runs leave it off.  Returns QSGS_OK,
+ * QSGS_ERR_INVALID or QSGS_ERR_CUDA (event creation failed). */
+int qsgs_set_profiling(qsgs_handle* h, int enable);
+
+/* Copies up to max_entries profiler totals into out (host) and returns the
+ * number of kernel classes (>= 0), or QSGS_ERR_INVALID. */
+int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries);
+
+/* Releases the handle (host memory only).  NULL is ignored. */
+void qsgs_destroy(qsgs_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSGS_H */

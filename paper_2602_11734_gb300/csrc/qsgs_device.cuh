@@ -1,0 +1,203 @@
+// qsgs_device.cuh -- device primitives of the QSGS generator (sm_103a).
+//
+// Grid geometry with division by invariant integers, the Philox4x32-10
+// counter-based generator, the 26-direction table of the growth step and
+// the device-resident run state.  Written for this library; it shares
+// nothing with the CPU oracle.
+#pragma once
+
+#include <cstdint>
+
+namespace qsgs {
+
+// ---------------------------------------------------------------------------
+// Unsigned division by an invariant 32-bit divisor with one multiply-high
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Sec. 4, the round-up method):
+//   l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+//   t = umulhi(m, n), q = (t + ((n - t) >> min(l,1))) >> max(l-1, 0).
+// Exact for every 32-bit n and every 1 <= d < 2^32.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{};
+  f.d = d;
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 0 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ inline uint32_t fast_div(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  uint32_t t = __umulhi(n, f.m);
+#else
+  uint32_t t = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// ---------------------------------------------------------------------------
+// Grid geometry.  Voxel v = x + nx (y + ny z); row r = y + ny z.  The
+// occupancy grid is bit-packed, x fastest: row r holds W = ceil(nx/32)
+// 32-bit words, bit (x & 31) of word r*W + (x >> 5).  Bits at x >= nx in
+// the last word of a row are kept zero.
+// ---------------------------------------------------------------------------
+struct Geom {
+  uint32_t nx, ny, nz;
+  uint32_t W;        // words per row
+  uint32_t nrows;    // ny * nz
+  uint32_t nwords;   // W * nrows
+  uint32_t n;        // nx * ny * nz (< 2^32)
+  uint32_t pad_mask; // bits of the last word of a row that lie at x >= nx
+  FastDiv div_nx, div_ny, div_W;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds, each two 32x32->64 products
+// (multipliers 0xD2511F53, 0xCD9E8D57) and a key bumped by the Weyl
+// constants (0x9E3779B9, 0xBB67AE85).
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t u4_word(const U4& r, int j) {
+  return j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
+}
+
+// Stream tags of the counter's fourth word: seeding draws and growth draws
+// never share a counter.
+constexpr uint32_t kSeedTag = 0x100u;
+constexpr uint32_t kGrowTag = 0x200u;
+
+// ---------------------------------------------------------------------------
+// Directions.  d = 0..5 faces, 6..17 edges, 18..25 corners; within a class
+// ordered by (dz, dy, dx) lexicographically.  The growth draw of direction
+// d is word (d & 3) of the Philox block with counter word 3 = 0x200|(d>>2).
+// A neighbourhood position packs the offset as (dz+1)*9 + (dy+1)*3 + (dx+1).
+// ---------------------------------------------------------------------------
+struct Dir {
+  int dx, dy, dz, cls;
+};
+
+// The table itself is only read in constant expressions; device code uses
+// the packed scalar forms below (2 bits per direction and field).
+constexpr Dir kDirs[26] = {
+    // faces
+    {0, 0, -1, 0}, {0, -1, 0, 0}, {-1, 0, 0, 0}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0},
+    // edges
+    {0, -1, -1, 1}, {-1, 0, -1, 1}, {1, 0, -1, 1}, {0, 1, -1, 1},
+    {-1, -1, 0, 1}, {1, -1, 0, 1}, {-1, 1, 0, 1}, {1, 1, 0, 1},
+    {0, -1, 1, 1}, {-1, 0, 1, 1}, {1, 0, 1, 1}, {0, 1, 1, 1},
+    // corners
+    {-1, -1, -1, 2}, {1, -1, -1, 2}, {-1, 1, -1, 2}, {1, 1, -1, 2},
+    {-1, -1, 1, 2}, {1, -1, 1, 2}, {-1, 1, 1, 2}, {1, 1, 1, 2},
+};
+
+constexpr uint64_t pack_dir_field(int field) {
+  uint64_t m = 0;
+  for (int d = 0; d < 26; ++d) {
+    int v = field == 0 ? kDirs[d].dx + 1
+          : field == 1 ? kDirs[d].dy + 1
+          : field == 2 ? kDirs[d].dz + 1
+                       : kDirs[d].cls;
+    m |= (uint64_t)v << (2 * d);
+  }
+  return m;
+}
+
+constexpr uint64_t kDxPacked = pack_dir_field(0);
+constexpr uint64_t kDyPacked = pack_dir_field(1);
+constexpr uint64_t kDzPacked = pack_dir_field(2);
+constexpr uint64_t kClsPacked = pack_dir_field(3);
+
+__host__ __device__ __forceinline__ int dir_dx(int d) { return (int)((kDxPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ __forceinline__ int dir_dy(int d) { return (int)((kDyPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ __forceinline__ int dir_dz(int d) { return (int)((kDzPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ __forceinline__ int dir_cls(int d) { return (int)((kClsPacked >> (2 * d)) & 3); }
+
+__host__ __device__ __forceinline__ int nb_pos(int dx, int dy, int dz) {
+  return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+}
+
+__host__ __device__ __forceinline__ int dir_pos(int d) {
+  return nb_pos(dir_dx(d), dir_dy(d), dir_dz(d));
+}
+
+// Neighbourhood positions of the directions drawn from Philox block b.
+__host__ __device__ __forceinline__ uint32_t block_pos_mask(int b) {
+  uint32_t m = 0;
+  for (int j = 0; j < 4; ++j) {
+    int d = 4 * b + j;
+    if (d < 26) m |= 1u << dir_pos(d);
+  }
+  return m;
+}
+
+// Neighbourhood positions of the directions of class cls.
+__host__ __device__ __forceinline__ uint32_t class_pos_mask(int cls) {
+  uint32_t m = 0;
+  for (int d = 0; d < 26; ++d)
+    if (dir_cls(d) == cls) m |= 1u << dir_pos(d);
+  return m;
+}
+
+constexpr uint32_t kNbAll = (1u << 27) - 1u;
+constexpr uint32_t kNbCentre = 1u << 13;
+
+// ---------------------------------------------------------------------------
+// Device-resident run state (one per realization, 256 bytes, in the
+// caller's workspace).  Kernels of a step read it; the one-thread step
+// kernels write it, so the host never has to synchronise between steps.
+// ---------------------------------------------------------------------------
+enum : int32_t { kRunning = -1 };
+enum : uint32_t { kErrTimeout = 1u, kErrOverflow = 2u };
+
+struct alignas(256) RunState {
+  unsigned long long solid;      // c_t (solid voxels)
+  unsigned long long nt;         // target count
+  unsigned long long thr[3];     // Eq. 1 thresholds for this step
+  unsigned long long t_ref[3];   // floor(G_ref 2^32) per class
+  unsigned long long t_seed;     // floor(cd 2^32)
+  unsigned long long claimed;    // |New_t| of this step (before the trim)
+  unsigned long long live;       // attempts with a positive threshold
+  unsigned long long sum_front;  // sum over steps of |A_t| (statistics)
+  unsigned long long trim_keep;  // voxels of New_t kept by the final trim
+  uint32_t front_n;              // |A_t|
+  uint32_t cand_n;               // Bernoulli candidates
+  uint32_t acc_n;                // seeds placed
+  uint32_t t;                    // steps executed
+  uint32_t max_steps;            // total step limit (0xFFFFFFFF = none)
+  uint32_t step_limit;           // pause point of the current call
+  int32_t status;                // kRunning or a QSGS_* status
+  uint32_t active;               // this step runs
+  uint32_t trim;                 // this step needs the exact-target trim
+  uint32_t error;                // kErr* bits
+  uint32_t undecided;            // spacing: candidates not yet decided
+  uint32_t scan_epoch;           // look-back scan launch counter
+  uint32_t scan_tile;            // look-back scan tile dispenser
+  uint32_t scan_done;            // look-back scan blocks finished
+};
+
+}  // namespace qsgs

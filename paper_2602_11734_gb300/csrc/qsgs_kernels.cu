@@ -1,0 +1,672 @@
+// qsgs_kernels.cu -- CUDA kernels of the LIETS QSGS generator (sm_103a).
+//
+// One realization lives in a caller-owned workspace: a run state, the
+// bit-packed occupancy grid, an auxiliary bit grid (seed candidates, then the
+// voxels claimed in the current step), the sorted active-front list and the
+// scratch of the seed-spacing pass.  Every step of the hot loop is a fixed
+// sequence of launches that read their sizes from the run state, so a step
+// can be replayed from a CUDA graph without the host.
+#include <cuda_runtime.h>
+
+#include "qsgs_device.cuh"
+#include "qsgs_launch.h"
+#include "qsgs_scan.cuh"
+
+namespace qsgs {
+
+// ---------------------------------------------------------------------------
+// Eq. 1 in integers: T(c) = min(2^32, floor(T_ref (20 Nt - 19 c) / Nt)).
+// With num = 20 Nt - 19 c = a Nt + b (0 <= b < Nt), the quotient is
+// T_ref a + floor(T_ref b / Nt), and T_ref b < 2^64 because T_ref <= 2^32
+// and b < Nt < 2^32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long eq1_threshold(unsigned long long t_ref,
+                                                            unsigned long long nt,
+                                                            unsigned long long c) {
+  const unsigned long long two32 = 1ull << 32;
+  if (nt == 0) return t_ref < two32 ? t_ref : two32;
+  if (19ull * c >= 20ull * nt) return 0;
+  const unsigned long long num = 20ull * nt - 19ull * c;
+  const unsigned long long a = num / nt, b = num % nt;
+  const unsigned long long q = t_ref * a + (t_ref * b) / nt;
+  return q > two32 ? two32 : q;
+}
+
+// ---------------------------------------------------------------------------
+// Run-state kernels (one thread).
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(RunState* st, StateInit init) {
+  st->solid = 0;
+  st->nt = init.nt;
+  for (int k = 0; k < 3; ++k) {
+    st->t_ref[k] = init.t_ref[k];
+    st->thr[k] = 0;
+  }
+  st->t_seed = init.t_seed;
+  st->claimed = 0;
+  st->live = 0;
+  st->sum_front = 0;
+  st->trim_keep = 0;
+  st->front_n = 0;
+  st->cand_n = 0;
+  st->acc_n = 0;
+  st->t = 0;
+  st->max_steps = init.max_steps;
+  st->step_limit = 0xFFFFFFFFu;
+  st->status = kRunning;
+  st->active = 1;
+  st->trim = 0;
+  st->error = 0;
+  st->undecided = 0;
+}
+
+// Exits before a step, in order: target reached, step limit, pause point of
+// the current call.  Idempotent, so it can close a chain of captured steps.
+__global__ void k_step_begin(RunState* st) {
+  st->active = 0;
+  if (st->status != kRunning) return;
+  if (st->solid >= st->nt) { st->status = kStatusDone; return; }
+  if (st->t >= st->max_steps) { st->status = kStatusMaxSteps; return; }
+  if (st->t >= st->step_limit) return;
+  for (int k = 0; k < 3; ++k) st->thr[k] = eq1_threshold(st->t_ref[k], st->nt, st->solid);
+  st->claimed = 0;
+  st->live = 0;
+  st->trim = 0;
+  st->active = 1;
+}
+
+// After the growth kernel: a step without a single attempt of positive
+// probability is a fixed point (stalled, not counted); otherwise count the
+// claims, arm the exact-target trim if they overshoot, advance t.
+__global__ void k_step_end(RunState* st) {
+  if (!st->active) return;
+  if (st->live == 0) {
+    st->status = kStatusStalled;
+    st->active = 0;
+    return;
+  }
+  st->sum_front += st->front_n;
+  const unsigned long long c = st->solid, k = st->claimed;
+  if (c + k > st->nt) {
+    st->trim = 1;
+    st->trim_keep = st->nt - c;
+    st->solid = st->nt;
+  } else {
+    st->solid = c + k;
+  }
+  st->t += 1;
+}
+
+__global__ void k_set_step_limit(RunState* st, uint32_t extra) {
+  if (extra == 0) {
+    st->step_limit = 0xFFFFFFFFu;
+  } else {
+    unsigned long long lim = (unsigned long long)st->t + extra;
+    st->step_limit = lim > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)lim;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return *p; }
+
+// Solid-or-outside mask of word xw of row (y+dy, z+dz), with the row's
+// padding bits and out-of-domain rows reading as solid.
+__device__ __forceinline__ uint32_t row_word(const Geom& g, const uint32_t* grid, uint32_t r_nb,
+                                             uint32_t xw) {
+  uint32_t w = ld_word(grid + (size_t)r_nb * g.W + xw);
+  if (xw == g.W - 1) w |= g.pad_mask;
+  return w;
+}
+
+// Front word of word index w: solid voxels with at least one void in-domain
+// 26-neighbour, evaluated bit-parallel over the 32 voxels of the word.
+__device__ __forceinline__ uint32_t front_word(const Geom& g, const uint32_t* grid, uint32_t w) {
+  const uint32_t r = fast_div(w, g.div_W);
+  const uint32_t xw = w - r * g.W;
+  const uint32_t z = fast_div(r, g.div_ny);
+  const uint32_t y = r - z * g.ny;
+  const uint32_t self = ld_word(grid + w);
+  if (self == 0) return 0;
+  uint32_t all_solid = 0xFFFFFFFFu;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = (int)y + dy, zz = (int)z + dz;
+      if (yy < 0 || yy >= (int)g.ny || zz < 0 || zz >= (int)g.nz) continue;  // outside: solid
+      const uint32_t rn = (uint32_t)(yy + (int)g.ny * zz);
+      const uint32_t c = row_word(g, grid, rn, xw);
+      const uint32_t l = xw > 0 ? ld_word(grid + (size_t)rn * g.W + xw - 1) : 0xFFFFFFFFu;
+      const uint32_t rr = xw + 1 < g.W ? row_word(g, grid, rn, xw + 1) : 0xFFFFFFFFu;
+      const uint32_t minus = (c << 1) | (l >> 31);  // bit i: solid at x - 1
+      const uint32_t plus = (c >> 1) | (rr << 31);  // bit i: solid at x + 1
+      all_solid &= minus & plus;
+      if (dy != 0 || dz != 0) all_solid &= c;
+    }
+  }
+  return self & ~all_solid;
+}
+
+// ---------------------------------------------------------------------------
+// Scan policies.
+// ---------------------------------------------------------------------------
+struct WordItem {
+  uint32_t w;     // word index
+  uint32_t bits;  // the word's set bits
+};
+
+// Emit the voxel index of every set bit of a word, ascending.
+__device__ __forceinline__ void emit_word_bits(const Geom& g, const WordItem& it, uint32_t* out,
+                                               unsigned long long off) {
+  const uint32_t r = fast_div(it.w, g.div_W);
+  const uint32_t xw = it.w - r * g.W;
+  const uint32_t v0 = r * g.nx + xw * 32u;
+  uint32_t b = it.bits;
+  while (b) {
+    const int i = __ffs(b) - 1;
+    b &= b - 1;
+    out[off++] = v0 + (uint32_t)i;
+  }
+}
+
+// Sec. 2.1 step 2: the Bernoulli candidates of one word, drawn from Philox
+// block (v >> 2) word (v & 3) with the seeding tag.
+struct SeedCompactPolicy {
+  Geom g;
+  RunState* st;
+  uint32_t* cand;
+  uint32_t k0, k1;
+  using Item = WordItem;
+  __device__ bool active() const { return true; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return g.nwords; }
+  __device__ Item load(uint32_t w) const {
+    const unsigned long long t_seed = st->t_seed;
+    uint32_t bits = 0;
+    if (t_seed != 0) {
+      const uint32_t r = fast_div(w, g.div_W);
+      const uint32_t xw = w - r * g.W;
+      const uint32_t x0 = xw * 32u;
+      const uint32_t len = min(32u, g.nx - x0);
+      const uint32_t v0 = r * g.nx + x0;
+      uint32_t gcur = v0 >> 2;
+      U4 blk = philox4x32_10(U4{gcur, 0u, 0xFFFFFFFFu, kSeedTag}, k0, k1);
+      for (uint32_t i = 0; i < len; ++i) {
+        const uint32_t v = v0 + i;
+        if ((v >> 2) != gcur) {
+          gcur = v >> 2;
+          blk = philox4x32_10(U4{gcur, 0u, 0xFFFFFFFFu, kSeedTag}, k0, k1);
+        }
+        if ((unsigned long long)u4_word(blk, (int)(v & 3)) < t_seed) bits |= 1u << i;
+      }
+    }
+    return Item{w, bits};
+  }
+  __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
+  __device__ void emit(const Item& it, unsigned long long off) const { emit_word_bits(g, it, cand, off); }
+  __device__ void total(unsigned long long n) const { st->cand_n = (uint32_t)n; }
+};
+
+// Sec. 2.3 step 2 / step 4: the active front rebuilt from the grid, in
+// ascending voxel order.  Also clears the claim grid for the next step.
+struct FrontPolicy {
+  Geom g;
+  RunState* st;
+  const uint32_t* grid;
+  uint32_t* aux;
+  uint32_t* front;
+  uint32_t always;  // 1: run even when no step is active (initial front)
+  using Item = WordItem;
+  __device__ bool active() const { return always || st->active; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return g.nwords; }
+  __device__ Item load(uint32_t w) const {
+    aux[w] = 0;
+    return Item{w, front_word(g, grid, w)};
+  }
+  __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
+  __device__ void emit(const Item& it, unsigned long long off) const { emit_word_bits(g, it, front, off); }
+  __device__ void total(unsigned long long n) const { st->front_n = (uint32_t)n; }
+};
+
+// Exact target: keep the trim_keep lowest-index voxels claimed in this step
+// (the claim grid, in ascending order), clear the others from the grid.
+struct TrimPolicy {
+  Geom g;
+  RunState* st;
+  uint32_t* grid;
+  const uint32_t* aux;
+  using Item = WordItem;
+  __device__ bool active() const { return st->active && st->trim; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return g.nwords; }
+  __device__ Item load(uint32_t w) const { return Item{w, aux[w]}; }
+  __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
+  __device__ void emit(const Item& it, unsigned long long off) const {
+    const unsigned long long keep = st->trim_keep;
+    uint32_t drop = it.bits;
+    if (off < keep) {
+      uint32_t k = (uint32_t)min((unsigned long long)__popc(it.bits), keep - off);
+      uint32_t b = it.bits;
+      while (k--) b &= b - 1;  // b = the bits beyond the first k
+      drop = b;
+    }
+    if (drop) grid[it.w] &= ~drop;
+  }
+  __device__ void total(unsigned long long) const {}
+};
+
+// Seeds: the accepted candidates in ascending order, capped at Nt, written
+// into the grid.
+struct AcceptPolicy {
+  Geom g;
+  RunState* st;
+  uint32_t* grid;
+  const uint32_t* cand;
+  const uint8_t* decision;  // nullptr: every candidate accepted
+  struct Item {
+    uint32_t v;
+    uint32_t ok;
+  };
+  __device__ bool active() const { return true; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return st->cand_n; }
+  __device__ Item load(uint32_t i) const {
+    return Item{cand[i], decision ? (uint32_t)(decision[i] == 1) : 1u};
+  }
+  __device__ uint32_t count(const Item& it) const { return it.ok; }
+  __device__ void emit(const Item& it, unsigned long long off) const {
+    if (off < st->nt) {
+      const uint32_t r = fast_div(it.v, g.div_nx);
+      const uint32_t x = it.v - r * g.nx;
+      atomicOr(grid + (size_t)r * g.W + (x >> 5), 1u << (x & 31));
+    }
+  }
+  __device__ void total(unsigned long long n) const {
+    const unsigned long long placed = n < st->nt ? n : st->nt;
+    st->acc_n = (uint32_t)placed;
+    st->solid = placed;
+  }
+};
+
+// Exclusive offsets of the spacing cells; the counts become fill cursors.
+struct CellOffsetPolicy {
+  RunState* st;
+  uint32_t ncells;
+  uint32_t* cell_count;  // in: per-cell counts; out: start offsets (cursors)
+  uint32_t* start;       // out: ncells + 1 offsets
+  struct Item {
+    uint32_t i, c;
+  };
+  __device__ bool active() const { return true; }
+  __device__ bool emit_empty() const { return true; }
+  __device__ uint32_t n_items() const { return ncells; }
+  __device__ Item load(uint32_t i) const { return Item{i, cell_count[i]}; }
+  __device__ uint32_t count(const Item& it) const { return it.c; }
+  __device__ void emit(const Item& it, unsigned long long off) const {
+    start[it.i] = (uint32_t)off;
+    cell_count[it.i] = (uint32_t)off;
+  }
+  __device__ void total(unsigned long long n) const { start[ncells] = (uint32_t)n; }
+};
+
+// ---------------------------------------------------------------------------
+// Seed spacing (Sec. 2.3, Fig. 1 D): greedy in ascending index -- keep a
+// candidate iff no kept candidate before it lies within L1 distance < s.
+// Candidates are binned into cubic cells of edge s, so every conflict lies
+// in the 27 surrounding cells.  The greedy choice is computed by rounds: a
+// candidate is kept once every earlier conflicting candidate is rejected,
+// and rejected once one of them is kept.  Each round settles at least the
+// lowest undecided candidate, so n + 1 rounds always suffice.
+// ---------------------------------------------------------------------------
+struct CellGeom {
+  uint32_t s, ncx, ncy, ncz;
+};
+
+__device__ __forceinline__ void decode_xyz(const Geom& g, uint32_t v, uint32_t& x, uint32_t& y,
+                                           uint32_t& z) {
+  const uint32_t r = fast_div(v, g.div_nx);
+  x = v - r * g.nx;
+  z = fast_div(r, g.div_ny);
+  y = r - z * g.ny;
+}
+
+__global__ void k_cell_count(Geom g, CellGeom cg, const RunState* st, const uint32_t* cand,
+                             uint32_t* count) {
+  const uint32_t n = st->cand_n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    decode_xyz(g, cand[i], x, y, z);
+    const uint32_t cell = x / cg.s + cg.ncx * (y / cg.s + cg.ncy * (z / cg.s));
+    atomicAdd(count + cell, 1u);
+  }
+}
+
+__global__ void k_cell_fill(Geom g, CellGeom cg, const RunState* st, const uint32_t* cand,
+                            uint32_t* cursor, uint32_t* items, uint8_t* decision) {
+  const uint32_t n = st->cand_n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    decode_xyz(g, cand[i], x, y, z);
+    const uint32_t cell = x / cg.s + cg.ncx * (y / cg.s + cg.ncy * (z / cg.s));
+    items[atomicAdd(cursor + cell, 1u)] = i;
+    decision[i] = 0;
+  }
+}
+
+// One block runs all rounds; a round re-examines every undecided candidate.
+__global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, RunState* st,
+                                                        const uint32_t* cand,
+                                                        const uint32_t* start,
+                                                        const uint32_t* items,
+                                                        uint8_t* decision) {
+  __shared__ uint32_t s_undecided;
+  const uint32_t n = st->cand_n;
+  const int s = (int)cg.s;
+  for (uint32_t round = 0; round <= n; ++round) {
+    if (threadIdx.x == 0) s_undecided = 0;
+    __syncthreads();
+    uint32_t mine = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      if (((volatile uint8_t*)decision)[i] != 0) continue;
+      uint32_t x, y, z;
+      decode_xyz(g, cand[i], x, y, z);
+      const int cx = (int)(x / cg.s), cy = (int)(y / cg.s), cz = (int)(z / cg.s);
+      bool pending = false, rejected = false;
+      for (int dz = -1; dz <= 1 && !rejected; ++dz) {
+        const int zz = cz + dz;
+        if (zz < 0 || zz >= (int)cg.ncz) continue;
+        for (int dy = -1; dy <= 1 && !rejected; ++dy) {
+          const int yy = cy + dy;
+          if (yy < 0 || yy >= (int)cg.ncy) continue;
+          for (int dx = -1; dx <= 1 && !rejected; ++dx) {
+            const int xx = cx + dx;
+            if (xx < 0 || xx >= (int)cg.ncx) continue;
+            const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
+            for (uint32_t k = start[cell]; k < start[cell + 1]; ++k) {
+              const uint32_t j = items[k];
+              if (j >= i) continue;  // only earlier candidates matter
+              uint32_t xj, yj, zj;
+              decode_xyz(g, cand[j], xj, yj, zj);
+              const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
+              if (l1 >= s) continue;
+              const uint8_t dj = ((volatile uint8_t*)decision)[j];
+              if (dj == 1) { rejected = true; break; }
+              if (dj == 0) pending = true;
+            }
+          }
+        }
+      }
+      if (rejected) decision[i] = 2;
+      else if (!pending) decision[i] = 1;
+      else ++mine;
+    }
+    if (mine) atomicAdd(&s_undecided, mine);
+    __syncthreads();
+    const uint32_t left = s_undecided;
+    __syncthreads();
+    if (left == 0) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The growth step (Sec. 2.3 step 3, Algorithm 3 lines 4-13): every front
+// voxel a tries each void in-domain neighbour q = a + e_d with the draw
+// word (d & 3) of Philox block (a, 0, t, 0x200 | d >> 2) against the class
+// threshold of Eq. 1.  A claim is an atomicOr into the grid; the thread that
+// flips the bit also records q in the claim grid.  Whether q becomes solid
+// depends only on the start-of-step grid and the draws, never on the order
+// of the threads: a thread that already sees q solid skips it, and q is
+// solid either way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t nb_row_bits(const Geom& g, const uint32_t* grid, uint32_t rn,
+                                                uint32_t xw, uint32_t bi) {
+  const uint32_t* row = grid + (size_t)rn * g.W;
+  uint32_t c = row[xw];
+  if (xw == g.W - 1) c |= g.pad_mask;
+  if (bi == 0) {
+    const uint32_t l = xw > 0 ? row[xw - 1] : 0xFFFFFFFFu;
+    return __funnelshift_r(l, c, 31) & 7u;
+  }
+  uint32_t rr = 0;
+  if (bi == 31) {
+    if (xw + 1 < g.W) {
+      rr = row[xw + 1];
+      if (xw + 1 == g.W - 1) rr |= g.pad_mask;
+    } else {
+      rr = 0xFFFFFFFFu;
+    }
+  }
+  return __funnelshift_r(c, rr, bi - 1) & 7u;
+}
+
+__global__ void __launch_bounds__(256) k_grow(Geom g, const uint32_t* __restrict__ front,
+                                              uint32_t* grid, uint32_t* aux, RunState* st,
+                                              uint32_t k0, uint32_t k1) {
+  if (!st->active) return;
+  const uint32_t n = st->front_n;
+  const uint32_t t = st->t;
+  const unsigned long long T0 = st->thr[0], T1 = st->thr[1], T2 = st->thr[2];
+  const uint32_t live_mask = (T0 ? class_pos_mask(0) : 0u) | (T1 ? class_pos_mask(1) : 0u) |
+                             (T2 ? class_pos_mask(2) : 0u);
+  uint32_t my_claimed = 0, my_live = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t v = front[i];
+    uint32_t x, y, z;
+    decode_xyz(g, v, x, y, z);
+    const uint32_t r = y + g.ny * z;
+    const uint32_t xw = x >> 5, bi = x & 31;
+    // 27-bit neighbourhood, bit set = solid or outside the domain.
+    uint32_t nb = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (int)y + dy, zz = (int)z + dz;
+        uint32_t bits3 = 7u;
+        if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz)
+          bits3 = nb_row_bits(g, grid, (uint32_t)((int)r + dy + (int)g.ny * dz), xw, bi);
+        nb |= bits3 << ((dz + 1) * 9 + (dy + 1) * 3);
+      }
+    }
+    const uint32_t cand = ~nb & kNbAll & ~kNbCentre & live_mask;
+    if (!cand) continue;
+    my_live += __popc(cand);
+#pragma unroll
+    for (int b = 0; b < 7; ++b) {
+      const uint32_t bm = cand & block_pos_mask(b);
+      if (!bm) continue;
+      const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | (uint32_t)b}, k0, k1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int d = 4 * b + j;
+        if (d >= 26) continue;
+        if (!((bm >> dir_pos(d)) & 1u)) continue;
+        const int cls = dir_cls(d);
+        const unsigned long long T = cls == 0 ? T0 : (cls == 1 ? T1 : T2);
+        if ((unsigned long long)u4_word(rnd, j) >= T) continue;
+        const uint32_t xx = (uint32_t)((int)x + dir_dx(d));
+        const uint32_t rq = (uint32_t)((int)r + dir_dy(d) + (int)g.ny * dir_dz(d));
+        const size_t wq = (size_t)rq * g.W + (xx >> 5);
+        const uint32_t bit = 1u << (xx & 31);
+        const uint32_t old = atomicOr(grid + wq, bit);
+        if (!(old & bit)) {
+          ++my_claimed;
+          atomicOr(aux + wq, bit);
+        }
+      }
+    }
+  }
+  // One atomic per warp for the step's counters.
+  const uint32_t wc = __reduce_add_sync(0xffffffffu, my_claimed);
+  const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
+  if ((threadIdx.x & 31) == 0) {
+    if (wc) atomicAdd(&st->claimed, (unsigned long long)wc);
+    if (wl) atomicAdd(&st->live, (unsigned long long)wl);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fetch: bit grid -> uint8 phase map (x fastest), 16 voxels per thread.
+// ---------------------------------------------------------------------------
+__global__ void k_unpack_u8(Geom g, const uint32_t* grid, uint8_t* out) {
+  const unsigned long long n = g.n;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x * 16ull;
+  for (unsigned long long v0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * 16ull;
+       v0 < n; v0 += stride) {
+    uint32_t r = fast_div((uint32_t)v0, g.div_nx);
+    uint32_t x = (uint32_t)v0 - r * g.nx;
+    uint8_t b[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      b[k] = 0;
+      if (v0 + k < n) b[k] = (uint8_t)((grid[(size_t)r * g.W + (x >> 5)] >> (x & 31)) & 1u);
+      if (++x == g.nx) { x = 0; ++r; }
+    }
+    if (v0 + 16 <= n && ((reinterpret_cast<uintptr_t>(out + v0) & 15u) == 0)) {
+      uint4 pk;
+      pk.x = b[0] | (b[1] << 8) | (b[2] << 16) | ((uint32_t)b[3] << 24);
+      pk.y = b[4] | (b[5] << 8) | (b[6] << 16) | ((uint32_t)b[7] << 24);
+      pk.z = b[8] | (b[9] << 8) | (b[10] << 16) | ((uint32_t)b[11] << 24);
+      pk.w = b[12] | (b[13] << 8) | (b[14] << 16) | ((uint32_t)b[15] << 24);
+      *reinterpret_cast<uint4*>(out + v0) = pk;
+    } else {
+      for (int k = 0; k < 16 && v0 + k < n; ++k) out[v0 + k] = b[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+static uint32_t scan_grid(uint64_t max_items) {
+  const uint64_t tiles = (max_items + kScanTile - 1) / kScanTile;
+  uint64_t blocks = (uint64_t)num_sms() * 4;
+  if (blocks > tiles) blocks = tiles;
+  return (uint32_t)(blocks ? blocks : 1);
+}
+
+Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz) {
+  Geom g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.W = (nx + 31) / 32;
+  g.nrows = ny * nz;
+  g.nwords = g.W * g.nrows;
+  g.n = nx * ny * nz;
+  const uint32_t tail = nx - (g.W - 1) * 32;  // voxels in the last word
+  g.pad_mask = tail == 32 ? 0u : ~((1u << tail) - 1u);
+  g.div_nx = make_fastdiv(nx);
+  g.div_ny = make_fastdiv(ny);
+  g.div_W = make_fastdiv(g.W);
+  return g;
+}
+
+// Every launch goes through LAUNCH so that the tracer counts (and, when
+// profiling, times) it.
+#define QSGS_LAUNCH(tr, cls, s, kernel, grid, block, ...)       \
+  do {                                                          \
+    cudaError_t e_ = (tr).before((cls), (s));                   \
+    if (e_ != cudaSuccess) return e_;                           \
+    kernel<<<(grid), (block), 0, (s)>>>(__VA_ARGS__);           \
+    e_ = cudaGetLastError();                                    \
+    if (e_ != cudaSuccess) return e_;                           \
+    e_ = (tr).after((s));                                       \
+    if (e_ != cudaSuccess) return e_;                           \
+  } while (0)
+
+cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr) {
+  QSGS_LAUNCH(tr, kClsSeed, s, k_init_state, 1, 1, st, init);
+  return cudaSuccess;
+}
+
+cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,
+                        uint32_t spin_limit, cudaStream_t s, Tracer& tr) {
+  ScanCtl ctl{b.st, b.scan_status, spin_limit};
+  // Candidates (ascending) into the list buffer.
+  SeedCompactPolicy sp{g, b.st, b.list, k0, k1};
+  QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<SeedCompactPolicy>, scan_grid(g.nwords),
+              kScanThreads, sp, ctl);
+  const uint8_t* decision = nullptr;
+  if (b.cg.s >= 2) {
+    const CellGeom cg{b.cg.s, b.cg.ncx, b.cg.ncy, b.cg.ncz};
+    const uint32_t ncells = cg.ncx * cg.ncy * cg.ncz;
+    cudaError_t e = cudaMemsetAsync(b.cell_count, 0, (size_t)ncells * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const uint32_t blocks = (uint32_t)num_sms() * 4;
+    QSGS_LAUNCH(tr, kClsSeed, s, k_cell_count, blocks, 256, g, cg, b.st, b.list, b.cell_count);
+    CellOffsetPolicy cp{b.st, ncells, b.cell_count, b.cell_start};
+    QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<CellOffsetPolicy>, scan_grid(ncells),
+                kScanThreads, cp, ctl);
+    QSGS_LAUNCH(tr, kClsSeed, s, k_cell_fill, blocks, 256, g, cg, b.st, b.list, b.cell_count,
+                b.cell_items, b.decision);
+    QSGS_LAUNCH(tr, kClsSeed, s, k_spacing_rounds, 1, 1024, g, cg, b.st, b.list, b.cell_start,
+                b.cell_items, b.decision);
+    decision = b.decision;
+  }
+  AcceptPolicy ap{g, b.st, b.grid, b.list, decision};
+  QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
+              ctl);
+  // Initial front (Sec. 2.3 step 2) replaces the candidate list.
+  FrontPolicy fp{g, b.st, b.grid, b.aux, b.list, 1u};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
+              fp, ctl);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
+  return cudaSuccess;
+}
+
+cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
+                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
+  ScanCtl ctl{b.st, b.scan_status, spin_limit};
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
+  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, 256, g, b.front, b.grid, b.aux, b.st, k0, k1);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
+  TrimPolicy tp{g, b.st, b.grid, b.aux};
+  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
+              ctl);
+  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, 0u};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
+              fp, ctl);
+  return cudaSuccess;
+}
+
+cudaError_t launch_step_begin(RunState* st, cudaStream_t s, Tracer& tr) {
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, st);
+  return cudaSuccess;
+}
+
+cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr) {
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_set_step_limit, 1, 1, st, extra);
+  return cudaSuccess;
+}
+
+cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
+                             Tracer& tr) {
+  const uint64_t chunks = ((uint64_t)g.n + 15) / 16;
+  uint64_t blocks = (chunks + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  QSGS_LAUNCH(tr, kClsFetch, s, k_unpack_u8, (uint32_t)blocks, 256, g, grid, out);
+  return cudaSuccess;
+}
+
+uint32_t default_grow_blocks() { return (uint32_t)num_sms() * 8; }
+
+}  // namespace qsgs

@@ -1,0 +1,144 @@
+// qsgs_launch.h -- internal interface between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "qsgs_device.cuh"
+
+namespace qsgs {
+
+// Kernel classes of the launch counter and the optional event profiler.
+enum KernelClass : int { kClsSeed, kClsGrow, kClsStepCtl, kClsTrim, kClsFront, kClsFetch, kNumClasses };
+inline const char* kernel_class_name(int c) {
+  static const char* names[kNumClasses] = {"seed", "grow", "step_ctl", "trim", "front", "fetch"};
+  return (c >= 0 && c < kNumClasses) ? names[c] : "?";
+}
+
+// Counts every kernel launch; when enabled, brackets each launch with a pair
+// of CUDA events and turns them into per-class totals at collect().
+class Tracer {
+ public:
+  uint64_t launches = 0;
+  uint64_t count[kNumClasses] = {};
+  double ms[kNumClasses] = {};
+
+  bool enabled() const { return enabled_; }
+
+  cudaError_t enable(bool on) {
+    reset();
+    enabled_ = on;
+    return cudaSuccess;
+  }
+
+  void reset() {
+    for (int c = 0; c < kNumClasses; ++c) { count[c] = 0; ms[c] = 0.0; }
+    for (auto& p : pending_) { free_.push_back(p.start); free_.push_back(p.stop); }
+    pending_.clear();
+  }
+
+  cudaError_t before(int cls, cudaStream_t s) {
+    ++launches;
+    if (!enabled_) return cudaSuccess;
+    Pending p{cls, take(), take()};
+    if (!p.start || !p.stop) return cudaErrorMemoryAllocation;
+    pending_.push_back(p);
+    return cudaEventRecord(p.start, s);
+  }
+
+  cudaError_t after(cudaStream_t s) {
+    if (!enabled_ || pending_.empty()) return cudaSuccess;
+    return cudaEventRecord(pending_.back().stop, s);
+  }
+
+  // Call after the stream has been synchronised.
+  cudaError_t collect() {
+    cudaError_t err = cudaSuccess;
+    for (auto& p : pending_) {
+      float t = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&t, p.start, p.stop);
+      if (e == cudaSuccess) { count[p.cls] += 1; ms[p.cls] += t; } else { err = e; }
+      free_.push_back(p.start);
+      free_.push_back(p.stop);
+    }
+    pending_.clear();
+    return err;
+  }
+
+  ~Tracer() {
+    reset();
+    for (auto e : free_) cudaEventDestroy(e);
+  }
+
+ private:
+  struct Pending {
+    int cls;
+    cudaEvent_t start, stop;
+  };
+  cudaEvent_t take() {
+    if (!free_.empty()) {
+      cudaEvent_t e = free_.back();
+      free_.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  bool enabled_ = false;
+  std::vector<Pending> pending_;
+  std::vector<cudaEvent_t> free_;
+};
+
+// Terminal statuses written into RunState::status (same values as the
+// public QSGS_* codes).
+enum : int32_t { kStatusDone = 0, kStatusStalled = 1, kStatusMaxSteps = 2 };
+
+struct StateInit {
+  unsigned long long nt;
+  unsigned long long t_ref[3];
+  unsigned long long t_seed;
+  uint32_t max_steps;
+};
+
+struct CellGeomHost {
+  uint32_t s, ncx, ncy, ncz;
+};
+
+struct SeedBuffers {
+  RunState* st;
+  unsigned long long* scan_status;
+  uint32_t* grid;
+  uint32_t* aux;
+  uint32_t* list;        // candidates, then the front
+  uint32_t* cell_count;  // spacing only
+  uint32_t* cell_start;
+  uint32_t* cell_items;
+  uint8_t* decision;
+  CellGeomHost cg;
+};
+
+struct StepBuffers {
+  RunState* st;
+  unsigned long long* scan_status;
+  uint32_t* grid;
+  uint32_t* aux;
+  uint32_t* front;
+};
+
+Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
+uint32_t default_grow_blocks();
+
+cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr);
+cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,
+                        uint32_t spin_limit, cudaStream_t s, Tracer& tr);
+cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
+                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr);
+cudaError_t launch_step_begin(RunState* st, cudaStream_t s, Tracer& tr);
+cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
+cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
+                             Tracer& tr);
+
+}  // namespace qsgs

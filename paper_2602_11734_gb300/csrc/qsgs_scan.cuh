@@ -1,0 +1,159 @@
+// qsgs_scan.cuh -- single-pass prefix scan with decoupled look-back.
+//
+// One persistent kernel template serves every order-preserving pass of the
+// generator (candidate compaction, front rebuild, exact trim, seed cap,
+// cell offsets).  Blocks take tiles from an atomic dispenser, so a tile
+// only ever waits on tiles already held by running blocks (Merrill &
+// Garland, "Single-pass parallel prefix scan with decoupled look-back",
+// NVIDIA TR 2016).  Every wait is bounded: after `spin_limit` polls the
+// block records kErrTimeout in the run state and carries on with a zero
+// prefix, so a fault is reported instead of hanging the GPU.
+#pragma once
+
+#include "qsgs_device.cuh"
+
+namespace qsgs {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;                         // items per thread
+constexpr int kScanTile = kScanThreads * kScanItems;  // items per tile
+
+// Tile status word: [63:62] flag, [61:33] launch epoch, [32:0] value.
+constexpr unsigned long long kFlagAggregate = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 33) - 1;
+constexpr uint32_t kEpochMask = (1u << 29) - 1;
+
+struct ScanCtl {
+  RunState* st;                  // epoch, tile dispenser, completion count, error
+  unsigned long long* status;    // one word per tile (zeroed before first use)
+  uint32_t spin_limit;
+};
+
+__device__ __forceinline__ unsigned long long tile_word(unsigned long long flag, uint32_t epoch,
+                                                        unsigned long long value) {
+  return flag | ((unsigned long long)(epoch & kEpochMask) << 33) | (value & kValueMask);
+}
+
+// Policy interface:
+//   bool active() const                  -- uniform: false skips the launch
+//   uint32_t n_items() const             -- number of items (read on device)
+//   Item load(uint32_t i) const          -- i < n_items
+//   uint32_t count(const Item&) const    -- outputs of the item
+//   void emit(const Item&, unsigned long long prefix) const
+//   void total(unsigned long long) const -- called once with the grand total
+template <class Policy>
+__global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, ScanCtl ctl) {
+  __shared__ uint32_t s_tile;
+  __shared__ unsigned long long s_prefix;
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+
+  if (!pol.active()) return;
+  const uint32_t n_items = pol.n_items();
+  const uint32_t ntiles = (uint32_t)(((unsigned long long)n_items + kScanTile - 1) / kScanTile);
+  const uint32_t epoch = *(volatile uint32_t*)&ctl.st->scan_epoch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) pol.total(0);
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctl.st->scan_tile, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) break;
+
+    typename Policy::Item it[kScanItems];
+    uint32_t cnt[kScanItems];
+    uint32_t mine = 0;
+    const unsigned long long base =
+        (unsigned long long)tile * kScanTile + (unsigned long long)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned long long i = base + k;
+      if (i < n_items) {
+        it[k] = pol.load((uint32_t)i);
+        cnt[k] = pol.count(it[k]);
+      } else {
+        cnt[k] = 0;
+      }
+      mine += cnt[k];
+    }
+
+    // Block-wide exclusive scan of the per-thread counts.
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_excl = warp ? s_warp[warp - 1] : 0;
+    const uint32_t aggregate = s_warp[kScanThreads / 32 - 1];
+
+    // Decoupled look-back (thread 0).
+    if (threadIdx.x == 0) {
+      unsigned long long prefix = 0;
+      if (tile == 0) {
+        atomicExch(&ctl.status[0], tile_word(kFlagPrefix, epoch, aggregate));
+      } else {
+        atomicExch(&ctl.status[tile], tile_word(kFlagAggregate, epoch, aggregate));
+        int64_t p = (int64_t)tile - 1;
+        while (p >= 0) {
+          unsigned long long w;
+          uint32_t polls = 0;
+          for (;;) {
+            w = *(volatile unsigned long long*)&ctl.status[p];
+            if ((w >> 62) != 0 && (uint32_t)((w >> 33) & kEpochMask) == (epoch & kEpochMask)) break;
+            if (++polls > ctl.spin_limit) {
+              atomicOr(&ctl.st->error, kErrTimeout);
+              w = kFlagPrefix;  // give up: treat as a zero inclusive prefix
+              break;
+            }
+            __nanosleep(32);
+          }
+          prefix += w & kValueMask;
+          if ((w & (3ull << 62)) == kFlagPrefix) break;
+          --p;
+        }
+        atomicExch(&ctl.status[tile], tile_word(kFlagPrefix, epoch, prefix + aggregate));
+      }
+      s_prefix = prefix;
+      if (tile == ntiles - 1) pol.total(prefix + aggregate);
+    }
+    __syncthreads();
+
+    unsigned long long off = s_prefix + warp_excl + (incl - mine);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (cnt[k] || pol.emit_empty()) {
+        if (base + k < n_items) pol.emit(it[k], off);
+      }
+      off += cnt[k];
+    }
+    __syncthreads();  // s_tile / s_warp / s_prefix are reused by the next tile
+  }
+
+  // The last block to finish re-arms the dispenser for the next launch.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t done = atomicAdd(&ctl.st->scan_done, 1u);
+    if (done == gridDim.x - 1) {
+      ctl.st->scan_tile = 0;
+      ctl.st->scan_done = 0;
+      ctl.st->scan_epoch = (epoch + 1) & kEpochMask;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace qsgs

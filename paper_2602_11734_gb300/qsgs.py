@@ -1,0 +1,283 @@
+"""Python binding of libqsgs (include/qsgs.h).
+
+Argument marshalling only: every step of generation runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory (the workspace
+and output tensors) and CUDA streams.  There is no CPU fallback: if the
+library is missing or no CUDA device is present, calls raise.
+
+The functions ``qsgs_*`` mirror the C entry points one to one; the
+``Generator`` class is a convenience wrapper that owns a workspace tensor
+and a stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libqsgs.so")
+
+QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING = 0, 1, 2, 3
+QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_CUDA = -1, -2, -3
+QSGS_ERR_TIMEOUT, QSGS_ERR_STATE, QSGS_ERR_NOMEM = -4, -5, -6
+QSGS_FMT_U8, QSGS_FMT_PACKED = 0, 1
+
+PARAM_KEYS = ("nx", "ny", "nz", "cd", "g_face", "g_edge", "g_corner", "spacing_s",
+              "target_solid_fraction", "target_count", "seed", "max_steps")
+
+
+class QsgsParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_uint32), ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32),
+                ("cd", ctypes.c_double), ("g_face", ctypes.c_double),
+                ("g_edge", ctypes.c_double), ("g_corner", ctypes.c_double),
+                ("spacing_s", ctypes.c_uint32), ("target_solid_fraction", ctypes.c_double),
+                ("target_count", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("max_steps", ctypes.c_uint32)]
+
+
+class QsgsStats(ctypes.Structure):
+    _fields_ = [("solid_count", ctypes.c_uint64), ("target_count", ctypes.c_uint64),
+                ("front_size", ctypes.c_uint64), ("n_candidates", ctypes.c_uint64),
+                ("n_seeds", ctypes.c_uint64), ("sum_front", ctypes.c_uint64),
+                ("steps", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("launches", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QsgsProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+
+class QsgsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libqsgs.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"libqsgs not built ({path} missing); run "
+                    "`python -m paper_2602_11734_gb300.build` (needs nvcc)")
+            L = ctypes.CDLL(path)
+            vp, u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+            P, S = ctypes.POINTER(QsgsParams), ctypes.POINTER(QsgsStats)
+            H = ctypes.c_void_p
+            sig = {
+                "qsgs_version": ([], ctypes.c_int),
+                "qsgs_strerror": ([ctypes.c_int], ctypes.c_char_p),
+                "qsgs_check_params": ([P, u64p, u64p, u64p], ctypes.c_int),
+                "qsgs_workspace_bytes": ([P], ctypes.c_size_t),
+                "qsgs_create": ([P, vp, ctypes.c_size_t, vp, ctypes.POINTER(H)], ctypes.c_int),
+                "qsgs_seed": ([H], ctypes.c_int),
+                "qsgs_grow_until": ([H, ctypes.c_uint32, S], ctypes.c_int),
+                "qsgs_fetch": ([H, vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+                "qsgs_query": ([H, S], ctypes.c_int),
+                "qsgs_set_profiling": ([H, ctypes.c_int], ctypes.c_int),
+                "qsgs_profile": ([H, ctypes.POINTER(QsgsProfileEntry), ctypes.c_int],
+                                 ctypes.c_int),
+                "qsgs_destroy": ([H], None),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load_library().qsgs_strerror(code).decode()
+    except RuntimeError:
+        return f"code {code}"
+
+
+def make_params(p: dict) -> QsgsParams:
+    unknown = set(p) - set(PARAM_KEYS)
+    if unknown:
+        raise KeyError(f"unknown parameter(s) {sorted(unknown)}")
+    q = dict(nx=1, ny=1, nz=1, cd=0.0, g_face=0.0, g_edge=0.0, g_corner=0.0, spacing_s=0,
+             target_solid_fraction=0.0, target_count=0, seed=0, max_steps=0)
+    q.update(p)
+    return QsgsParams(**q)
+
+
+# ---- thin one-to-one wrappers of the C entry points -----------------------
+def qsgs_check_params(p: dict):
+    """(Nt, T_seed, (T_face, T_edge, T_corner)); raises QsgsError if invalid."""
+    nt, ts = ctypes.c_uint64(), ctypes.c_uint64()
+    tr = (ctypes.c_uint64 * 3)()
+    rc = load_library().qsgs_check_params(ctypes.byref(make_params(p)), ctypes.byref(nt),
+                                          ctypes.byref(ts), tr)
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_check_params")
+    return nt.value, ts.value, tuple(tr)
+
+
+def qsgs_workspace_bytes(p: dict) -> int:
+    return int(load_library().qsgs_workspace_bytes(ctypes.byref(make_params(p))))
+
+
+def qsgs_create(p: dict, workspace_ptr: int, nbytes: int, stream_ptr: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    rc = load_library().qsgs_create(ctypes.byref(make_params(p)), ctypes.c_void_p(workspace_ptr),
+                                    nbytes, ctypes.c_void_p(stream_ptr), ctypes.byref(h))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_create")
+    return h
+
+
+def qsgs_seed(h) -> None:
+    rc = load_library().qsgs_seed(h)
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_seed")
+
+
+def qsgs_grow_until(h, max_steps: int = 0) -> tuple[int, dict]:
+    s = QsgsStats()
+    rc = load_library().qsgs_grow_until(h, max_steps, ctypes.byref(s))
+    if rc < 0:
+        raise QsgsError(rc, "qsgs_grow_until")
+    return rc, s.as_dict()
+
+
+def qsgs_fetch(h, dst_ptr: int, nbytes: int, fmt: int, dst_is_device: bool) -> None:
+    rc = load_library().qsgs_fetch(h, ctypes.c_void_p(dst_ptr), nbytes, fmt, int(dst_is_device))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_fetch")
+
+
+def qsgs_query(h) -> dict:
+    s = QsgsStats()
+    rc = load_library().qsgs_query(h, ctypes.byref(s))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_query")
+    return s.as_dict()
+
+
+def qsgs_set_profiling(h, enable: bool) -> None:
+    rc = load_library().qsgs_set_profiling(h, int(enable))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_set_profiling")
+
+
+def qsgs_profile(h) -> dict:
+    """{kernel class: (launches, total_ms)} of the event profiler."""
+    buf = (QsgsProfileEntry * 16)()
+    n = load_library().qsgs_profile(h, buf, 16)
+    if n < 0:
+        raise QsgsError(n, "qsgs_profile")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(min(n, 16))}
+
+
+def qsgs_destroy(h) -> None:
+    if h:
+        load_library().qsgs_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------
+@dataclass
+class Stats:
+    solid_count: int
+    target_count: int
+    front_size: int
+    n_candidates: int
+    n_seeds: int
+    sum_front: int
+    steps: int
+    status: int
+    launches: int
+
+
+class Generator:
+    """One realization bound to a torch-allocated workspace and stream."""
+
+    def __init__(self, params: dict, device=None, stream=None, workspace=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqsgs needs a CUDA device; there is no CPU fallback")
+        load_library()
+        self.params = dict(params)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.nbytes = qsgs_workspace_bytes(self.params)
+        if self.nbytes == 0:
+            raise QsgsError(QSGS_ERR_INVALID, "qsgs_workspace_bytes")
+        with torch.cuda.device(self.device):
+            if workspace is None:
+                workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self.workspace = workspace
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.handle = qsgs_create(self.params, workspace.data_ptr(), workspace.numel(),
+                                      self.stream.cuda_stream)
+        p = make_params(self.params)
+        self.shape = (p.nz, p.ny, p.nx)
+        self.n = p.nx * p.ny * p.nz
+        self.words = ((p.nx + 31) // 32) * p.ny * p.nz
+
+    def seed(self) -> None:
+        qsgs_seed(self.handle)
+
+    def grow(self, max_steps: int = 0) -> Stats:
+        _, s = qsgs_grow_until(self.handle, max_steps)
+        return Stats(**s)
+
+    def query(self) -> Stats:
+        return Stats(**qsgs_query(self.handle))
+
+    def fetch(self, out=None, fmt: str = "u8"):
+        """Phase map as a uint8 (nz, ny, nx) tensor, or the packed uint32
+        words (fmt='packed').  ``out`` may be a CUDA or CPU tensor."""
+        import torch
+        f = QSGS_FMT_U8 if fmt == "u8" else QSGS_FMT_PACKED
+        if out is None:
+            if f == QSGS_FMT_U8:
+                out = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
+            else:
+                out = torch.empty(self.words, dtype=torch.int32, device=self.device)
+        qsgs_fetch(self.handle, out.data_ptr(), out.numel() * out.element_size(), f, out.is_cuda)
+        return out
+
+    def set_profiling(self, enable: bool = True) -> None:
+        qsgs_set_profiling(self.handle, enable)
+
+    def profile(self) -> dict:
+        return qsgs_profile(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            qsgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate(params: dict, device=None, fmt: str = "u8"):
+    """Seed and grow one realization; returns (phase tensor on the device, Stats)."""
+    g = Generator(params, device=device)
+    try:
+        g.seed()
+        st = g.grow()
+        out = g.fetch(fmt=fmt)
+        return out, st
+    finally:
+        g.close()

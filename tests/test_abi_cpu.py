@@ -1,0 +1,100 @@
+"""The C-ABI library builds, loads and exports every declared entry point;
+its host-side parameter logic agrees with the oracle.  No GPU needed: only
+functions that touch no device are called."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2602_11734_gb300 import build as B
+from paper_2602_11734_gb300 import qsgs as Q
+from paper_2602_11734_gb300 import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return Q.load_library()
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(qsgs_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "qsgs_create" in syms and "qsgs_grow_until" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_version_and_strerror(lib):
+    assert lib.qsgs_version() >= 100
+    for code in (0, 1, 2, 3, -1, -2, -3, -4, -5, -6, 12345):
+        assert isinstance(Q.strerror(code), str) and Q.strerror(code)
+
+
+def test_check_params_matches_oracle(lib, oracle):
+    rng = np.random.default_rng(8)
+    cases = [workloads.small_64(), workloads.single_400()] + workloads.sweep_500()[:3]
+    cases += [workloads.random_small(rng) for _ in range(200)]
+    for p in cases:
+        assert Q.qsgs_check_params(p) == oracle.targets(p)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(cd=1.5), dict(cd=-0.1), dict(g_face=2.0),
+                                 dict(g_corner=float("nan")), dict(target_count=10**6),
+                                 dict(target_solid_fraction=1.2),
+                                 dict(nx=2**11, ny=2**11, nz=2**10)])
+def test_invalid_params_rejected(lib, bad):
+    p = dict(nx=8, ny=8, nz=8, target_solid_fraction=0.5)
+    p.update(bad)
+    with pytest.raises(Q.QsgsError) as e:
+        Q.qsgs_check_params(p)
+    assert e.value.code == Q.QSGS_ERR_INVALID
+    assert Q.qsgs_workspace_bytes(p) == 0
+
+
+def test_workspace_bytes(lib):
+    small = Q.qsgs_workspace_bytes(workloads.small_64())
+    assert small >= 4 * 64**3
+    big = Q.qsgs_workspace_bytes(workloads.single_400())
+    assert big >= 4 * 400**3 + 2 * 4 * 13 * 400 * 400
+    with_spacing = Q.qsgs_workspace_bytes(dict(workloads.small_64(), spacing_s=5))
+    assert with_spacing > small
+
+
+def test_create_rejects_bad_workspace_without_touching_the_device(lib):
+    p = Q.make_params(workloads.small_64())
+    need = lib.qsgs_workspace_bytes(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    rc = lib.qsgs_create(ctypes.byref(p), None, need, None, ctypes.byref(h))
+    assert rc == Q.QSGS_ERR_WORKSPACE and not h.value
+    rc = lib.qsgs_create(ctypes.byref(p), ctypes.c_void_p(256 * 7), need - 1, None, ctypes.byref(h))
+    assert rc == Q.QSGS_ERR_WORKSPACE
+    rc = lib.qsgs_create(ctypes.byref(p), ctypes.c_void_p(256 * 7 + 8), need, None, ctypes.byref(h))
+    assert rc == Q.QSGS_ERR_WORKSPACE
+    bad = Q.make_params(dict(workloads.small_64(), cd=3.0))
+    rc = lib.qsgs_create(ctypes.byref(bad), ctypes.c_void_p(256), 1 << 30, None, ctypes.byref(h))
+    assert rc == Q.QSGS_ERR_INVALID
+    assert lib.qsgs_create(ctypes.byref(p), None, 0, None, None) == Q.QSGS_ERR_INVALID
+
+
+def test_null_handles_are_rejected(lib):
+    s = Q.QsgsStats()
+    assert lib.qsgs_seed(None) == Q.QSGS_ERR_INVALID
+    assert lib.qsgs_grow_until(None, 0, ctypes.byref(s)) == Q.QSGS_ERR_INVALID
+    assert lib.qsgs_query(None, ctypes.byref(s)) == Q.QSGS_ERR_INVALID
+    assert lib.qsgs_fetch(None, None, 0, 0, 0) == Q.QSGS_ERR_INVALID
+    lib.qsgs_destroy(None)
