@@ -25,7 +25,9 @@ constexpr uint32_t kStepsPerSync = 8;      // steps enqueued between host checks
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t state, scan_status, grid, aux, list, cell_count, cell_start, cell_items, decision, total;
+  size_t state, scan_status, grid, aux, list, cell_count, cell_start, cell_items, decision;
+  size_t conf_off, adj, total;
+  uint64_t adj_cap;
   uint64_t ntiles;
   CellGeomHost cg;
 };
@@ -78,12 +80,18 @@ Layout make_layout(const qsgs_params* p) {
   L.scan_status = off; off = align_up(off + L.ntiles * sizeof(unsigned long long));
   L.grid = off; off = align_up(off + nwords * 4);
   L.aux = off; off = align_up(off + nwords * 4);
-  L.list = off; off = align_up(off + (n ? n : 1) * 4);
+  // Candidates (u32 each, at most N), then the front word list ({word,
+  // bits} pairs, at most nwords).
+  const uint64_t list_bytes = n * 4 > nwords * 8 ? n * 4 : nwords * 8;
+  L.list = off; off = align_up(off + list_bytes);
   if (ncells) {
     L.cell_count = off; off = align_up(off + ncells * 4);
     L.cell_start = off; off = align_up(off + (ncells + 1) * 4);
     L.cell_items = off; off = align_up(off + n * 4);
     L.decision = off; off = align_up(off + n);
+    L.conf_off = off; off = align_up(off + (n + 1) * 4);
+    L.adj_cap = n;
+    L.adj = off; off = align_up(off + L.adj_cap * 4);
   }
   L.total = off;
   return L;
@@ -103,7 +111,7 @@ struct qsgs_handle {
   uint32_t* grid;
   uint32_t* aux;
   uint32_t* list;
-  uint32_t *cell_count, *cell_start, *cell_items;
+  uint32_t *cell_count, *cell_start, *cell_items, *conf_off, *adj;
   uint8_t* decision;
   uint32_t k0, k1;
   uint32_t grow_blocks;
@@ -135,6 +143,7 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
   out->solid_count = s.solid;
   out->target_count = s.nt;
   out->front_size = s.front_n;
+  (void)s.front_words;
   out->n_candidates = s.cand_n;
   out->n_seeds = s.acc_n;
   out->sum_front = s.sum_front;
@@ -144,7 +153,7 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
 }
 
 StepBuffers step_buffers(const qsgs_handle* h) {
-  return StepBuffers{h->st, h->scan_status, h->grid, h->aux, h->list};
+  return StepBuffers{h->st, h->scan_status, h->grid, h->aux, reinterpret_cast<uint2*>(h->list)};
 }
 
 }  // namespace
@@ -214,6 +223,8 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->cell_start = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.cell_start) : nullptr;
   h->cell_items = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.cell_items) : nullptr;
   h->decision = spacing ? h->ws + L.decision : nullptr;
+  h->conf_off = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.conf_off) : nullptr;
+  h->adj = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.adj) : nullptr;
   h->k0 = (uint32_t)params->seed;
   h->k1 = (uint32_t)(params->seed >> 32);
   h->grow_blocks = default_grow_blocks();
@@ -243,8 +254,10 @@ int qsgs_seed(qsgs_handle* h) {
   init.max_steps = h->p.max_steps ? h->p.max_steps : 0xFFFFFFFFu;
   e = launch_init_state(h->st, init, h->stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  SeedBuffers b{h->st, h->scan_status, h->grid, h->aux, h->list, h->cell_count,
-                h->cell_start, h->cell_items, h->decision, h->L.cg};
+  SeedBuffers b{h->st,         h->scan_status, h->grid,     h->aux,
+                h->list,       h->cell_count,  h->cell_start, h->cell_items,
+                h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
+                h->L.cg};
   e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, h->stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->seeded = true;

@@ -184,7 +184,9 @@ struct alignas(256) RunState {
   unsigned long long live;       // attempts with a positive threshold
   unsigned long long sum_front;  // sum over steps of |A_t| (statistics)
   unsigned long long trim_keep;  // voxels of New_t kept by the final trim
-  uint32_t front_n;              // |A_t|
+  unsigned long long front_n;    // |A_t| (front voxels)
+  unsigned long long adj_n;      // spacing: total earlier-conflict entries
+  uint32_t front_words;          // entries of the front word list
   uint32_t cand_n;               // Bernoulli candidates
   uint32_t acc_n;                // seeds placed
   uint32_t t;                    // steps executed

@@ -48,6 +48,7 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->sum_front = 0;
   st->trim_keep = 0;
   st->front_n = 0;
+  st->front_words = 0;
   st->cand_n = 0;
   st->acc_n = 0;
   st->t = 0;
@@ -86,6 +87,7 @@ __global__ void k_step_end(RunState* st) {
     return;
   }
   st->sum_front += st->front_n;
+  st->front_n = 0;  // recounted by the front rebuild that follows
   const unsigned long long c = st->solid, k = st->claimed;
   if (c + k > st->nt) {
     st->trim = 1;
@@ -179,6 +181,8 @@ struct SeedCompactPolicy {
   uint32_t* cand;
   uint32_t k0, k1;
   using Item = WordItem;
+  __device__ uint32_t side(const Item&) const { return 0; }
+  __device__ unsigned long long* side_sum() const { return nullptr; }
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -209,14 +213,16 @@ struct SeedCompactPolicy {
   __device__ void total(unsigned long long n) const { st->cand_n = (uint32_t)n; }
 };
 
-// Sec. 2.3 step 2 / step 4: the active front rebuilt from the grid, in
-// ascending voxel order.  Also clears the claim grid for the next step.
+// Sec. 2.3 step 2 / step 4: the active front rebuilt from the grid, as an
+// ascending list of {word index, front bits} -- one entry per 32-voxel row
+// word that holds at least one front voxel.  The front voxels are counted
+// into front_n.  Also clears the claim grid for the next step.
 struct FrontPolicy {
   Geom g;
   RunState* st;
   const uint32_t* grid;
   uint32_t* aux;
-  uint32_t* front;
+  uint2* front;
   uint32_t always;  // 1: run even when no step is active (initial front)
   using Item = WordItem;
   __device__ bool active() const { return always || st->active; }
@@ -226,9 +232,11 @@ struct FrontPolicy {
     aux[w] = 0;
     return Item{w, front_word(g, grid, w)};
   }
-  __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
-  __device__ void emit(const Item& it, unsigned long long off) const { emit_word_bits(g, it, front, off); }
-  __device__ void total(unsigned long long n) const { st->front_n = (uint32_t)n; }
+  __device__ uint32_t count(const Item& it) const { return it.bits ? 1u : 0u; }
+  __device__ uint32_t side(const Item& it) const { return __popc(it.bits); }
+  __device__ unsigned long long* side_sum() const { return &st->front_n; }
+  __device__ void emit(const Item& it, unsigned long long off) const { front[off] = make_uint2(it.w, it.bits); }
+  __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
 };
 
 // Exact target: keep the trim_keep lowest-index voxels claimed in this step
@@ -239,6 +247,8 @@ struct TrimPolicy {
   uint32_t* grid;
   const uint32_t* aux;
   using Item = WordItem;
+  __device__ uint32_t side(const Item&) const { return 0; }
+  __device__ unsigned long long* side_sum() const { return nullptr; }
   __device__ bool active() const { return st->active && st->trim; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -270,6 +280,8 @@ struct AcceptPolicy {
     uint32_t v;
     uint32_t ok;
   };
+  __device__ uint32_t side(const Item&) const { return 0; }
+  __device__ unsigned long long* side_sum() const { return nullptr; }
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return st->cand_n; }
@@ -300,6 +312,8 @@ struct CellOffsetPolicy {
   struct Item {
     uint32_t i, c;
   };
+  __device__ uint32_t side(const Item&) const { return 0; }
+  __device__ unsigned long long* side_sum() const { return nullptr; }
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return ncells; }
@@ -356,13 +370,126 @@ __global__ void k_cell_fill(Geom g, CellGeom cg, const RunState* st, const uint3
   }
 }
 
-// One block runs all rounds; a round re-examines every undecided candidate.
+// Earlier conflicts of candidate i: candidates j < i at L1 distance < s,
+// found in the 27 cells around i.  count_only: just count them.
+__device__ __forceinline__ uint32_t scan_conflicts(const Geom& g, const CellGeom& cg,
+                                                   const uint32_t* cand, const uint32_t* start,
+                                                   const uint32_t* items, uint32_t i,
+                                                   uint32_t* out) {
+  uint32_t x, y, z;
+  decode_xyz(g, cand[i], x, y, z);
+  const int cx = (int)(x / cg.s), cy = (int)(y / cg.s), cz = (int)(z / cg.s);
+  uint32_t n = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = cz + dz;
+    if (zz < 0 || zz >= (int)cg.ncz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= (int)cg.ncy) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = cx + dx;
+        if (xx < 0 || xx >= (int)cg.ncx) continue;
+        const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
+        for (uint32_t k = start[cell]; k < start[cell + 1]; ++k) {
+          const uint32_t j = items[k];
+          if (j >= i) continue;
+          uint32_t xj, yj, zj;
+          decode_xyz(g, cand[j], xj, yj, zj);
+          const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
+          if (l1 >= (int)cg.s) continue;
+          if (out) out[n] = j;
+          ++n;
+        }
+      }
+    }
+  }
+  return n;
+}
+
+__global__ void k_conflict_count(Geom g, CellGeom cg, const RunState* st, const uint32_t* cand,
+                                 const uint32_t* start, const uint32_t* items, uint32_t* cnt) {
+  const uint32_t n = st->cand_n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    cnt[i] = scan_conflicts(g, cg, cand, start, items, i, nullptr);
+}
+
+// Exclusive offsets of the conflict lists (in place: counts -> offsets).
+struct ConflictOffsetPolicy {
+  RunState* st;
+  uint32_t* off;  // in: counts; out: offsets, off[cand_n] = total
+  struct Item {
+    uint32_t i, c;
+  };
+  __device__ uint32_t side(const Item&) const { return 0; }
+  __device__ unsigned long long* side_sum() const { return nullptr; }
+  __device__ bool active() const { return true; }
+  __device__ bool emit_empty() const { return true; }
+  __device__ uint32_t n_items() const { return st->cand_n; }
+  __device__ Item load(uint32_t i) const { return Item{i, off[i]}; }
+  __device__ uint32_t count(const Item& it) const { return it.c; }
+  __device__ void emit(const Item& it, unsigned long long o) const { off[it.i] = (uint32_t)o; }
+  __device__ void total(unsigned long long n) const {
+    off[st->cand_n] = (uint32_t)(n > 0xFFFFFFFFull ? 0xFFFFFFFFull : n);
+    st->adj_n = n;
+  }
+};
+
+__global__ void k_conflict_fill(Geom g, CellGeom cg, const RunState* st, const uint32_t* cand,
+                                const uint32_t* start, const uint32_t* items, const uint32_t* off,
+                                uint32_t* adj, unsigned long long cap) {
+  if (st->adj_n > cap) return;
+  const uint32_t n = st->cand_n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    scan_conflicts(g, cg, cand, start, items, i, adj + off[i]);
+}
+
+// Rounds over the conflict lists (one block).  Each round settles at least
+// the lowest undecided candidate, so cand_n + 1 rounds always suffice.
+__global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
+                                                            const uint32_t* off,
+                                                            const uint32_t* adj,
+                                                            uint8_t* decision,
+                                                            unsigned long long cap) {
+  __shared__ uint32_t s_undecided;
+  if (st->adj_n > cap) return;
+  const uint32_t n = st->cand_n;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = 0;
+  __syncthreads();
+  for (uint32_t round = 0; round <= n; ++round) {
+    if (threadIdx.x == 0) s_undecided = 0;
+    __syncthreads();
+    uint32_t mine = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      if (((volatile uint8_t*)decision)[i] != 0) continue;
+      bool pending = false, rejected = false;
+      for (uint32_t k = off[i]; k < off[i + 1]; ++k) {
+        const uint8_t dj = ((volatile uint8_t*)decision)[adj[k]];
+        if (dj == 1) { rejected = true; break; }
+        if (dj == 0) pending = true;
+      }
+      if (rejected) decision[i] = 2;
+      else if (!pending) decision[i] = 1;
+      else ++mine;
+    }
+    if (mine) atomicAdd(&s_undecided, mine);
+    __syncthreads();
+    const uint32_t left = s_undecided;
+    __syncthreads();
+    if (left == 0) break;
+  }
+}
+
+// Fallback when the conflict lists exceed their buffer: one block runs all
+// rounds and re-examines the 27 cells of every undecided candidate.
+
 __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, RunState* st,
                                                         const uint32_t* cand,
                                                         const uint32_t* start,
                                                         const uint32_t* items,
-                                                        uint8_t* decision) {
+                                                        uint8_t* decision,
+                                                        unsigned long long cap) {
   __shared__ uint32_t s_undecided;
+  if (st->adj_n <= cap) return;
   const uint32_t n = st->cand_n;
   const int s = (int)cg.s;
   for (uint32_t round = 0; round <= n; ++round) {
@@ -412,98 +539,177 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 }
 
 // ---------------------------------------------------------------------------
-// The growth step (Sec. 2.3 step 3, Algorithm 3 lines 4-13): every front
+// The growth step (Sec. 2.3 step 3, Algorithm 3 lines 4-13).  Every front
 // voxel a tries each void in-domain neighbour q = a + e_d with the draw
 // word (d & 3) of Philox block (a, 0, t, 0x200 | d >> 2) against the class
-// threshold of Eq. 1.  A claim is an atomicOr into the grid; the thread that
-// flips the bit also records q in the claim grid.  Whether q becomes solid
-// depends only on the start-of-step grid and the draws, never on the order
-// of the threads: a thread that already sees q solid skips it, and q is
+// threshold of Eq. 1; a success claims q with an atomicOr into the grid, and
+// the thread that flips the bit also records q in the claim grid.  Whether q
+// becomes solid depends only on the start-of-step front and the draws, never
+// on thread order: a thread that already sees q solid skips it, and q is
 // solid either way.
+//
+// Work layout.  A warp takes 32 entries of the front word list.  Phase 1:
+// each lane builds, bit-parallel over its 32 voxels, the 26 "void target"
+// masks V_d (bit i: voxel i is a front voxel and its d-neighbour is void and
+// inside the domain) and the 7 Philox-block masks B_b = OR of V_d over the
+// live directions of block b.  Phase 2: the warp spreads the (voxel, block)
+// pairs of all 32 words evenly over its lanes, one Philox call per pair, so
+// no lane idles while another draws.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t nb_row_bits(const Geom& g, const uint32_t* grid, uint32_t rn,
-                                                uint32_t xw, uint32_t bi) {
-  const uint32_t* row = grid + (size_t)rn * g.W;
-  uint32_t c = row[xw];
-  if (xw == g.W - 1) c |= g.pad_mask;
-  if (bi == 0) {
-    const uint32_t l = xw > 0 ? row[xw - 1] : 0xFFFFFFFFu;
-    return __funnelshift_r(l, c, 31) & 7u;
-  }
-  uint32_t rr = 0;
-  if (bi == 31) {
+constexpr int kGrowThreads = 256;
+constexpr int kGrowWarps = kGrowThreads / 32;
+
+struct GrowWarpSmem {
+  uint32_t V[32][27];  // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
+  uint32_t B[7][32];   // per block, per lane word
+  uint32_t off[33];    // exclusive offsets of the current block's pairs
+  uint32_t r[32], xw[32], v0[32];
+};
+
+// Position of the j-th (0-based) set bit of m; m has more than j set bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t j) {
+  uint32_t pos = 0, c;
+  c = __popc(m & 0xFFFFu); if (j >= c) { j -= c; pos += 16; m >>= 16; }
+  c = __popc(m & 0xFFu);   if (j >= c) { j -= c; pos += 8;  m >>= 8; }
+  c = __popc(m & 0xFu);    if (j >= c) { j -= c; pos += 4;  m >>= 4; }
+  c = __popc(m & 0x3u);    if (j >= c) { j -= c; pos += 2;  m >>= 2; }
+  if (j >= (m & 1u)) pos += 1;
+  return pos;
+}
+
+// Direction index of offset (dx, dy, dz), evaluated at compile time.
+__host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
+  int found = -1;
+  for (int d = 0; d < 26; ++d)
+    if (kDirs[d].dx == dx && kDirs[d].dy == dy && kDirs[d].dz == dz) found = d;
+  return found;
+}
+
+template <int DZ, int DY>
+__device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, uint32_t y,
+                                          uint32_t z, uint32_t r, uint32_t xw, uint32_t src,
+                                          uint32_t live_dirs, uint32_t (&V)[26]) {
+  const int yy = (int)y + DY, zz = (int)z + DZ;
+  uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
+  if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
+    const uint32_t* row = grid + (size_t)((int)r + DY + (int)g.ny * DZ) * g.W;
+    c = row[xw];
+    if (xw == g.W - 1) c |= g.pad_mask;
+    if (xw > 0) l = row[xw - 1];
     if (xw + 1 < g.W) {
       rr = row[xw + 1];
       if (xw + 1 == g.W - 1) rr |= g.pad_mask;
-    } else {
-      rr = 0xFFFFFFFFu;
     }
   }
-  return __funnelshift_r(c, rr, bi - 1) & 7u;
+  const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
+  const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
+  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
+  V[dm] = ~at_minus & src & (0u - ((live_dirs >> dm) & 1u));
+  if (d0 >= 0) V[d0 < 0 ? 0 : d0] = ~c & src & (0u - ((live_dirs >> (d0 < 0 ? 0 : d0)) & 1u));
+  V[dp] = ~at_plus & src & (0u - ((live_dirs >> dp) & 1u));
 }
 
-__global__ void __launch_bounds__(256) k_grow(Geom g, const uint32_t* __restrict__ front,
-                                              uint32_t* grid, uint32_t* aux, RunState* st,
-                                              uint32_t k0, uint32_t k1) {
+__global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* __restrict__ front,
+                                                       uint32_t* grid, uint32_t* aux,
+                                                       RunState* st, uint32_t k0, uint32_t k1) {
+  __shared__ GrowWarpSmem smem[kGrowWarps];
   if (!st->active) return;
-  const uint32_t n = st->front_n;
+  const uint32_t n = st->front_words;
   const uint32_t t = st->t;
   const unsigned long long T0 = st->thr[0], T1 = st->thr[1], T2 = st->thr[2];
-  const uint32_t live_mask = (T0 ? class_pos_mask(0) : 0u) | (T1 ? class_pos_mask(1) : 0u) |
-                             (T2 ? class_pos_mask(2) : 0u);
+  uint32_t live_dirs = 0;
+#pragma unroll
+  for (int d = 0; d < 26; ++d) {
+    const int c = dir_cls(d);
+    if ((c == 0 ? T0 : (c == 1 ? T1 : T2)) != 0) live_dirs |= 1u << d;
+  }
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  GrowWarpSmem& S = smem[warp];
+  const uint32_t nwarps = gridDim.x * kGrowWarps;
   uint32_t my_claimed = 0, my_live = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t v = front[i];
-    uint32_t x, y, z;
-    decode_xyz(g, v, x, y, z);
-    const uint32_t r = y + g.ny * z;
-    const uint32_t xw = x >> 5, bi = x & 31;
-    // 27-bit neighbourhood, bit set = solid or outside the domain.
-    uint32_t nb = 0;
+
+  for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
+    // Phase 1: masks of this lane's word.
+    uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
+    const uint32_t idx = base + lane;
+    if (idx < n) {
+      const uint2 e = front[idx];
+      const uint32_t w = e.x, src = e.y;
+      const uint32_t r = fast_div(w, g.div_W);
+      const uint32_t xw = w - r * g.W;
+      const uint32_t z = fast_div(r, g.div_ny);
+      const uint32_t y = r - z * g.ny;
+      uint32_t V[26];
+      row_masks<-1, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<-1, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<-1, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<0, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<0, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<0, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<1, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<1, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
+      row_masks<1, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = (int)y + dy, zz = (int)z + dz;
-        uint32_t bits3 = 7u;
-        if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz)
-          bits3 = nb_row_bits(g, grid, (uint32_t)((int)r + dy + (int)g.ny * dz), xw, bi);
-        nb |= bits3 << ((dz + 1) * 9 + (dy + 1) * 3);
+      for (int d = 0; d < 26; ++d) {
+        S.V[lane][d] = V[d];
+        Bm[d >> 2] |= V[d];
       }
+      S.r[lane] = r;
+      S.xw[lane] = xw;
+      S.v0[lane] = r * g.nx + xw * 32u;
     }
-    const uint32_t cand = ~nb & kNbAll & ~kNbCentre & live_mask;
-    if (!cand) continue;
-    my_live += __popc(cand);
+#pragma unroll
+    for (int b = 0; b < 7; ++b) S.B[b][lane] = Bm[b];
+    __syncwarp();
+
+    // Phase 2: one Philox call per (voxel, block) pair, spread over the warp.
 #pragma unroll
     for (int b = 0; b < 7; ++b) {
-      const uint32_t bm = cand & block_pos_mask(b);
-      if (!bm) continue;
-      const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | (uint32_t)b}, k0, k1);
+      const uint32_t cnt = __popc(Bm[b]);
+      uint32_t incl = cnt;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int d = 4 * b + j;
-        if (d >= 26) continue;
-        if (!((bm >> dir_pos(d)) & 1u)) continue;
-        const int cls = dir_cls(d);
-        const unsigned long long T = cls == 0 ? T0 : (cls == 1 ? T1 : T2);
-        if ((unsigned long long)u4_word(rnd, j) >= T) continue;
-        const uint32_t xx = (uint32_t)((int)x + dir_dx(d));
-        const uint32_t rq = (uint32_t)((int)r + dir_dy(d) + (int)g.ny * dir_dz(d));
-        const size_t wq = (size_t)rq * g.W + (xx >> 5);
-        const uint32_t bit = 1u << (xx & 31);
-        const uint32_t old = atomicOr(grid + wq, bit);
-        if (!(old & bit)) {
-          ++my_claimed;
-          atomicOr(aux + wq, bit);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      S.off[lane] = incl - cnt;
+      if (lane == 31) S.off[32] = total;
+      __syncwarp();
+      for (uint32_t k = lane; k < total; k += 32) {
+        uint32_t owner = 0;
+#pragma unroll
+        for (uint32_t step = 16; step >= 1; step >>= 1)
+          if (S.off[owner + step] <= k) owner += step;
+        const uint32_t i = select_bit(S.B[b][owner], k - S.off[owner]);
+        const uint32_t v = S.v0[owner] + i;
+        const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | (uint32_t)b}, k0, k1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int d = 4 * b + j;
+          if (d >= 26) continue;
+          if (!((S.V[owner][d] >> i) & 1u)) continue;
+          ++my_live;
+          const int cls = dir_cls(d);
+          const unsigned long long T = cls == 0 ? T0 : (cls == 1 ? T1 : T2);
+          if ((unsigned long long)u4_word(rnd, j) >= T) continue;
+          const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
+          const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
+          const size_t wq = (size_t)rq * g.W + (xx >> 5);
+          const uint32_t bit = 1u << (xx & 31);
+          const uint32_t old = atomicOr(grid + wq, bit);
+          if (!(old & bit)) {
+            ++my_claimed;
+            atomicOr(aux + wq, bit);
+          }
         }
       }
+      __syncwarp();  // S.off is rewritten for the next block
     }
   }
-  // One atomic per warp for the step's counters.
   const uint32_t wc = __reduce_add_sync(0xffffffffu, my_claimed);
   const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (wc) atomicAdd(&st->claimed, (unsigned long long)wc);
     if (wl) atomicAdd(&st->live, (unsigned long long)wl);
   }
@@ -616,15 +822,24 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
                 kScanThreads, cp, ctl);
     QSGS_LAUNCH(tr, kClsSeed, s, k_cell_fill, blocks, 256, g, cg, b.st, b.list, b.cell_count,
                 b.cell_items, b.decision);
+    QSGS_LAUNCH(tr, kClsSeed, s, k_conflict_count, blocks, 256, g, cg, b.st, b.list, b.cell_start,
+                b.cell_items, b.conf_off);
+    ConflictOffsetPolicy op{b.st, b.conf_off};
+    QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<ConflictOffsetPolicy>, scan_grid(g.n),
+                kScanThreads, op, ctl);
+    QSGS_LAUNCH(tr, kClsSeed, s, k_conflict_fill, blocks, 256, g, cg, b.st, b.list, b.cell_start,
+                b.cell_items, b.conf_off, b.adj, b.adj_cap);
+    QSGS_LAUNCH(tr, kClsSeed, s, k_spacing_rounds_csr, 1, 1024, b.st, b.conf_off, b.adj,
+                b.decision, b.adj_cap);
     QSGS_LAUNCH(tr, kClsSeed, s, k_spacing_rounds, 1, 1024, g, cg, b.st, b.list, b.cell_start,
-                b.cell_items, b.decision);
+                b.cell_items, b.decision, b.adj_cap);
     decision = b.decision;
   }
   AcceptPolicy ap{g, b.st, b.grid, b.list, decision};
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
               ctl);
   // Initial front (Sec. 2.3 step 2) replaces the candidate list.
-  FrontPolicy fp{g, b.st, b.grid, b.aux, b.list, 1u};
+  FrontPolicy fp{g, b.st, b.grid, b.aux, reinterpret_cast<uint2*>(b.list), 1u};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
               fp, ctl);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
@@ -635,7 +850,8 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
                         uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
-  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, 256, g, b.front, b.grid, b.aux, b.st, k0, k1);
+  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.front, b.grid, b.aux, b.st,
+              k0, k1);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
   TrimPolicy tp{g, b.st, b.grid, b.aux};
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,

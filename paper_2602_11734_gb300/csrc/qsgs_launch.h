@@ -117,6 +117,9 @@ struct SeedBuffers {
   uint32_t* cell_start;
   uint32_t* cell_items;
   uint8_t* decision;
+  uint32_t* conf_off;            // cand_n + 1 conflict-list offsets
+  uint32_t* adj;                 // conflict lists
+  unsigned long long adj_cap;    // entries adj can hold
   CellGeomHost cg;
 };
 
@@ -125,7 +128,7 @@ struct StepBuffers {
   unsigned long long* scan_status;
   uint32_t* grid;
   uint32_t* aux;
-  uint32_t* front;
+  uint2* front;  // {word index, front bits} list
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);

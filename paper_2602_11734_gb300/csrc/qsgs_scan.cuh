@@ -42,6 +42,8 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 //   uint32_t count(const Item&) const    -- outputs of the item
 //   void emit(const Item&, unsigned long long prefix) const
 //   void total(unsigned long long) const -- called once with the grand total
+//   uint32_t side(const Item&) const     -- a second per-item value, summed
+//   unsigned long long* side_sum() const --   into this counter (nullptr: none)
 template <class Policy>
 __global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, ScanCtl ctl) {
   __shared__ uint32_t s_tile;
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, Scan
 
     typename Policy::Item it[kScanItems];
     uint32_t cnt[kScanItems];
-    uint32_t mine = 0;
+    uint32_t mine = 0, side = 0;
     const unsigned long long base =
         (unsigned long long)tile * kScanTile + (unsigned long long)threadIdx.x * kScanItems;
 #pragma unroll
@@ -72,10 +74,16 @@ __global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, Scan
       if (i < n_items) {
         it[k] = pol.load((uint32_t)i);
         cnt[k] = pol.count(it[k]);
+        side += pol.side(it[k]);
       } else {
         cnt[k] = 0;
       }
       mine += cnt[k];
+    }
+
+    if (pol.side_sum() != nullptr) {
+      const uint32_t ws = __reduce_add_sync(0xffffffffu, side);
+      if (lane == 0 && ws) atomicAdd(pol.side_sum(), (unsigned long long)ws);
     }
 
     // Block-wide exclusive scan of the per-thread counts.
