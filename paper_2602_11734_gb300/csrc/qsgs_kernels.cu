@@ -550,32 +550,21 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 //
 // Work layout.  A warp takes 32 entries of the front word list.  Phase 1:
 // each lane builds, bit-parallel over its 32 voxels, the 26 "void target"
-// masks V_d (bit i: voxel i is a front voxel and its d-neighbour is void and
-// inside the domain) and the 7 Philox-block masks B_b = OR of V_d over the
-// live directions of block b.  Phase 2: the warp spreads the (voxel, block)
-// pairs of all 32 words evenly over its lanes, one Philox call per pair, so
-// no lane idles while another draws.
+// masks V_d (bit i: voxel i is a front voxel, its d-neighbour is void and
+// inside the domain, and d's class has a positive threshold) and the 7
+// Philox-block masks B_b = OR of V_d over the directions of block b.
+// Phase 2, per block b: the lanes queue their (word, voxel) pairs with a
+// set bit in B_b in shared memory, then the warp drains the queue one pair
+// per lane, one Philox call per pair, so no lane idles while another draws.
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
 
 struct GrowWarpSmem {
-  uint32_t V[32][27];  // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
-  uint32_t B[7][32];   // per block, per lane word
-  uint32_t off[33];    // exclusive offsets of the current block's pairs
+  uint32_t V[32][27];   // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
+  uint16_t Q[32 * 32];  // queued pairs of the current block: lane << 5 | bit
   uint32_t r[32], xw[32], v0[32];
 };
-
-// Position of the j-th (0-based) set bit of m; m has more than j set bits.
-__device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t j) {
-  uint32_t pos = 0, c;
-  c = __popc(m & 0xFFFFu); if (j >= c) { j -= c; pos += 16; m >>= 16; }
-  c = __popc(m & 0xFFu);   if (j >= c) { j -= c; pos += 8;  m >>= 8; }
-  c = __popc(m & 0xFu);    if (j >= c) { j -= c; pos += 4;  m >>= 4; }
-  c = __popc(m & 0x3u);    if (j >= c) { j -= c; pos += 2;  m >>= 2; }
-  if (j >= (m & 1u)) pos += 1;
-  return pos;
-}
 
 // Direction index of offset (dx, dy, dz), evaluated at compile time.
 __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
@@ -585,10 +574,11 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
   return found;
 }
 
+// V masks of the three directions that land in row (y+DY, z+DZ).
 template <int DZ, int DY>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, uint32_t y,
                                           uint32_t z, uint32_t r, uint32_t xw, uint32_t src,
-                                          uint32_t live_dirs, uint32_t (&V)[26]) {
+                                          uint32_t live_dirs, uint32_t (&V)[27], uint32_t (&Bm)[7]) {
   const int yy = (int)y + DY, zz = (int)z + DZ;
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
@@ -605,18 +595,27 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, u
   const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
   constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   V[dm] = ~at_minus & src & (0u - ((live_dirs >> dm) & 1u));
-  if (d0 >= 0) V[d0 < 0 ? 0 : d0] = ~c & src & (0u - ((live_dirs >> (d0 < 0 ? 0 : d0)) & 1u));
+  Bm[dm >> 2] |= V[dm];
+  if (d0 >= 0) {
+    constexpr int d = d0 < 0 ? 26 : d0;
+    V[d] = ~c & src & (0u - ((live_dirs >> (d & 31)) & 1u));
+    Bm[(d >> 2) % 7] |= V[d];
+  }
   V[dp] = ~at_plus & src & (0u - ((live_dirs >> dp) & 1u));
+  Bm[dp >> 2] |= V[dp];
 }
 
 __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* __restrict__ front,
-                                                       uint32_t* grid, uint32_t* aux,
-                                                       RunState* st, uint32_t k0, uint32_t k1) {
+                                                          uint32_t* grid, uint32_t* aux,
+                                                          RunState* st, uint32_t k0, uint32_t k1) {
   __shared__ GrowWarpSmem smem[kGrowWarps];
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
+  // Live classes have T >= 1, so r < T  <=>  r <= T - 1 in 32 bits.
   const unsigned long long T0 = st->thr[0], T1 = st->thr[1], T2 = st->thr[2];
+  const uint32_t tm[3] = {(uint32_t)(T0 - (T0 != 0)), (uint32_t)(T1 - (T1 != 0)),
+                          (uint32_t)(T2 - (T2 != 0))};
   uint32_t live_dirs = 0;
 #pragma unroll
   for (int d = 0; d < 26; ++d) {
@@ -639,33 +638,31 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
       const uint32_t xw = w - r * g.W;
       const uint32_t z = fast_div(r, g.div_ny);
       const uint32_t y = r - z * g.ny;
-      uint32_t V[26];
-      row_masks<-1, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<-1, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<-1, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<0, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<0, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<0, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<1, -1>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<1, 0>(g, grid, y, z, r, xw, src, live_dirs, V);
-      row_masks<1, 1>(g, grid, y, z, r, xw, src, live_dirs, V);
+      uint32_t V[27];
+      row_masks<-1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<-1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<-1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<0, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<0, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<0, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      row_masks<1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
 #pragma unroll
-      for (int d = 0; d < 26; ++d) {
-        S.V[lane][d] = V[d];
-        Bm[d >> 2] |= V[d];
-      }
+      for (int d = 0; d < 26; ++d) S.V[lane][d] = V[d];
       S.r[lane] = r;
       S.xw[lane] = xw;
       S.v0[lane] = r * g.nx + xw * 32u;
     }
-#pragma unroll
-    for (int b = 0; b < 7; ++b) S.B[b][lane] = Bm[b];
-    __syncwarp();
 
-    // Phase 2: one Philox call per (voxel, block) pair, spread over the warp.
-#pragma unroll
+    // Phase 2: per block, queue the pairs, then one Philox call per pair.
+#pragma unroll 1
     for (int b = 0; b < 7; ++b) {
-      const uint32_t cnt = __popc(Bm[b]);
+      uint32_t m = Bm[0];
+#pragma unroll
+      for (int k = 1; k < 7; ++k)
+        if (b == k) m = Bm[k];
+      const uint32_t cnt = __popc(m);
       uint32_t incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -673,15 +670,16 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
         if (lane >= (uint32_t)o) incl += y;
       }
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      S.off[lane] = incl - cnt;
-      if (lane == 31) S.off[32] = total;
+      uint32_t pos = incl - cnt;
+      while (m) {
+        const uint32_t i = __ffs(m) - 1;
+        m &= m - 1;
+        S.Q[pos++] = (uint16_t)((lane << 5) | i);
+      }
       __syncwarp();
       for (uint32_t k = lane; k < total; k += 32) {
-        uint32_t owner = 0;
-#pragma unroll
-        for (uint32_t step = 16; step >= 1; step >>= 1)
-          if (S.off[owner + step] <= k) owner += step;
-        const uint32_t i = select_bit(S.B[b][owner], k - S.off[owner]);
+        const uint32_t e = S.Q[k];
+        const uint32_t owner = e >> 5, i = e & 31u;
         const uint32_t v = S.v0[owner] + i;
         const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | (uint32_t)b}, k0, k1);
 #pragma unroll
@@ -691,8 +689,8 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
           if (!((S.V[owner][d] >> i) & 1u)) continue;
           ++my_live;
           const int cls = dir_cls(d);
-          const unsigned long long T = cls == 0 ? T0 : (cls == 1 ? T1 : T2);
-          if ((unsigned long long)u4_word(rnd, j) >= T) continue;
+          const uint32_t thr = cls == 0 ? tm[0] : (cls == 1 ? tm[1] : tm[2]);
+          if (u4_word(rnd, j) > thr) continue;
           const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
           const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
           const size_t wq = (size_t)rq * g.W + (xx >> 5);
@@ -704,7 +702,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
           }
         }
       }
-      __syncwarp();  // S.off is rewritten for the next block
+      __syncwarp();  // S.Q is refilled for the next block
     }
   }
   const uint32_t wc = __reduce_add_sync(0xffffffffu, my_claimed);

@@ -108,35 +108,50 @@ __global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, Scan
     const uint32_t warp_excl = warp ? s_warp[warp - 1] : 0;
     const uint32_t aggregate = s_warp[kScanThreads / 32 - 1];
 
-    // Decoupled look-back (thread 0).
-    if (threadIdx.x == 0) {
+    // Decoupled look-back by warp 0: each round reads the 32 tiles before
+    // the current window in parallel, waits (bounded) until all of them have
+    // published, and stops at the nearest inclusive prefix.
+    if (warp == 0) {
       unsigned long long prefix = 0;
       if (tile == 0) {
-        atomicExch(&ctl.status[0], tile_word(kFlagPrefix, epoch, aggregate));
+        if (lane == 0) atomicExch(&ctl.status[0], tile_word(kFlagPrefix, epoch, aggregate));
       } else {
-        atomicExch(&ctl.status[tile], tile_word(kFlagAggregate, epoch, aggregate));
-        int64_t p = (int64_t)tile - 1;
-        while (p >= 0) {
-          unsigned long long w;
-          uint32_t polls = 0;
-          for (;;) {
-            w = *(volatile unsigned long long*)&ctl.status[p];
-            if ((w >> 62) != 0 && (uint32_t)((w >> 33) & kEpochMask) == (epoch & kEpochMask)) break;
-            if (++polls > ctl.spin_limit) {
-              atomicOr(&ctl.st->error, kErrTimeout);
-              w = kFlagPrefix;  // give up: treat as a zero inclusive prefix
-              break;
+        if (lane == 0) atomicExch(&ctl.status[tile], tile_word(kFlagAggregate, epoch, aggregate));
+        int64_t window_end = (int64_t)tile - 1;  // highest tile of the window
+        for (;;) {
+          const int64_t p = window_end - lane;  // lane 0 = nearest predecessor
+          unsigned long long w = kFlagPrefix;  // tiles before 0: empty prefix
+          if (p >= 0) {
+            uint32_t polls = 0;
+            for (;;) {
+              w = *(volatile unsigned long long*)&ctl.status[p];
+              if ((w >> 62) != 0 && (uint32_t)((w >> 33) & kEpochMask) == (epoch & kEpochMask)) break;
+              if (++polls > ctl.spin_limit) {
+                atomicOr(&ctl.st->error, kErrTimeout);
+                w = kFlagPrefix;  // give up: treat as a zero inclusive prefix
+                break;
+              }
+              __nanosleep(32);
             }
-            __nanosleep(32);
           }
-          prefix += w & kValueMask;
-          if ((w & (3ull << 62)) == kFlagPrefix) break;
-          --p;
+          const bool is_prefix = (w & (3ull << 62)) == kFlagPrefix;
+          const uint32_t pmask = __ballot_sync(0xffffffffu, is_prefix);
+          // Lanes up to and including the nearest inclusive prefix contribute.
+          const int stop = pmask ? __ffs(pmask) - 1 : 31;
+          unsigned long long v = (lane <= stop) ? (w & kValueMask) : 0ull;
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          prefix += v;
+          if (pmask) break;
+          window_end -= 32;
         }
-        atomicExch(&ctl.status[tile], tile_word(kFlagPrefix, epoch, prefix + aggregate));
+        if (lane == 0)
+          atomicExch(&ctl.status[tile], tile_word(kFlagPrefix, epoch, prefix + aggregate));
       }
-      s_prefix = prefix;
-      if (tile == ntiles - 1) pol.total(prefix + aggregate);
+      if (lane == 0) {
+        s_prefix = prefix;
+        if (tile == ntiles - 1) pol.total(prefix + aggregate);
+      }
     }
     __syncthreads();
 
