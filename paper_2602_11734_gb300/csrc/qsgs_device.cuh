@@ -82,6 +82,37 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The ten round keys of a 64-bit seed, precomputed on the host so that a
+// kernel can take them as (constant-bank) parameters.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys make_philox_keys(uint64_t seed) {
+  PhiloxKeys k{};
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int i = 0; i < 10; ++i) {
+    k.k0[i] = a;
+    k.k1[i] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return k;
+}
+
+// Philox4x32-10 with precomputed round keys; each round's two products are
+// formed as 64-bit multiplies.
+__device__ __forceinline__ U4 philox4x32_10(U4 c, const PhiloxKeys& key) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ key.k0[i], (uint32_t)p1,
+           (uint32_t)(p0 >> 32) ^ c.w ^ key.k1[i], (uint32_t)p0};
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t u4_word(const U4& r, int j) {
   return j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
 }

@@ -553,16 +553,17 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // masks V_d (bit i: voxel i is a front voxel, its d-neighbour is void and
 // inside the domain, and d's class has a positive threshold) and the 7
 // Philox-block masks B_b = OR of V_d over the directions of block b.
-// Phase 2, per block b: the lanes queue their (word, voxel) pairs with a
-// set bit in B_b in shared memory, then the warp drains the queue one pair
-// per lane, one Philox call per pair, so no lane idles while another draws.
+// Phase 2: the lanes queue their (word, block, voxel) pairs in shared
+// memory, then the warp drains the queue one pair per lane -- one Philox
+// call per pair -- so no lane idles while another draws.
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
+constexpr int kGrowQueue = 1024;  // pairs per drain round; a word has at most 7 * 32
 
 struct GrowWarpSmem {
-  uint32_t V[32][27];   // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
-  uint16_t Q[32 * 32];  // queued pairs of the current block: lane << 5 | bit
+  uint32_t V[32][27];        // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
+  uint16_t Q[kGrowQueue];    // queued pairs: lane << 8 | block << 5 | bit
   uint32_t r[32], xw[32], v0[32];
 };
 
@@ -607,21 +608,24 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, u
 
 __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* __restrict__ front,
                                                           uint32_t* grid, uint32_t* aux,
-                                                          RunState* st, uint32_t k0, uint32_t k1) {
+                                                          RunState* st, const PhiloxKeys keys) {
   __shared__ GrowWarpSmem smem[kGrowWarps];
+  __shared__ uint32_t s_thr[28];  // per direction: T - 1 (draw succeeds iff r <= it)
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
-  // Live classes have T >= 1, so r < T  <=>  r <= T - 1 in 32 bits.
-  const unsigned long long T0 = st->thr[0], T1 = st->thr[1], T2 = st->thr[2];
-  const uint32_t tm[3] = {(uint32_t)(T0 - (T0 != 0)), (uint32_t)(T1 - (T1 != 0)),
-                          (uint32_t)(T2 - (T2 != 0))};
   uint32_t live_dirs = 0;
 #pragma unroll
   for (int d = 0; d < 26; ++d) {
     const int c = dir_cls(d);
-    if ((c == 0 ? T0 : (c == 1 ? T1 : T2)) != 0) live_dirs |= 1u << d;
+    if (st->thr[c] != 0) live_dirs |= 1u << d;
   }
+  if (threadIdx.x < 28) {
+    const int d = threadIdx.x;
+    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
+    s_thr[d] = T ? (uint32_t)(T - 1) : 0u;  // dead directions never reach the test
+  }
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
@@ -654,43 +658,63 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
       S.xw[lane] = xw;
       S.v0[lane] = r * g.nx + xw * 32u;
     }
+    uint32_t items = 0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b) items += __popc(Bm[b]);
+    uint32_t incl = items;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t excl = incl - items;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
 
-    // Phase 2: per block, queue the pairs, then one Philox call per pair.
-#pragma unroll 1
-    for (int b = 0; b < 7; ++b) {
-      uint32_t m = Bm[0];
+    // Phase 2: drain in rounds of at most kGrowQueue pairs (whole words).
+    uint32_t done = 0;  // pairs of the lanes already drained
+    while (done < total) {
+      // Lanes whose pairs all fit into this round.
+      const bool fits = excl >= done && incl - done <= (uint32_t)kGrowQueue;
+      const uint32_t fit_mask = __ballot_sync(0xffffffffu, fits && items > 0);
+      uint32_t round_end = done;
+      if (fit_mask) round_end = __shfl_sync(0xffffffffu, incl, 31 - __clz(fit_mask));
+      if (fits && items > 0) {
+        uint32_t pos = excl - done;
 #pragma unroll
-      for (int k = 1; k < 7; ++k)
-        if (b == k) m = Bm[k];
-      const uint32_t cnt = __popc(m);
-      uint32_t incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-      }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      uint32_t pos = incl - cnt;
-      while (m) {
-        const uint32_t i = __ffs(m) - 1;
-        m &= m - 1;
-        S.Q[pos++] = (uint16_t)((lane << 5) | i);
+        for (int b = 0; b < 7; ++b) {
+          uint32_t m = Bm[b];
+          while (m) {
+            const uint32_t i = __ffs(m) - 1;
+            m &= m - 1;
+            S.Q[pos++] = (uint16_t)((lane << 8) | (b << 5) | i);
+          }
+        }
       }
       __syncwarp();
-      for (uint32_t k = lane; k < total; k += 32) {
+      const uint32_t round_n = round_end - done;
+      for (uint32_t k = lane; k < round_n; k += 32) {
         const uint32_t e = S.Q[k];
-        const uint32_t owner = e >> 5, i = e & 31u;
+        const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
         const uint32_t v = S.v0[owner] + i;
-        const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | (uint32_t)b}, k0, k1);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int d = 4 * b + j;
-          if (d >= 26) continue;
-          if (!((S.V[owner][d] >> i) & 1u)) continue;
-          ++my_live;
-          const int cls = dir_cls(d);
-          const uint32_t thr = cls == 0 ? tm[0] : (cls == 1 ? tm[1] : tm[2]);
-          if (u4_word(rnd, j) > thr) continue;
+        const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
+        const uint32_t d0 = 4u * b;
+        uint32_t vb = (S.V[owner][d0] >> i) & 1u;
+        vb |= ((S.V[owner][d0 + 1] >> i) & 1u) << 1;
+        if (b < 6) {
+          vb |= ((S.V[owner][d0 + 2] >> i) & 1u) << 2;
+          vb |= ((S.V[owner][d0 + 3] >> i) & 1u) << 3;
+        }
+        my_live += __popc(vb);
+        uint32_t win = 0;
+        win |= (rnd.x <= s_thr[d0]) ? 1u : 0u;
+        win |= (rnd.y <= s_thr[d0 + 1]) ? 2u : 0u;
+        win |= (rnd.z <= s_thr[d0 + 2]) ? 4u : 0u;
+        win |= (rnd.w <= s_thr[d0 + 3]) ? 8u : 0u;
+        win &= vb;
+        while (win) {
+          const uint32_t j = __ffs(win) - 1;
+          win &= win - 1;
+          const int d = (int)(d0 + j);
           const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
           const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
           const size_t wq = (size_t)rq * g.W + (xx >> 5);
@@ -702,7 +726,8 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
           }
         }
       }
-      __syncwarp();  // S.Q is refilled for the next block
+      __syncwarp();  // S.Q is refilled by the next round
+      done = round_end;
     }
   }
   const uint32_t wc = __reduce_add_sync(0xffffffffu, my_claimed);
@@ -849,7 +874,7 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
   QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.front, b.grid, b.aux, b.st,
-              k0, k1);
+              make_philox_keys((uint64_t)k1 << 32 | k0));
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
   TrimPolicy tp{g, b.st, b.grid, b.aux};
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
