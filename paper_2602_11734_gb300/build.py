@@ -52,15 +52,21 @@ def common_flags(extra=()):
             "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), *extra]
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          defines=(), out: str | None = None) -> str:
+    """Compile libqsgs.so; ``defines`` are -D macros of tuning knobs, ``out``
+    an alternative output path (both imply a fresh build)."""
+    lib_path = out or LIB
+    if not force and not defines and out is None and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = os.path.join(os.path.dirname(lib_path), "obj") if out else BUILD
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra += [f"-D{d}" for d in defines]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *common_flags(extra), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -72,14 +78,21 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = [cc, "-gencode", GENCODE, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--ptxas", action="store_true")
+    ap.add_argument("-D", dest="defines", action="append", default=[])
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    print(build(force=a.force, verbose=True, ptxas_info=a.ptxas, defines=a.defines, out=a.out))

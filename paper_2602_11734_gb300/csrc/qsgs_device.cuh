@@ -214,7 +214,6 @@ struct alignas(256) RunState {
   unsigned long long claimed;    // |New_t| of this step (before the trim)
   unsigned long long live;       // attempts with a positive threshold
   unsigned long long sum_front;  // sum over steps of |A_t| (statistics)
-  unsigned long long trim_keep;  // voxels of New_t kept by the final trim
   unsigned long long front_n;    // |A_t| (front voxels)
   unsigned long long adj_n;      // spacing: total earlier-conflict entries
   uint32_t front_words;          // entries of the front word list
@@ -225,7 +224,6 @@ struct alignas(256) RunState {
   uint32_t step_limit;           // pause point of the current call
   int32_t status;                // kRunning or a QSGS_* status
   uint32_t active;               // this step runs
-  uint32_t trim;                 // this step needs the exact-target trim
   uint32_t error;                // kErr* bits
   uint32_t undecided;            // spacing: candidates not yet decided
   uint32_t scan_epoch;           // look-back scan launch counter

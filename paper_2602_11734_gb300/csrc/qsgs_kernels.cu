@@ -46,7 +46,6 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->claimed = 0;
   st->live = 0;
   st->sum_front = 0;
-  st->trim_keep = 0;
   st->front_n = 0;
   st->front_words = 0;
   st->cand_n = 0;
@@ -56,7 +55,6 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->step_limit = 0xFFFFFFFFu;
   st->status = kRunning;
   st->active = 1;
-  st->trim = 0;
   st->error = 0;
   st->undecided = 0;
 }
@@ -72,13 +70,13 @@ __global__ void k_step_begin(RunState* st) {
   for (int k = 0; k < 3; ++k) st->thr[k] = eq1_threshold(st->t_ref[k], st->nt, st->solid);
   st->claimed = 0;
   st->live = 0;
-  st->trim = 0;
   st->active = 1;
 }
 
-// After the growth kernel: a step without a single attempt of positive
-// probability is a fixed point (stalled, not counted); otherwise count the
-// claims, arm the exact-target trim if they overshoot, advance t.
+// After the growth kernel and the claim scan: a step without a single
+// attempt of positive probability is a fixed point (stalled, not counted);
+// otherwise add the claims -- already cut to the target by the claim scan --
+// and advance t.
 __global__ void k_step_end(RunState* st) {
   if (!st->active) return;
   if (st->live == 0) {
@@ -89,13 +87,7 @@ __global__ void k_step_end(RunState* st) {
   st->sum_front += st->front_n;
   st->front_n = 0;  // recounted by the front rebuild that follows
   const unsigned long long c = st->solid, k = st->claimed;
-  if (c + k > st->nt) {
-    st->trim = 1;
-    st->trim_keep = st->nt - c;
-    st->solid = st->nt;
-  } else {
-    st->solid = c + k;
-  }
+  st->solid = c + k > st->nt ? st->nt : c + k;
   st->t += 1;
 }
 
@@ -239,9 +231,11 @@ struct FrontPolicy {
   __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
 };
 
-// Exact target: keep the trim_keep lowest-index voxels claimed in this step
-// (the claim grid, in ascending order), clear the others from the grid.
-struct TrimPolicy {
+// The claims of a step (the claim grid holds exactly New_t: every success
+// targets a voxel that was void when the step began).  Counts |New_t| and
+// applies the exact-target rule: of New_t in ascending order only the first
+// Nt - c_t stay solid; the rest are cleared from the grid again.
+struct ClaimPolicy {
   Geom g;
   RunState* st;
   uint32_t* grid;
@@ -249,23 +243,24 @@ struct TrimPolicy {
   using Item = WordItem;
   __device__ uint32_t side(const Item&) const { return 0; }
   __device__ unsigned long long* side_sum() const { return nullptr; }
-  __device__ bool active() const { return st->active && st->trim; }
+  __device__ bool active() const { return st->active; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w) const { return Item{w, aux[w]}; }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
   __device__ void emit(const Item& it, unsigned long long off) const {
-    const unsigned long long keep = st->trim_keep;
+    const unsigned long long keep = st->nt - st->solid;
+    if (off + __popc(it.bits) <= keep) return;
     uint32_t drop = it.bits;
     if (off < keep) {
-      uint32_t k = (uint32_t)min((unsigned long long)__popc(it.bits), keep - off);
+      uint32_t k = (uint32_t)(keep - off);
       uint32_t b = it.bits;
-      while (k--) b &= b - 1;  // b = the bits beyond the first k
+      while (k--) b &= b - 1;  // b = the bits beyond the first (keep - off)
       drop = b;
     }
-    if (drop) grid[it.w] &= ~drop;
+    grid[it.w] &= ~drop;
   }
-  __device__ void total(unsigned long long) const {}
+  __device__ void total(unsigned long long n) const { st->claimed = n; }
 };
 
 // Seeds: the accepted candidates in ascending order, capped at Nt, written
@@ -559,10 +554,13 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
+#ifndef QSGS_GROW_MIN_BLOCKS
+#define QSGS_GROW_MIN_BLOCKS 3  // resident blocks per SM the register budget aims for
+#endif
 constexpr int kGrowQueue = 1024;  // pairs per drain round; a word has at most 7 * 32
 
 struct GrowWarpSmem {
-  uint32_t V[32][27];        // per lane word: V_d, d = 0..25 (odd pitch: no bank conflicts)
+  uint4 V[32][7];            // per lane word, per block b: V_{4b..4b+3}
   uint16_t Q[kGrowQueue];    // queued pairs: lane << 8 | block << 5 | bit
   uint32_t r[32], xw[32], v0[32];
 };
@@ -579,7 +577,7 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
 template <int DZ, int DY>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, uint32_t y,
                                           uint32_t z, uint32_t r, uint32_t xw, uint32_t src,
-                                          uint32_t live_dirs, uint32_t (&V)[27], uint32_t (&Bm)[7]) {
+                                          uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7]) {
   const int yy = (int)y + DY, zz = (int)z + DZ;
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
@@ -606,11 +604,11 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, u
   Bm[dp >> 2] |= V[dp];
 }
 
-__global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* __restrict__ front,
+__global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geom g, const uint2* __restrict__ front,
                                                           uint32_t* grid, uint32_t* aux,
                                                           RunState* st, const PhiloxKeys keys) {
   __shared__ GrowWarpSmem smem[kGrowWarps];
-  __shared__ uint32_t s_thr[28];  // per direction: T - 1 (draw succeeds iff r <= it)
+  __shared__ uint4 s_thr[7];  // per block, per direction: T - 1 (success iff r <= it)
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
@@ -623,13 +621,13 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
   if (threadIdx.x < 28) {
     const int d = threadIdx.x;
     const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
-    s_thr[d] = T ? (uint32_t)(T - 1) : 0u;  // dead directions never reach the test
+    reinterpret_cast<uint32_t*>(s_thr)[d] = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
   }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  uint32_t my_claimed = 0, my_live = 0;
+  uint32_t my_live = 0;
 
   for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
     // Phase 1: masks of this lane's word.
@@ -642,7 +640,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
       const uint32_t xw = w - r * g.W;
       const uint32_t z = fast_div(r, g.div_ny);
       const uint32_t y = r - z * g.ny;
-      uint32_t V[27];
+      uint32_t V[28];
       row_masks<-1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
       row_masks<-1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
       row_masks<-1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
@@ -652,8 +650,10 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
       row_masks<1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
       row_masks<1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
       row_masks<1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      V[26] = 0;
+      V[27] = 0;
 #pragma unroll
-      for (int d = 0; d < 26; ++d) S.V[lane][d] = V[d];
+      for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
       S.r[lane] = r;
       S.xw[lane] = xw;
       S.v0[lane] = r * g.nx + xw * 32u;
@@ -697,45 +697,33 @@ __global__ void __launch_bounds__(kGrowThreads, 3) k_grow(Geom g, const uint2* _
         const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
         const uint32_t v = S.v0[owner] + i;
         const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
-        const uint32_t d0 = 4u * b;
-        uint32_t vb = (S.V[owner][d0] >> i) & 1u;
-        vb |= ((S.V[owner][d0 + 1] >> i) & 1u) << 1;
-        if (b < 6) {
-          vb |= ((S.V[owner][d0 + 2] >> i) & 1u) << 2;
-          vb |= ((S.V[owner][d0 + 3] >> i) & 1u) << 3;
-        }
+        const uint4 vm = S.V[owner][b];
+        const uint32_t vb = ((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
+                            (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3);
         my_live += __popc(vb);
-        uint32_t win = 0;
-        win |= (rnd.x <= s_thr[d0]) ? 1u : 0u;
-        win |= (rnd.y <= s_thr[d0 + 1]) ? 2u : 0u;
-        win |= (rnd.z <= s_thr[d0 + 2]) ? 4u : 0u;
-        win |= (rnd.w <= s_thr[d0 + 3]) ? 8u : 0u;
+        const uint4 th = s_thr[b];
+        uint32_t win = (rnd.x <= th.x ? 1u : 0u) | (rnd.y <= th.y ? 2u : 0u) |
+                       (rnd.z <= th.z ? 4u : 0u) | (rnd.w <= th.w ? 8u : 0u);
         win &= vb;
         while (win) {
           const uint32_t j = __ffs(win) - 1;
           win &= win - 1;
-          const int d = (int)(d0 + j);
+          const int d = (int)(4u * b + j);
           const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
           const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
           const size_t wq = (size_t)rq * g.W + (xx >> 5);
           const uint32_t bit = 1u << (xx & 31);
-          const uint32_t old = atomicOr(grid + wq, bit);
-          if (!(old & bit)) {
-            ++my_claimed;
-            atomicOr(aux + wq, bit);
-          }
+          // Fire-and-forget: the claim grid collects New_t; nobody waits.
+          atomicOr(grid + wq, bit);
+          atomicOr(aux + wq, bit);
         }
       }
       __syncwarp();  // S.Q is refilled by the next round
       done = round_end;
     }
   }
-  const uint32_t wc = __reduce_add_sync(0xffffffffu, my_claimed);
   const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
-  if (lane == 0) {
-    if (wc) atomicAdd(&st->claimed, (unsigned long long)wc);
-    if (wl) atomicAdd(&st->live, (unsigned long long)wl);
-  }
+  if (lane == 0 && wl) atomicAdd(&st->live, (unsigned long long)wl);
 }
 
 // ---------------------------------------------------------------------------
@@ -875,10 +863,10 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
   QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.front, b.grid, b.aux, b.st,
               make_philox_keys((uint64_t)k1 << 32 | k0));
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
-  TrimPolicy tp{g, b.st, b.grid, b.aux};
-  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
+  ClaimPolicy cp{g, b.st, b.grid, b.aux};
+  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<ClaimPolicy>, scan_grid(g.nwords), kScanThreads, cp,
               ctl);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
   FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, 0u};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
               fp, ctl);

@@ -17,7 +17,8 @@ import threading
 from dataclasses import dataclass
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "_build", "libqsgs.so")
+# QSGS_LIBRARY overrides the library path (e.g. a build with other tuning).
+LIB_PATH = os.environ.get("QSGS_LIBRARY") or os.path.join(PKG, "_build", "libqsgs.so")
 
 QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING = 0, 1, 2, 3
 QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_CUDA = -1, -2, -3
