@@ -79,7 +79,7 @@ Layout make_layout(const qsgs_params* p) {
   L.state = off; off = align_up(off + sizeof(RunState));
   L.scan_status = off; off = align_up(off + L.ntiles * sizeof(unsigned long long));
   L.grid = off; off = align_up(off + nwords * 4);
-  L.aux = off; off = align_up(off + nwords * 4);
+  L.aux = off; off = align_up(off + 2 * nwords * 4);  // claim grids of even / odd steps
   // Candidates (u32 each, at most N), then the front word list ({word,
   // bits} pairs, at most nwords).
   const uint64_t list_bytes = n * 4 > nwords * 8 ? n * 4 : nwords * 8;
@@ -118,6 +118,14 @@ struct qsgs_handle {
   bool seeded;
   cudaError_t last_cuda;
   Tracer tracer;
+  // Whole-run graph: while (active) { grow; front; control } then the
+  // exact-target epilogue.  Built on first use; direct launches when the
+  // profiler is on, the stream is the legacy default stream, or building
+  // the graph failed.
+  cudaGraph_t graph;
+  cudaGraphExec_t graph_exec;
+  bool graph_tried;
+  uint32_t iters_seen;
 };
 
 namespace {
@@ -154,6 +162,53 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
 
 StepBuffers step_buffers(const qsgs_handle* h) {
   return StepBuffers{h->st, h->scan_status, h->grid, h->aux, reinterpret_cast<uint2*>(h->list)};
+}
+
+void destroy_graph(qsgs_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+}
+
+// Captures the whole growth loop of this handle into one graph: a while
+// node whose body is one step (its last kernel sets the loop condition),
+// followed by the exact-target epilogue.  Kernel arguments are fixed per
+// handle, so the graph is built once and relaunched by every call.
+cudaError_t build_graph(qsgs_handle* h) {
+  cudaError_t e = cudaGraphCreate(&h->graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle cond;
+  e = cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  e = cudaGraphAddNode(&loop, h->graph, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const StepBuffers b = step_buffers(h);
+  Tracer capture_tracer;  // launches inside the graph are counted from iters
+  e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, h->grow_blocks, h->stream,
+                               capture_tracer, cond, 1);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(h->stream, &captured);
+  if (le != cudaSuccess) return le;
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(h->stream, h->graph, &loop, nullptr, 1,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  le = launch_epilogue(h->g, b, kSpinLimit, h->stream, capture_tracer);
+  e = cudaStreamEndCapture(h->stream, &captured);
+  if (le != cudaSuccess) return le;
+  if (e != cudaSuccess) return e;
+  return cudaGraphInstantiate(&h->graph_exec, h->graph, 0);
 }
 
 }  // namespace
@@ -230,6 +285,10 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->grow_blocks = default_grow_blocks();
   h->seeded = false;
   h->last_cuda = cudaSuccess;
+  h->graph = nullptr;
+  h->graph_exec = nullptr;
+  h->graph_tried = false;
+  h->iters_seen = 0;
   // The scan status words must start with flag 0; the run state is set by
   // qsgs_seed.
   cudaError_t e = cudaMemsetAsync(h->ws, 0, L.grid, h->stream);
@@ -245,7 +304,7 @@ int qsgs_seed(qsgs_handle* h) {
   if (!h) return QSGS_ERR_INVALID;
   const size_t grids = (size_t)h->g.nwords * 4;
   cudaError_t e = cudaMemsetAsync(h->grid, 0, grids, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, grids, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   StateInit init{};
   init.nt = h->ints.nt;
@@ -261,6 +320,7 @@ int qsgs_seed(qsgs_handle* h) {
   e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, h->stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->seeded = true;
+  h->iters_seen = 0;
   return QSGS_OK;
 }
 
@@ -271,16 +331,38 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
   if (e != cudaSuccess) return cuda_fail(h, e);
   const StepBuffers b = step_buffers(h);
   RunState s{};
-  for (;;) {
-    for (uint32_t k = 0; k < kStepsPerSync; ++k) {
-      e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, h->grow_blocks, h->stream, h->tracer);
-      if (e != cudaSuccess) return cuda_fail(h, e);
+  if (!h->tracer.enabled() && h->stream != nullptr && !h->graph_tried) {
+    h->graph_tried = true;
+    if (build_graph(h) != cudaSuccess) {
+      destroy_graph(h);
+      (void)cudaGetLastError();
     }
-    e = launch_step_begin(h->st, h->stream, h->tracer);
+  }
+  if (!h->tracer.enabled() && h->graph_exec) {
+    e = cudaGraphLaunch(h->graph_exec, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     const int rc = read_state(h, &s);
     if (rc != QSGS_OK) return rc;
-    if (s.status != kRunning || !s.active) break;
+    // Count the kernels the graph ran: three per loop iteration, three in
+    // the epilogue.
+    h->tracer.launches += 3ull * (s.iters - h->iters_seen) + 3ull;
+    h->iters_seen = s.iters;
+  } else {
+    for (;;) {
+      for (uint32_t k = 0; k < kStepsPerSync; ++k) {
+        e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, h->grow_blocks, h->stream, h->tracer,
+                        (cudaGraphConditionalHandle)0, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+      }
+      const int rc = read_state(h, &s);
+      if (rc != QSGS_OK) return rc;
+      if (s.status != kRunning || !s.active) break;
+    }
+    e = launch_epilogue(h->g, b, kSpinLimit, h->stream, h->tracer);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    const int rc = read_state(h, &s);
+    if (rc != QSGS_OK) return rc;
+    h->iters_seen = s.iters;
   }
   fill_stats(h, s, out);
   return s.status == kRunning ? QSGS_RUNNING : s.status;
@@ -349,6 +431,10 @@ int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries) {
   return kNumClasses;
 }
 
-void qsgs_destroy(qsgs_handle* h) { delete h; }
+void qsgs_destroy(qsgs_handle* h) {
+  if (!h) return;
+  destroy_graph(h);
+  delete h;
+}
 
 }  // extern "C"

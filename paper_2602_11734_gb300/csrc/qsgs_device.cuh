@@ -211,11 +211,13 @@ struct alignas(256) RunState {
   unsigned long long thr[3];     // Eq. 1 thresholds for this step
   unsigned long long t_ref[3];   // floor(G_ref 2^32) per class
   unsigned long long t_seed;     // floor(cd 2^32)
-  unsigned long long claimed;    // |New_t| of this step (before the trim)
+  unsigned long long claimed;    // |New_t|, counted by the front rebuild
   unsigned long long live;       // attempts with a positive threshold
   unsigned long long sum_front;  // sum over steps of |A_t| (statistics)
   unsigned long long front_n;    // |A_t| (front voxels)
+  unsigned long long front_acc;  // |A_{t+1}| being counted by the rebuild
   unsigned long long adj_n;      // spacing: total earlier-conflict entries
+  unsigned long long trim_keep;  // exact target: claims of the last step kept
   uint32_t front_words;          // entries of the front word list
   uint32_t cand_n;               // Bernoulli candidates
   uint32_t acc_n;                // seeds placed
@@ -223,9 +225,11 @@ struct alignas(256) RunState {
   uint32_t max_steps;            // total step limit (0xFFFFFFFF = none)
   uint32_t step_limit;           // pause point of the current call
   int32_t status;                // kRunning or a QSGS_* status
-  uint32_t active;               // this step runs
+  uint32_t active;               // the next step runs
+  uint32_t trim_pending;         // the last step overshot Nt: trim before fetch
+  uint32_t trim_parity;          // claim grid of that step
   uint32_t error;                // kErr* bits
-  uint32_t undecided;            // spacing: candidates not yet decided
+  uint32_t iters;                // step-control launches (closed/opened steps)
   uint32_t scan_epoch;           // look-back scan launch counter
   uint32_t scan_tile;            // look-back scan tile dispenser
   uint32_t scan_done;            // look-back scan blocks finished

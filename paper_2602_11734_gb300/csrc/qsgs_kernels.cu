@@ -47,6 +47,9 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->live = 0;
   st->sum_front = 0;
   st->front_n = 0;
+  st->front_acc = 0;
+  st->adj_n = 0;
+  st->trim_keep = 0;
   st->front_words = 0;
   st->cand_n = 0;
   st->acc_n = 0;
@@ -54,41 +57,58 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->max_steps = init.max_steps;
   st->step_limit = 0xFFFFFFFFu;
   st->status = kRunning;
-  st->active = 1;
+  st->active = 0;
+  st->trim_pending = 0;
+  st->trim_parity = 0;
   st->error = 0;
-  st->undecided = 0;
+  st->iters = 0;
 }
 
-// Exits before a step, in order: target reached, step limit, pause point of
-// the current call.  Idempotent, so it can close a chain of captured steps.
-__global__ void k_step_begin(RunState* st) {
+// Decides whether the next step runs.  Exits, tested in order: target
+// reached, step limit, pause point of the current call.  Sets the Eq. 1
+// thresholds of the step from the solid count before it.
+__device__ void begin_step(RunState* st) {
   st->active = 0;
   if (st->status != kRunning) return;
   if (st->solid >= st->nt) { st->status = kStatusDone; return; }
   if (st->t >= st->max_steps) { st->status = kStatusMaxSteps; return; }
   if (st->t >= st->step_limit) return;
   for (int k = 0; k < 3; ++k) st->thr[k] = eq1_threshold(st->t_ref[k], st->nt, st->solid);
-  st->claimed = 0;
-  st->live = 0;
   st->active = 1;
 }
 
-// After the growth kernel and the claim scan: a step without a single
-// attempt of positive probability is a fixed point (stalled, not counted);
-// otherwise add the claims -- already cut to the target by the claim scan --
-// and advance t.
-__global__ void k_step_end(RunState* st) {
-  if (!st->active) return;
-  if (st->live == 0) {
-    st->status = kStatusStalled;
-    st->active = 0;
-    return;
+// Closes the step that just ran (if one did) and opens the next.  A step
+// without a single attempt of positive probability is a fixed point:
+// stalled, not counted.  Otherwise the claims counted by the front rebuild
+// are added; if they overshoot Nt the solid count is capped and the
+// exact-target trim is left pending (the run ends with this step).  With a
+// graph conditional handle, also tells the enclosing while loop whether to
+// go on.
+__global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  if (st->active) {
+    if (st->live == 0) {
+      st->status = kStatusStalled;
+    } else {
+      st->sum_front += st->front_n;
+      st->front_n = st->front_acc;
+      const unsigned long long c = st->solid, k = st->claimed;
+      if (c + k > st->nt) {
+        st->trim_pending = 1;
+        st->trim_parity = st->t & 1u;
+        st->trim_keep = st->nt - c;
+        st->solid = st->nt;
+      } else {
+        st->solid = c + k;
+      }
+      st->t += 1;
+    }
   }
-  st->sum_front += st->front_n;
-  st->front_n = 0;  // recounted by the front rebuild that follows
-  const unsigned long long c = st->solid, k = st->claimed;
-  st->solid = c + k > st->nt ? st->nt : c + k;
-  st->t += 1;
+  st->front_acc = 0;
+  st->claimed = 0;
+  st->live = 0;
+  st->iters += 1;
+  begin_step(st);
+  if (use_cond) cudaGraphSetConditional(cond, st->active ? 1u : 0u);
 }
 
 __global__ void k_set_step_limit(RunState* st, uint32_t extra) {
@@ -98,7 +118,10 @@ __global__ void k_set_step_limit(RunState* st, uint32_t extra) {
     unsigned long long lim = (unsigned long long)st->t + extra;
     st->step_limit = lim > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)lim;
   }
+  begin_step(st);
 }
+
+__global__ void k_trim_done(RunState* st) { st->trim_pending = 0; }
 
 // ---------------------------------------------------------------------------
 // Shared helpers.
@@ -147,8 +170,9 @@ __device__ __forceinline__ uint32_t front_word(const Geom& g, const uint32_t* gr
 // Scan policies.
 // ---------------------------------------------------------------------------
 struct WordItem {
-  uint32_t w;     // word index
-  uint32_t bits;  // the word's set bits
+  uint32_t w;      // word index
+  uint32_t bits;   // the word's set bits
+  uint32_t extra;  // policy-specific second word
 };
 
 // Emit the voxel index of every set bit of a word, ascending.
@@ -173,8 +197,10 @@ struct SeedCompactPolicy {
   uint32_t* cand;
   uint32_t k0, k1;
   using Item = WordItem;
-  __device__ uint32_t side(const Item&) const { return 0; }
-  __device__ unsigned long long* side_sum() const { return nullptr; }
+  static constexpr bool kBatched = false;
+  __device__ uint32_t side(const Item&, int) const { return 0; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -198,7 +224,7 @@ struct SeedCompactPolicy {
         if ((unsigned long long)u4_word(blk, (int)(v & 3)) < t_seed) bits |= 1u << i;
       }
     }
-    return Item{w, bits};
+    return Item{w, bits, 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
   __device__ void emit(const Item& it, unsigned long long off) const { emit_word_bits(g, it, cand, off); }
@@ -207,49 +233,137 @@ struct SeedCompactPolicy {
 
 // Sec. 2.3 step 2 / step 4: the active front rebuilt from the grid, as an
 // ascending list of {word index, front bits} -- one entry per 32-voxel row
-// word that holds at least one front voxel.  The front voxels are counted
-// into front_n.  Also clears the claim grid for the next step.
+// word that holds at least one front voxel.
+//
+// Why a rebuild from the grid equals prune(A_t U New_t): a voxel solid after
+// step t with a void neighbour either is in New_t or was solid before with
+// that neighbour already void (voids only shrink), hence in A_t.  So the
+// front is a function of the grid alone, and one order-preserving scan over
+// all grid words yields it sorted, with no sort of New_t.
+//
+// Modes: kFrontInitial (after seeding: counts into front_n), kFrontStep
+// (after a growth step: counts the front into front_acc and the step's
+// claims into claimed, and clears the other claim grid for the next step),
+// kFrontFinal (after the exact-target trim: recounts front_n).
+enum : int { kFrontInitial = 0, kFrontStep = 1, kFrontFinal = 2 };
+
 struct FrontPolicy {
   Geom g;
   RunState* st;
   const uint32_t* grid;
-  uint32_t* aux;
+  uint32_t* aux;  // two claim grids of nwords words each
   uint2* front;
-  uint32_t always;  // 1: run even when no step is active (initial front)
+  int mode;
   using Item = WordItem;
-  __device__ bool active() const { return always || st->active; }
+  static constexpr bool kBatched = true;
+  __device__ bool active() const {
+    return mode == kFrontInitial ? true : (mode == kFrontStep ? st->active != 0 : st->trim_pending != 0);
+  }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  __device__ Item load(uint32_t w) const {
-    aux[w] = 0;
-    return Item{w, front_word(g, grid, w)};
+  __device__ Item load(uint32_t w) const { return Item{w, front_word(g, grid, w), 0u}; }
+  // The front bits of words first .. first+n-1.  Each neighbour row is read
+  // as one window of n + 2 consecutive words (the layout puts the rows of
+  // consecutive words at a fixed offset), instead of 3 loads per word.
+  __device__ void load_run(uint32_t first, uint32_t n, Item (&it)[kScanItems]) const {
+    uint32_t r = fast_div(first, g.div_W);
+    uint32_t xw0 = first - r * g.W;
+    uint32_t z0 = fast_div(r, g.div_ny);
+    uint32_t y0 = r - z0 * g.ny;
+    uint32_t self[kScanItems], solid_all[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      self[k] = (uint32_t)k < n ? grid[first + k] : 0u;
+      solid_all[k] = 0xFFFFFFFFu;
+    }
+    const int64_t plane = (int64_t)g.W * g.ny;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int64_t off = (int64_t)dy * g.W + (int64_t)dz * plane;
+        uint32_t win[kScanItems + 2];
+#pragma unroll
+        for (int k = 0; k < kScanItems + 2; ++k) {
+          const int64_t q = (int64_t)first + off + k - 1;
+          win[k] = (q >= 0 && q < (int64_t)g.nwords && (uint32_t)k <= n + 1) ? grid[q] : 0u;
+        }
+        uint32_t xw = xw0, y = y0, z = z0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+          const int yy = (int)y + dy, zz = (int)z + dz;
+          if ((uint32_t)k < n && yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
+            uint32_t c = win[k + 1];
+            if (xw == g.W - 1) c |= g.pad_mask;
+            const uint32_t l = xw > 0 ? win[k] : 0xFFFFFFFFu;
+            uint32_t rr = 0xFFFFFFFFu;
+            if (xw + 1 < g.W) {
+              rr = win[k + 2];
+              if (xw + 1 == g.W - 1) rr |= g.pad_mask;
+            }
+            uint32_t a = ((c << 1) | (l >> 31)) & ((c >> 1) | (rr << 31));
+            if (dy != 0 || dz != 0) a &= c;
+            solid_all[k] &= a;
+          }
+          if (++xw == g.W) {
+            xw = 0;
+            if (++y == g.ny) { y = 0; ++z; }
+          }
+        }
+      }
+    }
+    const uint32_t par = st->t & 1u;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if ((uint32_t)k >= n) break;
+      const uint32_t w = first + k;
+      uint32_t claims = 0;
+      if (mode == kFrontStep) {
+        claims = aux[(size_t)par * g.nwords + w];
+        aux[(size_t)(par ^ 1u) * g.nwords + w] = 0;
+      }
+      it[k] = Item{w, self[k] & ~solid_all[k], claims};
+    }
   }
   __device__ uint32_t count(const Item& it) const { return it.bits ? 1u : 0u; }
-  __device__ uint32_t side(const Item& it) const { return __popc(it.bits); }
-  __device__ unsigned long long* side_sum() const { return &st->front_n; }
-  __device__ void emit(const Item& it, unsigned long long off) const { front[off] = make_uint2(it.w, it.bits); }
-  __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
+  __device__ uint32_t side(const Item& it, int k) const {
+    return k == 0 ? __popc(it.bits) : __popc(it.extra);
+  }
+  __device__ unsigned long long* side_sum(int k) const {
+    if (k == 0) return mode == kFrontStep ? &st->front_acc : &st->front_n;
+    return mode == kFrontStep ? &st->claimed : nullptr;
+  }
+  __device__ void emit(const Item& it, unsigned long long off) const {
+    if (mode != kFrontFinal) front[off] = make_uint2(it.w, it.bits);
+  }
+  __device__ void total(unsigned long long n) const {
+    if (mode != kFrontFinal) st->front_words = (uint32_t)n;
+  }
 };
 
-// The claims of a step (the claim grid holds exactly New_t: every success
-// targets a voxel that was void when the step began).  Counts |New_t| and
-// applies the exact-target rule: of New_t in ascending order only the first
-// Nt - c_t stay solid; the rest are cleared from the grid again.
-struct ClaimPolicy {
+// The exact-target trim, once, after the step that overshot Nt.  The claim
+// grid of that step holds exactly New_t (every success targets a voxel that
+// was void when the step began); of New_t in ascending order only the first
+// trim_keep voxels stay solid, the rest are cleared from the grid again.
+struct TrimPolicy {
   Geom g;
   RunState* st;
   uint32_t* grid;
-  const uint32_t* aux;
+  const uint32_t* aux;  // two claim grids
   using Item = WordItem;
-  __device__ uint32_t side(const Item&) const { return 0; }
-  __device__ unsigned long long* side_sum() const { return nullptr; }
-  __device__ bool active() const { return st->active; }
+  static constexpr bool kBatched = false;
+  __device__ uint32_t side(const Item&, int) const { return 0; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
+  __device__ bool active() const { return st->trim_pending != 0; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  __device__ Item load(uint32_t w) const { return Item{w, aux[w]}; }
+  __device__ Item load(uint32_t w) const {
+    return Item{w, aux[(size_t)st->trim_parity * g.nwords + w], 0u};
+  }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
   __device__ void emit(const Item& it, unsigned long long off) const {
-    const unsigned long long keep = st->nt - st->solid;
+    const unsigned long long keep = st->trim_keep;
     if (off + __popc(it.bits) <= keep) return;
     uint32_t drop = it.bits;
     if (off < keep) {
@@ -260,7 +374,8 @@ struct ClaimPolicy {
     }
     grid[it.w] &= ~drop;
   }
-  __device__ void total(unsigned long long n) const { st->claimed = n; }
+  // front_n is recounted by the final front pass that follows.
+  __device__ void total(unsigned long long) const { st->front_n = 0; }
 };
 
 // Seeds: the accepted candidates in ascending order, capped at Nt, written
@@ -275,8 +390,10 @@ struct AcceptPolicy {
     uint32_t v;
     uint32_t ok;
   };
-  __device__ uint32_t side(const Item&) const { return 0; }
-  __device__ unsigned long long* side_sum() const { return nullptr; }
+  static constexpr bool kBatched = false;
+  __device__ uint32_t side(const Item&, int) const { return 0; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return st->cand_n; }
@@ -307,8 +424,10 @@ struct CellOffsetPolicy {
   struct Item {
     uint32_t i, c;
   };
-  __device__ uint32_t side(const Item&) const { return 0; }
-  __device__ unsigned long long* side_sum() const { return nullptr; }
+  static constexpr bool kBatched = false;
+  __device__ uint32_t side(const Item&, int) const { return 0; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return ncells; }
@@ -415,8 +534,10 @@ struct ConflictOffsetPolicy {
   struct Item {
     uint32_t i, c;
   };
-  __device__ uint32_t side(const Item&) const { return 0; }
-  __device__ unsigned long long* side_sum() const { return nullptr; }
+  static constexpr bool kBatched = false;
+  __device__ uint32_t side(const Item&, int) const { return 0; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return st->cand_n; }
@@ -624,6 +745,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
     reinterpret_cast<uint32_t*>(s_thr)[d] = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
   }
   __syncthreads();
+  uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
@@ -715,7 +837,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
           const uint32_t bit = 1u << (xx & 31);
           // Fire-and-forget: the claim grid collects New_t; nobody waits.
           atomicOr(grid + wq, bit);
-          atomicOr(aux + wq, bit);
+          atomicOr(claims + wq, bit);
         }
       }
       __syncwarp();  // S.Q is refilled by the next round
@@ -850,31 +972,36 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
               ctl);
   // Initial front (Sec. 2.3 step 2) replaces the candidate list.
-  FrontPolicy fp{g, b.st, b.grid, b.aux, reinterpret_cast<uint2*>(b.list), 1u};
+  FrontPolicy fp{g, b.st, b.grid, b.aux, reinterpret_cast<uint2*>(b.list), kFrontInitial};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
               fp, ctl);
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, (cudaGraphConditionalHandle)0, 0);
   return cudaSuccess;
 }
 
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
+                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
+                        cudaGraphConditionalHandle cond, int use_cond) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, b.st);
   QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.front, b.grid, b.aux, b.st,
               make_philox_keys((uint64_t)k1 << 32 | k0));
-  ClaimPolicy cp{g, b.st, b.grid, b.aux};
-  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<ClaimPolicy>, scan_grid(g.nwords), kScanThreads, cp,
-              ctl);
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_end, 1, 1, b.st);
-  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, 0u};
+  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, kFrontStep};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
               fp, ctl);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);
   return cudaSuccess;
 }
 
-cudaError_t launch_step_begin(RunState* st, cudaStream_t s, Tracer& tr) {
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_begin, 1, 1, st);
+cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
+                            cudaStream_t s, Tracer& tr) {
+  ScanCtl ctl{b.st, b.scan_status, spin_limit};
+  TrimPolicy tp{g, b.st, b.grid, b.aux};
+  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
+              ctl);
+  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, kFrontFinal};
+  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
+              fp, ctl);
+  QSGS_LAUNCH(tr, kClsTrim, s, k_trim_done, 1, 1, b.st);
   return cudaSuccess;
 }
 

@@ -127,8 +127,8 @@ struct StepBuffers {
   RunState* st;
   unsigned long long* scan_status;
   uint32_t* grid;
-  uint32_t* aux;
-  uint2* front;  // {word index, front bits} list
+  uint32_t* aux;  // two claim grids (step parity)
+  uint2* front;   // {word index, front bits} list
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
@@ -137,9 +137,16 @@ uint32_t default_grow_blocks();
 cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr);
 cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, cudaStream_t s, Tracer& tr);
+// One growth step: k_grow, the front rebuild (which also counts the
+// step's claims) and the step control.  With use_cond, the step control
+// also sets the graph conditional `cond` (while-loop body).
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr);
-cudaError_t launch_step_begin(RunState* st, cudaStream_t s, Tracer& tr);
+                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
+                        cudaGraphConditionalHandle cond, int use_cond);
+// Exact-target trim and final front count; no-ops unless the last step
+// overshot Nt.
+cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
+                            cudaStream_t s, Tracer& tr);
 cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
 cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
                              Tracer& tr);

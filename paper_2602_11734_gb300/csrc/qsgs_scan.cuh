@@ -42,10 +42,14 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 //   uint32_t count(const Item&) const    -- outputs of the item
 //   void emit(const Item&, unsigned long long prefix) const
 //   void total(unsigned long long) const -- called once with the grand total
-//   uint32_t side(const Item&) const     -- a second per-item value, summed
-//   unsigned long long* side_sum() const --   into this counter (nullptr: none)
+//   uint32_t side(const Item&, int k) const     -- extra per-item values k = 0, 1,
+//   unsigned long long* side_sum(int k) const   --   summed into these counters
+//                                                   (nullptr: not summed)
+//   static constexpr bool kBatched              -- true: items are loaded by
+//   void load_run(uint32_t first, uint32_t n, Item (&it)[kScanItems]) const
+//                                                   (n consecutive valid items)
 template <class Policy>
-__global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, ScanCtl ctl) {
+__global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, ScanCtl ctl) {
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_prefix;
   __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -65,25 +69,36 @@ __global__ void __launch_bounds__(kScanThreads) k_lookback_scan(Policy pol, Scan
 
     typename Policy::Item it[kScanItems];
     uint32_t cnt[kScanItems];
-    uint32_t mine = 0, side = 0;
+    uint32_t mine = 0, side0 = 0, side1 = 0;
     const unsigned long long base =
         (unsigned long long)tile * kScanTile + (unsigned long long)threadIdx.x * kScanItems;
+    const uint32_t n_valid =
+        base >= n_items ? 0u : (uint32_t)min((unsigned long long)kScanItems, n_items - base);
+    if constexpr (Policy::kBatched) {
+      if (n_valid) pol.load_run((uint32_t)base, n_valid, it);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k)
+        if ((uint32_t)k < n_valid) it[k] = pol.load((uint32_t)(base + k));
+    }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      const unsigned long long i = base + k;
-      if (i < n_items) {
-        it[k] = pol.load((uint32_t)i);
+      cnt[k] = 0;
+      if ((uint32_t)k < n_valid) {
         cnt[k] = pol.count(it[k]);
-        side += pol.side(it[k]);
-      } else {
-        cnt[k] = 0;
+        side0 += pol.side(it[k], 0);
+        side1 += pol.side(it[k], 1);
       }
       mine += cnt[k];
     }
 
-    if (pol.side_sum() != nullptr) {
-      const uint32_t ws = __reduce_add_sync(0xffffffffu, side);
-      if (lane == 0 && ws) atomicAdd(pol.side_sum(), (unsigned long long)ws);
+    if (pol.side_sum(0) != nullptr) {
+      const uint32_t ws = __reduce_add_sync(0xffffffffu, side0);
+      if (lane == 0 && ws) atomicAdd(pol.side_sum(0), (unsigned long long)ws);
+    }
+    if (pol.side_sum(1) != nullptr) {
+      const uint32_t ws = __reduce_add_sync(0xffffffffu, side1);
+      if (lane == 0 && ws) atomicAdd(pol.side_sum(1), (unsigned long long)ws);
     }
 
     // Block-wide exclusive scan of the per-thread counts.

@@ -170,3 +170,50 @@ def test_batch_96_instances_golden(Q):
 def test_serve_small_golden(Q):
     for row in _golden("serve_small"):
         _check_golden_row(Q, row)
+
+
+def test_direct_launch_path_matches_graph_path(oracle, Q):
+    # The event profiler forces direct launches (no CUDA graph); both paths
+    # must give the oracle's grid.
+    p = dict(workloads.small_64(), nx=61, ny=47, nz=39, spacing_s=5, cd=0.006)
+    want = oracle.run(p)
+    g = Q.Generator(p)
+    try:
+        g.set_profiling(True)
+        g.seed()
+        st = g.grow()
+        prof = g.profile()
+        got = g.fetch().cpu().numpy()
+    finally:
+        g.close()
+    assert np.array_equal(got, want.phase)
+    assert (st.solid_count, st.steps, st.status) == (want.solid_count, want.steps, want.status)
+    assert prof["grow"][0] >= st.steps and prof["grow"][1] > 0
+
+
+def test_legacy_default_stream(oracle, Q):
+    class NullStream:
+        cuda_stream = 0
+    p = dict(workloads.small_64(), nx=33, ny=35, nz=37, spacing_s=2)
+    want = oracle.run(p)
+    g = Q.Generator(p, stream=NullStream())
+    try:
+        g.seed()
+        st = g.grow()
+        got = g.fetch().cpu().numpy()
+    finally:
+        g.close()
+    assert np.array_equal(got, want.phase)
+    assert st.steps == want.steps
+
+
+def test_launch_counter_grows_with_steps(Q):
+    p = dict(workloads.small_64(), nx=50, ny=50, nz=50)
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        before = g.query().launches
+        st = g.grow()
+        assert st.launches - before >= 3 * st.steps
+    finally:
+        g.close()
