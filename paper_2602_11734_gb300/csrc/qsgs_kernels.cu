@@ -262,68 +262,55 @@ struct FrontPolicy {
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w) const { return Item{w, front_word(g, grid, w), 0u}; }
-  // The front bits of words first .. first+n-1.  Each neighbour row is read
-  // as one window of n + 2 consecutive words (the layout puts the rows of
-  // consecutive words at a fixed offset), instead of 3 loads per word.
-  __device__ void load_run(uint32_t first, uint32_t n, Item (&it)[kScanItems]) const {
-    uint32_t r = fast_div(first, g.div_W);
-    uint32_t xw0 = first - r * g.W;
-    uint32_t z0 = fast_div(r, g.div_ny);
-    uint32_t y0 = r - z0 * g.ny;
-    uint32_t self[kScanItems], solid_all[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      self[k] = (uint32_t)k < n ? grid[first + k] : 0u;
-      solid_all[k] = 0xFFFFFFFFu;
-    }
+  // One word per lane: the 32 lanes of a warp hold 32 consecutive words, so
+  // each of the 9 neighbour rows arrives in one coalesced load and the x-1 /
+  // x+1 bits come from the neighbouring lanes (lanes 0 and 31 load the word
+  // beyond the warp).  Called by all lanes; n = 0 marks an idle lane.
+  static constexpr int kItems = 1;
+  __device__ void load_run(uint32_t w, uint32_t n, Item (&it)[1]) const {
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool valid = n != 0;
+    const uint32_t r = fast_div(w, g.div_W);
+    const uint32_t xw = w - r * g.W;
+    const uint32_t z = fast_div(r, g.div_ny);
+    const uint32_t y = r - z * g.ny;
+    const uint32_t self = valid ? grid[w] : 0u;
     const int64_t plane = (int64_t)g.W * g.ny;
-#pragma unroll 1
+    uint32_t solid_all = 0xFFFFFFFFu;
+#pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy) {
-        const int64_t off = (int64_t)dy * g.W + (int64_t)dz * plane;
-        uint32_t win[kScanItems + 2];
-#pragma unroll
-        for (int k = 0; k < kScanItems + 2; ++k) {
-          const int64_t q = (int64_t)first + off + k - 1;
-          win[k] = (q >= 0 && q < (int64_t)g.nwords && (uint32_t)k <= n + 1) ? grid[q] : 0u;
-        }
-        uint32_t xw = xw0, y = y0, z = z0;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-          const int yy = (int)y + dy, zz = (int)z + dz;
-          if ((uint32_t)k < n && yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
-            uint32_t c = win[k + 1];
-            if (xw == g.W - 1) c |= g.pad_mask;
-            const uint32_t l = xw > 0 ? win[k] : 0xFFFFFFFFu;
-            uint32_t rr = 0xFFFFFFFFu;
-            if (xw + 1 < g.W) {
-              rr = win[k + 2];
-              if (xw + 1 == g.W - 1) rr |= g.pad_mask;
-            }
-            uint32_t a = ((c << 1) | (l >> 31)) & ((c >> 1) | (rr << 31));
-            if (dy != 0 || dz != 0) a &= c;
-            solid_all[k] &= a;
+        const int yy = (int)y + dy, zz = (int)z + dz;
+        const bool row_ok = valid && yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz;
+        const int64_t q = (int64_t)w + (int64_t)dy * g.W + (int64_t)dz * plane;
+        const uint32_t c0 = row_ok ? grid[q] : 0xFFFFFFFFu;
+        uint32_t l = __shfl_up_sync(0xffffffffu, c0, 1);
+        uint32_t rr = __shfl_down_sync(0xffffffffu, c0, 1);
+        if (lane == 0 && row_ok && xw > 0) l = grid[q - 1];
+        if (lane == 31 && row_ok && xw + 1 < g.W) rr = grid[q + 1];
+        if (row_ok) {
+          uint32_t c = c0;
+          if (xw == g.W - 1) c |= g.pad_mask;
+          if (xw == 0) l = 0xFFFFFFFFu;
+          if (xw + 1 >= g.W) {
+            rr = 0xFFFFFFFFu;
+          } else if (xw + 1 == g.W - 1) {
+            rr |= g.pad_mask;
           }
-          if (++xw == g.W) {
-            xw = 0;
-            if (++y == g.ny) { y = 0; ++z; }
-          }
+          uint32_t a = ((c << 1) | (l >> 31)) & ((c >> 1) | (rr << 31));
+          if (dy != 0 || dz != 0) a &= c;
+          solid_all &= a;
         }
       }
     }
-    const uint32_t par = st->t & 1u;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      if ((uint32_t)k >= n) break;
-      const uint32_t w = first + k;
-      uint32_t claims = 0;
-      if (mode == kFrontStep) {
-        claims = aux[(size_t)par * g.nwords + w];
-        aux[(size_t)(par ^ 1u) * g.nwords + w] = 0;
-      }
-      it[k] = Item{w, self[k] & ~solid_all[k], claims};
+    uint32_t claims = 0;
+    if (valid && mode == kFrontStep) {
+      const uint32_t par = st->t & 1u;
+      claims = aux[(size_t)par * g.nwords + w];
+      aux[(size_t)(par ^ 1u) * g.nwords + w] = 0;
     }
+    it[0] = Item{w, self & ~solid_all, claims};
   }
   __device__ uint32_t count(const Item& it) const { return it.bits ? 1u : 0u; }
   __device__ uint32_t side(const Item& it, int k) const {
@@ -894,7 +881,7 @@ static int num_sms() {
 }
 
 static uint32_t scan_grid(uint64_t max_items) {
-  const uint64_t tiles = (max_items + kScanTile - 1) / kScanTile;
+  const uint64_t tiles = (max_items + kScanMinTile - 1) / kScanMinTile;
   uint64_t blocks = (uint64_t)num_sms() * 4;
   if (blocks > tiles) blocks = tiles;
   return (uint32_t)(blocks ? blocks : 1);

@@ -15,8 +15,20 @@
 namespace qsgs {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;                         // items per thread
-constexpr int kScanTile = kScanThreads * kScanItems;  // items per tile
+constexpr int kScanItems = 8;                         // default items per thread
+constexpr int kScanTile = kScanThreads * kScanItems;  // default items per tile
+constexpr int kScanMinTile = kScanThreads;             // smallest tile (1 item per thread):
+                                                       // sizes the tile-status array
+
+// Items per thread of a policy: Policy::kItems if it declares one, else 8.
+template <class P, class = void>
+struct ItemsPerThread {
+  static constexpr int value = kScanItems;
+};
+template <class P>
+struct ItemsPerThread<P, decltype((void)P::kItems, void())> {
+  static constexpr int value = P::kItems;
+};
 
 // Tile status word: [63:62] flag, [61:33] launch epoch, [32:0] value.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
@@ -46,17 +58,22 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 //   unsigned long long* side_sum(int k) const   --   summed into these counters
 //                                                   (nullptr: not summed)
 //   static constexpr bool kBatched              -- true: items are loaded by
-//   void load_run(uint32_t first, uint32_t n, Item (&it)[kScanItems]) const
+//   void load_run(uint32_t first, uint32_t n, Item (&it)[kItems]) const
 //                                                   (n consecutive valid items)
+//   static constexpr int kItems (optional)      -- items per thread (default 8);
+//                                                   with 1, the 32 lanes of a
+//                                                   warp hold consecutive items
 template <class Policy>
 __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, ScanCtl ctl) {
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_prefix;
   __shared__ uint32_t s_warp[kScanThreads / 32];
 
+  constexpr int kItems = ItemsPerThread<Policy>::value;
+  constexpr int kTile = kScanThreads * kItems;
   if (!pol.active()) return;
   const uint32_t n_items = pol.n_items();
-  const uint32_t ntiles = (uint32_t)(((unsigned long long)n_items + kScanTile - 1) / kScanTile);
+  const uint32_t ntiles = (uint32_t)(((unsigned long long)n_items + kTile - 1) / kTile);
   const uint32_t epoch = *(volatile uint32_t*)&ctl.st->scan_epoch;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) pol.total(0);
@@ -67,22 +84,23 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
     const uint32_t tile = s_tile;
     if (tile >= ntiles) break;
 
-    typename Policy::Item it[kScanItems];
-    uint32_t cnt[kScanItems];
+    typename Policy::Item it[kItems];
+    uint32_t cnt[kItems];
     uint32_t mine = 0, side0 = 0, side1 = 0;
     const unsigned long long base =
-        (unsigned long long)tile * kScanTile + (unsigned long long)threadIdx.x * kScanItems;
+        (unsigned long long)tile * kTile + (unsigned long long)threadIdx.x * kItems;
     const uint32_t n_valid =
-        base >= n_items ? 0u : (uint32_t)min((unsigned long long)kScanItems, n_items - base);
+        base >= n_items ? 0u : (uint32_t)min((unsigned long long)kItems, n_items - base);
     if constexpr (Policy::kBatched) {
-      if (n_valid) pol.load_run((uint32_t)base, n_valid, it);
+      // Called by every thread (warp-cooperative loaders need all lanes).
+      pol.load_run((uint32_t)min(base, (unsigned long long)n_items), n_valid, it);
     } else {
 #pragma unroll
-      for (int k = 0; k < kScanItems; ++k)
+      for (int k = 0; k < kItems; ++k)
         if ((uint32_t)k < n_valid) it[k] = pol.load((uint32_t)(base + k));
     }
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    for (int k = 0; k < kItems; ++k) {
       cnt[k] = 0;
       if ((uint32_t)k < n_valid) {
         cnt[k] = pol.count(it[k]);
@@ -172,7 +190,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
 
     unsigned long long off = s_prefix + warp_excl + (incl - mine);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    for (int k = 0; k < kItems; ++k) {
       if (cnt[k] || pol.emit_empty()) {
         if (base + k < n_items) pol.emit(it[k], off);
       }
