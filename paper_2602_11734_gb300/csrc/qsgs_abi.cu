@@ -74,7 +74,7 @@ Layout make_layout(const qsgs_params* p) {
   }
   uint64_t max_items = n > nwords ? n : nwords;
   if (ncells > max_items) max_items = ncells;
-  L.ntiles = (max_items + kScanMinTile - 1) / kScanMinTile + 1;
+  L.ntiles = (max_items + kScanTile - 1) / kScanTile + 1;
   size_t off = 0;
   L.state = off; off = align_up(off + sizeof(RunState));
   L.scan_status = off; off = align_up(off + L.ntiles * sizeof(unsigned long long));

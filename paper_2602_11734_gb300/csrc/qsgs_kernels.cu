@@ -128,44 +128,6 @@ __global__ void k_trim_done(RunState* st) { st->trim_pending = 0; }
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return *p; }
 
-// Solid-or-outside mask of word xw of row (y+dy, z+dz), with the row's
-// padding bits and out-of-domain rows reading as solid.
-__device__ __forceinline__ uint32_t row_word(const Geom& g, const uint32_t* grid, uint32_t r_nb,
-                                             uint32_t xw) {
-  uint32_t w = ld_word(grid + (size_t)r_nb * g.W + xw);
-  if (xw == g.W - 1) w |= g.pad_mask;
-  return w;
-}
-
-// Front word of word index w: solid voxels with at least one void in-domain
-// 26-neighbour, evaluated bit-parallel over the 32 voxels of the word.
-__device__ __forceinline__ uint32_t front_word(const Geom& g, const uint32_t* grid, uint32_t w) {
-  const uint32_t r = fast_div(w, g.div_W);
-  const uint32_t xw = w - r * g.W;
-  const uint32_t z = fast_div(r, g.div_ny);
-  const uint32_t y = r - z * g.ny;
-  const uint32_t self = ld_word(grid + w);
-  if (self == 0) return 0;
-  uint32_t all_solid = 0xFFFFFFFFu;
-#pragma unroll
-  for (int dz = -1; dz <= 1; ++dz) {
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = (int)y + dy, zz = (int)z + dz;
-      if (yy < 0 || yy >= (int)g.ny || zz < 0 || zz >= (int)g.nz) continue;  // outside: solid
-      const uint32_t rn = (uint32_t)(yy + (int)g.ny * zz);
-      const uint32_t c = row_word(g, grid, rn, xw);
-      const uint32_t l = xw > 0 ? ld_word(grid + (size_t)rn * g.W + xw - 1) : 0xFFFFFFFFu;
-      const uint32_t rr = xw + 1 < g.W ? row_word(g, grid, rn, xw + 1) : 0xFFFFFFFFu;
-      const uint32_t minus = (c << 1) | (l >> 31);  // bit i: solid at x - 1
-      const uint32_t plus = (c >> 1) | (rr << 31);  // bit i: solid at x + 1
-      all_solid &= minus & plus;
-      if (dy != 0 || dz != 0) all_solid &= c;
-    }
-  }
-  return self & ~all_solid;
-}
-
 // ---------------------------------------------------------------------------
 // Scan policies.
 // ---------------------------------------------------------------------------
@@ -197,14 +159,13 @@ struct SeedCompactPolicy {
   uint32_t* cand;
   uint32_t k0, k1;
   using Item = WordItem;
-  static constexpr bool kBatched = false;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  __device__ Item load(uint32_t w) const {
+  __device__ Item load(uint32_t w, bool valid) const {
+    if (!valid) return Item{};
     const unsigned long long t_seed = st->t_seed;
     uint32_t bits = 0;
     if (t_seed != 0) {
@@ -255,21 +216,17 @@ struct FrontPolicy {
   uint2* front;
   int mode;
   using Item = WordItem;
-  static constexpr bool kBatched = true;
   __device__ bool active() const {
     return mode == kFrontInitial ? true : (mode == kFrontStep ? st->active != 0 : st->trim_pending != 0);
   }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  __device__ Item load(uint32_t w) const { return Item{w, front_word(g, grid, w), 0u}; }
-  // One word per lane: the 32 lanes of a warp hold 32 consecutive words, so
-  // each of the 9 neighbour rows arrives in one coalesced load and the x-1 /
-  // x+1 bits come from the neighbouring lanes (lanes 0 and 31 load the word
-  // beyond the warp).  Called by all lanes; n = 0 marks an idle lane.
-  static constexpr int kItems = 1;
-  __device__ void load_run(uint32_t w, uint32_t n, Item (&it)[1]) const {
+  // Warp-cooperative: the 32 lanes hold 32 consecutive words, so each of the
+  // 9 neighbour rows arrives in one coalesced load and the x-1 / x+1 bits
+  // come from the neighbouring lanes (lanes 0 and 31 load the word beyond
+  // the warp).  Idle lanes take part in the shuffles only.
+  __device__ Item load(uint32_t w, bool valid) const {
     const uint32_t lane = threadIdx.x & 31u;
-    const bool valid = n != 0;
     const uint32_t r = fast_div(w, g.div_W);
     const uint32_t xw = w - r * g.W;
     const uint32_t z = fast_div(r, g.div_ny);
@@ -310,7 +267,7 @@ struct FrontPolicy {
       claims = aux[(size_t)par * g.nwords + w];
       aux[(size_t)(par ^ 1u) * g.nwords + w] = 0;
     }
-    it[0] = Item{w, self & ~solid_all, claims};
+    return Item{w, self & ~solid_all, claims};
   }
   __device__ uint32_t count(const Item& it) const { return it.bits ? 1u : 0u; }
   __device__ uint32_t side(const Item& it, int k) const {
@@ -338,14 +295,13 @@ struct TrimPolicy {
   uint32_t* grid;
   const uint32_t* aux;  // two claim grids
   using Item = WordItem;
-  static constexpr bool kBatched = false;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return st->trim_pending != 0; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  __device__ Item load(uint32_t w) const {
+  __device__ Item load(uint32_t w, bool valid) const {
+    if (!valid) return Item{};
     return Item{w, aux[(size_t)st->trim_parity * g.nwords + w], 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
@@ -377,14 +333,13 @@ struct AcceptPolicy {
     uint32_t v;
     uint32_t ok;
   };
-  static constexpr bool kBatched = false;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return st->cand_n; }
-  __device__ Item load(uint32_t i) const {
+  __device__ Item load(uint32_t i, bool valid) const {
+    if (!valid) return Item{};
     return Item{cand[i], decision ? (uint32_t)(decision[i] == 1) : 1u};
   }
   __device__ uint32_t count(const Item& it) const { return it.ok; }
@@ -411,14 +366,15 @@ struct CellOffsetPolicy {
   struct Item {
     uint32_t i, c;
   };
-  static constexpr bool kBatched = false;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return ncells; }
-  __device__ Item load(uint32_t i) const { return Item{i, cell_count[i]}; }
+  __device__ Item load(uint32_t i, bool valid) const {
+    if (!valid) return Item{};
+    return Item{i, cell_count[i]};
+  }
   __device__ uint32_t count(const Item& it) const { return it.c; }
   __device__ void emit(const Item& it, unsigned long long off) const {
     start[it.i] = (uint32_t)off;
@@ -521,14 +477,15 @@ struct ConflictOffsetPolicy {
   struct Item {
     uint32_t i, c;
   };
-  static constexpr bool kBatched = false;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void load_run(uint32_t, uint32_t, Item (&)[kScanItems]) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return st->cand_n; }
-  __device__ Item load(uint32_t i) const { return Item{i, off[i]}; }
+  __device__ Item load(uint32_t i, bool valid) const {
+    if (!valid) return Item{};
+    return Item{i, off[i]};
+  }
   __device__ uint32_t count(const Item& it) const { return it.c; }
   __device__ void emit(const Item& it, unsigned long long o) const { off[it.i] = (uint32_t)o; }
   __device__ void total(unsigned long long n) const {
@@ -881,7 +838,7 @@ static int num_sms() {
 }
 
 static uint32_t scan_grid(uint64_t max_items) {
-  const uint64_t tiles = (max_items + kScanMinTile - 1) / kScanMinTile;
+  const uint64_t tiles = (max_items + kScanTile - 1) / kScanTile;
   uint64_t blocks = (uint64_t)num_sms() * 4;
   if (blocks > tiles) blocks = tiles;
   return (uint32_t)(blocks ? blocks : 1);

@@ -15,20 +15,8 @@
 namespace qsgs {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;                         // default items per thread
-constexpr int kScanTile = kScanThreads * kScanItems;  // default items per tile
-constexpr int kScanMinTile = kScanThreads;             // smallest tile (1 item per thread):
-                                                       // sizes the tile-status array
-
-// Items per thread of a policy: Policy::kItems if it declares one, else 8.
-template <class P, class = void>
-struct ItemsPerThread {
-  static constexpr int value = kScanItems;
-};
-template <class P>
-struct ItemsPerThread<P, decltype((void)P::kItems, void())> {
-  static constexpr int value = P::kItems;
-};
+constexpr int kScanItems = 8;                         // items per thread
+constexpr int kScanTile = kScanThreads * kScanItems;  // items per tile
 
 // Tile status word: [63:62] flag, [61:33] launch epoch, [32:0] value.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
@@ -50,32 +38,38 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 // Policy interface:
 //   bool active() const                  -- uniform: false skips the launch
 //   uint32_t n_items() const             -- number of items (read on device)
-//   Item load(uint32_t i) const          -- i < n_items
+//   Item load(uint32_t i, bool valid) const
+//                                        -- called by all 32 lanes of a warp
+//                                           together (lane l gets item base+l,
+//                                           so warp-cooperative loaders may use
+//                                           shuffles); invalid lanes get
+//                                           i = n_items and must not touch it
 //   uint32_t count(const Item&) const    -- outputs of the item
 //   void emit(const Item&, unsigned long long prefix) const
+//   bool emit_empty() const              -- also emit items with count 0
 //   void total(unsigned long long) const -- called once with the grand total
 //   uint32_t side(const Item&, int k) const     -- extra per-item values k = 0, 1,
 //   unsigned long long* side_sum(int k) const   --   summed into these counters
 //                                                   (nullptr: not summed)
-//   static constexpr bool kBatched              -- true: items are loaded by
-//   void load_run(uint32_t first, uint32_t n, Item (&it)[kItems]) const
-//                                                   (n consecutive valid items)
-//   static constexpr int kItems (optional)      -- items per thread (default 8);
-//                                                   with 1, the 32 lanes of a
-//                                                   warp hold consecutive items
+//
+// Tile layout: a tile holds kScanTile items; thread t of the block handles
+// items base + k * kScanThreads + t for k < kScanItems, so every warp works
+// on 32 consecutive items at a time (coalesced loads).  The order of the
+// outputs is the order of the items: offsets are taken over (k, warp, lane)
+// in that nesting.
 template <class Policy>
 __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, ScanCtl ctl) {
+  constexpr int kWarps = kScanThreads / 32;
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_prefix;
-  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_off[kScanItems * kWarps];  // warp totals, then their offsets
+  __shared__ uint32_t s_agg;
 
-  constexpr int kItems = ItemsPerThread<Policy>::value;
-  constexpr int kTile = kScanThreads * kItems;
   if (!pol.active()) return;
   const uint32_t n_items = pol.n_items();
-  const uint32_t ntiles = (uint32_t)(((unsigned long long)n_items + kTile - 1) / kTile);
+  const uint32_t ntiles = (uint32_t)(((unsigned long long)n_items + kScanTile - 1) / kScanTile);
   const uint32_t epoch = *(volatile uint32_t*)&ctl.st->scan_epoch;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) pol.total(0);
 
   for (;;) {
@@ -84,32 +78,29 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
     const uint32_t tile = s_tile;
     if (tile >= ntiles) break;
 
-    typename Policy::Item it[kItems];
-    uint32_t cnt[kItems];
-    uint32_t mine = 0, side0 = 0, side1 = 0;
-    const unsigned long long base =
-        (unsigned long long)tile * kTile + (unsigned long long)threadIdx.x * kItems;
-    const uint32_t n_valid =
-        base >= n_items ? 0u : (uint32_t)min((unsigned long long)kItems, n_items - base);
-    if constexpr (Policy::kBatched) {
-      // Called by every thread (warp-cooperative loaders need all lanes).
-      pol.load_run((uint32_t)min(base, (unsigned long long)n_items), n_valid, it);
-    } else {
+    typename Policy::Item it[kScanItems];
+    uint32_t cnt[kScanItems], lex[kScanItems];
+    uint32_t side0 = 0, side1 = 0;
+    const unsigned long long base = (unsigned long long)tile * kScanTile + threadIdx.x;
 #pragma unroll
-      for (int k = 0; k < kItems; ++k)
-        if ((uint32_t)k < n_valid) it[k] = pol.load((uint32_t)(base + k));
-    }
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      cnt[k] = 0;
-      if ((uint32_t)k < n_valid) {
-        cnt[k] = pol.count(it[k]);
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned long long i = base + (unsigned long long)k * kScanThreads;
+      const bool valid = i < n_items;
+      it[k] = pol.load(valid ? (uint32_t)i : n_items, valid);
+      cnt[k] = valid ? pol.count(it[k]) : 0u;
+      if (valid) {
         side0 += pol.side(it[k], 0);
         side1 += pol.side(it[k], 1);
       }
-      mine += cnt[k];
+      uint32_t incl = cnt[k];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      lex[k] = incl - cnt[k];
+      if (lane == 31) s_off[k * kWarps + warp] = incl;
     }
-
     if (pol.side_sum(0) != nullptr) {
       const uint32_t ws = __reduce_add_sync(0xffffffffu, side0);
       if (lane == 0 && ws) atomicAdd(pol.side_sum(0), (unsigned long long)ws);
@@ -118,28 +109,26 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
       const uint32_t ws = __reduce_add_sync(0xffffffffu, side1);
       if (lane == 0 && ws) atomicAdd(pol.side_sum(1), (unsigned long long)ws);
     }
-
-    // Block-wide exclusive scan of the per-thread counts.
-    uint32_t incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
+
+    // Exclusive offsets of the kScanItems x kWarps warp totals (k-major),
+    // two per lane of warp 0.
     if (warp == 0) {
-      uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+      static_assert(kScanItems * kWarps == 64, "two warp totals per lane");
+      const uint32_t a = s_off[2 * lane], b = s_off[2 * lane + 1];
+      uint32_t incl = a + b;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
       }
-      if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive warp totals
+      const uint32_t excl = incl - a - b;
+      s_off[2 * lane] = excl;
+      s_off[2 * lane + 1] = excl + a;
+      if (lane == 31) s_agg = incl;
     }
     __syncthreads();
-    const uint32_t warp_excl = warp ? s_warp[warp - 1] : 0;
-    const uint32_t aggregate = s_warp[kScanThreads / 32 - 1];
+    const uint32_t aggregate = s_agg;
 
     // Decoupled look-back by warp 0: each round reads the 32 tiles before
     // the current window in parallel, waits (bounded) until all of them have
@@ -152,8 +141,8 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
         if (lane == 0) atomicExch(&ctl.status[tile], tile_word(kFlagAggregate, epoch, aggregate));
         int64_t window_end = (int64_t)tile - 1;  // highest tile of the window
         for (;;) {
-          const int64_t p = window_end - lane;  // lane 0 = nearest predecessor
-          unsigned long long w = kFlagPrefix;  // tiles before 0: empty prefix
+          const int64_t p = window_end - (int64_t)lane;  // lane 0 = nearest predecessor
+          unsigned long long w = kFlagPrefix;           // tiles before 0: empty prefix
           if (p >= 0) {
             uint32_t polls = 0;
             for (;;) {
@@ -171,7 +160,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
           const uint32_t pmask = __ballot_sync(0xffffffffu, is_prefix);
           // Lanes up to and including the nearest inclusive prefix contribute.
           const int stop = pmask ? __ffs(pmask) - 1 : 31;
-          unsigned long long v = (lane <= stop) ? (w & kValueMask) : 0ull;
+          unsigned long long v = ((int)lane <= stop) ? (w & kValueMask) : 0ull;
 #pragma unroll
           for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           prefix += v;
@@ -188,15 +177,14 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
     }
     __syncthreads();
 
-    unsigned long long off = s_prefix + warp_excl + (incl - mine);
+    const unsigned long long tile_prefix = s_prefix;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      if (cnt[k] || pol.emit_empty()) {
-        if (base + k < n_items) pol.emit(it[k], off);
-      }
-      off += cnt[k];
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned long long i = base + (unsigned long long)k * kScanThreads;
+      if (i < n_items && (cnt[k] || pol.emit_empty()))
+        pol.emit(it[k], tile_prefix + s_off[k * kWarps + warp] + lex[k]);
     }
-    __syncthreads();  // s_tile / s_warp / s_prefix are reused by the next tile
+    __syncthreads();  // s_tile / s_off / s_prefix are reused by the next tile
   }
 
   // The last block to finish re-arms the dispenser for the next launch.
