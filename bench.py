@@ -35,8 +35,7 @@ WORKLOAD = "single_400"
 L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2: written between timed steps
 CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
-BYTES_PER_FRONT_VOXEL = 40       # k_grow: 4 B front entry + 9 row words of 4 B
-BYTES_PER_CLAIM = 8              # k_grow: atomicOr into grid and claim grid
+PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
 
 
 def parse():
@@ -216,20 +215,28 @@ def main():
     value = n_vox * a.steps * world / (total_ms / 1000.0)
 
     # Kernel-level pass with the library's event profiler (not timed above).
+    # k_grow is bound by integer ALU work: one Philox4x32-10 block per
+    # (front voxel, direction block) pair.  Its ceiling is the rate of the
+    # library's Philox probe on this GPU (same generator, no memory traffic).
     g.set_profiling(True)
     g.seed()
     st_prof = g.grow()
     prof = g.profile()
     g.set_profiling(False)
     grow_launches, grow_ms = prof["grow"]
-    claims = st_prof.solid_count - st_prof.n_seeds
-    alg_bytes = BYTES_PER_FRONT_VOXEL * st_prof.sum_front + BYTES_PER_CLAIM * claims
+    probe_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    probe_ms = min(Q.qsgs_bench_philox(PEAK_PROBE_BLOCKS, probe_out.data_ptr(), s.cuda_stream)
+                   for _ in range(3))
+    peak = PEAK_PROBE_BLOCKS / (probe_ms / 1000.0) / 1e9
+    achieved = st_prof.sum_draws / (grow_ms / 1000.0) / 1e9
     pk, pk_kind = peaks()
-    achieved = alg_bytes / (grow_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_grow",
-                "peak_kind": pk_kind, "launches": grow_launches,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gblock/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_grow",
+                "work": "Philox4x32-10 blocks drawn per second",
+                "peak_kind": "measured (qsgs_bench_philox probe on this GPU)",
+                "draws": st_prof.sum_draws, "launches": grow_launches,
                 "mean_launch_ms": grow_ms / max(1, grow_launches),
+                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
                 "phases_ms": {k: round(v[1], 4) for k, v in prof.items()}}
 
     # End to end through the C ABI with host buffers: create, seed, grow and

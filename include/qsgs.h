@@ -103,6 +103,7 @@ typedef struct qsgs_stats {
   uint32_t steps;
   int32_t status;
   uint64_t launches; /* kernels this handle has launched since creation  */
+  uint64_t sum_draws; /* Philox blocks drawn by growth steps (sum over t)  */
 } qsgs_stats;
 
 /* One kernel class of the optional event profiler (qsgs_profile).
@@ -187,6 +188,16 @@ int qsgs_set_profiling(qsgs_handle* h, int enable);
 /* Copies up to max_entries profiler totals into out (host) and returns the
  * number of kernel classes (>= 0), or QSGS_ERR_INVALID. */
 int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries);
+
+/* Calibration probe: times Philox4x32-10 blocks drawn as fast as the GPU
+ * can, with no memory traffic -- the ALU ceiling of the growth step, whose
+ * work is one Philox block per (front voxel, direction block) pair.
+ *   n_blocks   blocks to time (rounded up to whole threads)
+ *   dev_out    device, 8 bytes: receives a checksum (keeps the work live)
+ *   cuda_stream  stream to run on (NULL = legacy default stream)
+ *   ms         host: elapsed milliseconds for n_blocks blocks
+ * Blocks until done.  Returns QSGS_OK, QSGS_ERR_INVALID or QSGS_ERR_CUDA. */
+int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, double* ms);
 
 /* Releases the handle (host memory only).  NULL is ignored. */
 void qsgs_destroy(qsgs_handle* h);

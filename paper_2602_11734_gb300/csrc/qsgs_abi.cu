@@ -158,6 +158,7 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
   out->steps = s.t;
   out->status = s.status == kRunning ? QSGS_RUNNING : s.status;
   out->launches = h->tracer.launches;
+  out->sum_draws = s.sum_draws;
 }
 
 StepBuffers step_buffers(const qsgs_handle* h) {
@@ -429,6 +430,36 @@ int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries) {
     out[c].total_ms = h->tracer.ms[c];
   }
   return kNumClasses;
+}
+
+int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, double* ms) {
+  if (!dev_out || !ms || n_blocks == 0) return QSGS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return QSGS_ERR_CUDA;
+  const uint32_t blocks = (uint32_t)sms * 8u;  // 2048 threads per SM
+  const uint64_t threads = (uint64_t)blocks * 256u;
+  uint64_t per = (n_blocks + threads - 1) / threads;
+  if (per > 0xFFFFFFFFull) return QSGS_ERR_INVALID;
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev_out, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess)
+    e = launch_philox_rate(0x0123456789ABCDEFull, blocks, (uint32_t)per,
+                           static_cast<unsigned long long*>(dev_out), s);
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return QSGS_ERR_CUDA;
+  *ms = (double)t * (double)n_blocks / (double)(threads * per);  // scaled to n_blocks
+  return QSGS_OK;
 }
 
 void qsgs_destroy(qsgs_handle* h) {

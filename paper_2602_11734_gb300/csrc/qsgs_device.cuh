@@ -214,6 +214,7 @@ struct alignas(256) RunState {
   unsigned long long claimed;    // |New_t|, counted by the front rebuild
   unsigned long long live;       // attempts with a positive threshold
   unsigned long long sum_front;  // sum over steps of |A_t| (statistics)
+  unsigned long long sum_draws;  // Philox blocks drawn by growth steps
   unsigned long long front_n;    // |A_t| (front voxels)
   unsigned long long front_acc;  // |A_{t+1}| being counted by the rebuild
   unsigned long long adj_n;      // spacing: total earlier-conflict entries

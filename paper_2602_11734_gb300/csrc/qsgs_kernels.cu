@@ -46,6 +46,7 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->claimed = 0;
   st->live = 0;
   st->sum_front = 0;
+  st->sum_draws = 0;
   st->front_n = 0;
   st->front_acc = 0;
   st->adj_n = 0;
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  uint32_t my_live = 0;
+  uint32_t my_live = 0, my_draws = 0;
 
   for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
     // Phase 1: masks of this lane's word.
@@ -763,6 +764,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
         const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
         const uint32_t v = S.v0[owner] + i;
         const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
+        ++my_draws;
         const uint4 vm = S.V[owner][b];
         const uint32_t vb = ((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
                             (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3);
@@ -789,7 +791,32 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
     }
   }
   const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
+  const uint32_t wd = __reduce_add_sync(0xffffffffu, my_draws);
   if (lane == 0 && wl) atomicAdd(&st->live, (unsigned long long)wl);
+  if (lane == 0 && wd) atomicAdd(&st->sum_draws, (unsigned long long)wd);
+}
+
+// ---------------------------------------------------------------------------
+// Philox throughput probe: every thread draws `per_thread` blocks with
+// distinct counters and folds them into one word, so nothing is optimised
+// away.  Its rate is the ALU ceiling the growth kernel is compared with.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_philox_rate(PhiloxKeys keys, uint32_t per_thread,
+                                                     unsigned long long* out) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (uint32_t k = 0; k < per_thread; ++k) {
+    const U4 r = philox4x32_10(U4{tid, 0u, k, kGrowTag}, keys);
+    acc ^= r.x ^ r.y ^ r.z ^ r.w;
+  }
+  const uint32_t wsum = __reduce_add_sync(0xffffffffu, acc & 0xFFFFu);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, (unsigned long long)wsum);
+}
+
+cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
+                               unsigned long long* out, cudaStream_t s) {
+  k_philox_rate<<<blocks, 256, 0, s>>>(make_philox_keys(seed), per_thread, out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -148,6 +148,8 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
 cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                             cudaStream_t s, Tracer& tr);
 cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
+cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
+                               unsigned long long* out, cudaStream_t s);
 cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
                              Tracer& tr);
 

@@ -43,7 +43,7 @@ class QsgsStats(ctypes.Structure):
                 ("front_size", ctypes.c_uint64), ("n_candidates", ctypes.c_uint64),
                 ("n_seeds", ctypes.c_uint64), ("sum_front", ctypes.c_uint64),
                 ("steps", ctypes.c_uint32), ("status", ctypes.c_int32),
-                ("launches", ctypes.c_uint64)]
+                ("launches", ctypes.c_uint64), ("sum_draws", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_set_profiling": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_profile": ([H, ctypes.POINTER(QsgsProfileEntry), ctypes.c_int],
                                  ctypes.c_int),
+                "qsgs_bench_philox": ([ctypes.c_uint64, vp, vp, ctypes.POINTER(ctypes.c_double)],
+                                      ctypes.c_int),
                 "qsgs_destroy": ([H], None),
             }
             for name, (args, res) in sig.items():
@@ -186,6 +188,16 @@ def qsgs_profile(h) -> dict:
             for i in range(min(n, 16))}
 
 
+def qsgs_bench_philox(n_blocks: int, dev_out_ptr: int, stream_ptr: int) -> float:
+    """Milliseconds the GPU needs for n_blocks Philox4x32-10 blocks."""
+    ms = ctypes.c_double()
+    rc = load_library().qsgs_bench_philox(n_blocks, ctypes.c_void_p(dev_out_ptr),
+                                          ctypes.c_void_p(stream_ptr), ctypes.byref(ms))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_bench_philox")
+    return ms.value
+
+
 def qsgs_destroy(h) -> None:
     if h:
         load_library().qsgs_destroy(h)
@@ -203,6 +215,7 @@ class Stats:
     steps: int
     status: int
     launches: int
+    sum_draws: int
 
 
 class Generator:

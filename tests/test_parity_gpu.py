@@ -217,3 +217,18 @@ def test_launch_counter_grows_with_steps(Q):
         assert st.launches - before >= 3 * st.steps
     finally:
         g.close()
+
+
+def test_philox_probe_and_draw_counter(Q):
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = Q.qsgs_bench_philox(1 << 24, out.data_ptr(), 0)
+    assert ms > 0 and int(out.item()) != 0
+    p = dict(workloads.small_64(), nx=40, ny=40, nz=40)
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        st = g.grow()
+        # at least one Philox block per growth step, at most 7 per front voxel
+        assert st.steps <= st.sum_draws <= 7 * st.sum_front
+    finally:
+        g.close()
