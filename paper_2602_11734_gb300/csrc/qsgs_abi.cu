@@ -25,7 +25,7 @@ constexpr uint32_t kStepsPerSync = 8;      // steps enqueued between host checks
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t state, scan_status, grid, aux, list, cell_count, cell_start, cell_items, decision;
+  size_t state, scan_status, grid, aux, mark, list, cell_count, cell_start, cell_items, decision;
   size_t conf_off, adj, total;
   uint64_t adj_cap;
   uint64_t ntiles;
@@ -80,9 +80,10 @@ Layout make_layout(const qsgs_params* p) {
   L.scan_status = off; off = align_up(off + L.ntiles * sizeof(unsigned long long));
   L.grid = off; off = align_up(off + nwords * 4);
   L.aux = off; off = align_up(off + 2 * nwords * 4);  // claim grids of even / odd steps
-  // Candidates (u32 each, at most N), then the front word list ({word,
-  // bits} pairs, at most nwords).
-  const uint64_t list_bytes = n * 4 > nwords * 8 ? n * 4 : nwords * 8;
+  L.mark = off; off = align_up(off + (nwords / 32 + 1) * 4);
+  // Seed candidates (at most N), then the candidate word list (at most
+  // nwords); u32 entries.
+  const uint64_t list_bytes = (n > nwords ? n : nwords) * 4;
   L.list = off; off = align_up(off + list_bytes);
   if (ncells) {
     L.cell_count = off; off = align_up(off + ncells * 4);
@@ -111,6 +112,7 @@ struct qsgs_handle {
   uint32_t* grid;
   uint32_t* aux;
   uint32_t* list;
+  uint32_t* mark;
   uint32_t *cell_count, *cell_start, *cell_items, *conf_off, *adj;
   uint8_t* decision;
   uint32_t k0, k1;
@@ -162,7 +164,7 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
 }
 
 StepBuffers step_buffers(const qsgs_handle* h) {
-  return StepBuffers{h->st, h->scan_status, h->grid, h->aux, reinterpret_cast<uint2*>(h->list)};
+  return StepBuffers{h->st, h->scan_status, h->grid, h->aux, h->mark, h->list};
 }
 
 void destroy_graph(qsgs_handle* h) {
@@ -274,6 +276,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->grid = reinterpret_cast<uint32_t*>(h->ws + L.grid);
   h->aux = reinterpret_cast<uint32_t*>(h->ws + L.aux);
   h->list = reinterpret_cast<uint32_t*>(h->ws + L.list);
+  h->mark = reinterpret_cast<uint32_t*>(h->ws + L.mark);
   const bool spacing = params->spacing_s >= 2;
   h->cell_count = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.cell_count) : nullptr;
   h->cell_start = spacing ? reinterpret_cast<uint32_t*>(h->ws + L.cell_start) : nullptr;
@@ -306,6 +309,7 @@ int qsgs_seed(qsgs_handle* h) {
   const size_t grids = (size_t)h->g.nwords * 4;
   cudaError_t e = cudaMemsetAsync(h->grid, 0, grids, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->mark, 0, (h->g.nwords / 32 + 1) * 4, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   StateInit init{};
   init.nt = h->ints.nt;
@@ -315,7 +319,7 @@ int qsgs_seed(qsgs_handle* h) {
   e = launch_init_state(h->st, init, h->stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
   SeedBuffers b{h->st,         h->scan_status, h->grid,     h->aux,
-                h->list,       h->cell_count,  h->cell_start, h->cell_items,
+                h->list,       h->mark,        h->cell_count,  h->cell_start, h->cell_items,
                 h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
                 h->L.cg};
   e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, h->stream, h->tracer);
@@ -344,9 +348,9 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
     if (e != cudaSuccess) return cuda_fail(h, e);
     const int rc = read_state(h, &s);
     if (rc != QSGS_OK) return rc;
-    // Count the kernels the graph ran: three per loop iteration, three in
+    // Count the kernels the graph ran: three per loop iteration, four in
     // the epilogue.
-    h->tracer.launches += 3ull * (s.iters - h->iters_seen) + 3ull;
+    h->tracer.launches += 3ull * (s.iters - h->iters_seen) + 4ull;
     h->iters_seen = s.iters;
   } else {
     for (;;) {

@@ -90,7 +90,7 @@ __global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, in
     if (st->live == 0) {
       st->status = kStatusStalled;
     } else {
-      st->sum_front += st->front_n;
+      st->sum_front += st->front_acc;  // |A_t|, counted by the growth kernel
       st->front_n = st->front_acc;
       const unsigned long long c = st->solid, k = st->claimed;
       if (c + k > st->nt) {
@@ -123,6 +123,8 @@ __global__ void k_set_step_limit(RunState* st, uint32_t extra) {
 }
 
 __global__ void k_trim_done(RunState* st) { st->trim_pending = 0; }
+
+__global__ void k_zero_front(RunState* st) { st->front_n = 0; }
 
 // ---------------------------------------------------------------------------
 // Shared helpers.
@@ -193,39 +195,79 @@ struct SeedCompactPolicy {
   __device__ void total(unsigned long long n) const { st->cand_n = (uint32_t)n; }
 };
 
-// Sec. 2.3 step 2 / step 4: the active front rebuilt from the grid, as an
-// ascending list of {word index, front bits} -- one entry per 32-voxel row
-// word that holds at least one front voxel.
+// The candidate word list that drives the growth kernel: words that may
+// hold front voxels (Sec. 2.3 step 2: solids with a void neighbour).
 //
-// Why a rebuild from the grid equals prune(A_t U New_t): a voxel solid after
-// step t with a void neighbour either is in New_t or was solid before with
-// that neighbour already void (voids only shrink), hence in A_t.  So the
-// front is a function of the grid alone, and one order-preserving scan over
-// all grid words yields it sorted, with no sort of New_t.
+// Why "words marked by the last growth step, plus words that received
+// claims" is enough: a voxel solid after step t with a void neighbour either
+// is in New_t or was solid before with that neighbour already void (voids
+// only shrink), i.e. it was a front voxel of step t.  So A_{t+1} = prune(A_t
+// U New_t) lies in those words, and the growth kernel itself computes the
+// exact front bits of every candidate word from the grid.
 //
-// Modes: kFrontInitial (after seeding: counts into front_n), kFrontStep
-// (after a growth step: counts the front into front_acc and the step's
-// claims into claimed, and clears the other claim grid for the next step),
-// kFrontFinal (after the exact-target trim: recounts front_n).
-enum : int { kFrontInitial = 0, kFrontStep = 1, kFrontFinal = 2 };
+// kCommitInitial (after seeding): every word holding a solid voxel.
+// kCommitStep (after a growth step): ORs the step's claims into the grid,
+// counts them, emits marked or claimed words, clears the marks and the
+// claim grid of the next step.  The list stays in ascending word order.
+enum : int { kCommitInitial = 0, kCommitStep = 1 };
 
-struct FrontPolicy {
+struct CommitPolicy {
+  Geom g;
+  RunState* st;
+  uint32_t* grid;
+  uint32_t* aux;   // two claim grids of nwords words each
+  uint32_t* mark;  // one bit per word, set by the growth kernel
+  uint32_t* list;
+  int mode;
+  using Item = WordItem;
+  __device__ bool active() const { return mode == kCommitInitial || st->active != 0; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return g.nwords; }
+  // Called by the 32 lanes of a warp together; lane l holds word 32j + l, so
+  // lane 0 reads the warp's mark word and shares it.
+  __device__ Item load(uint32_t w, bool valid) const {
+    const uint32_t lane = threadIdx.x & 31u;
+    if (mode == kCommitInitial) {
+      const uint32_t solid = valid ? grid[w] : 0u;
+      return Item{w, solid ? 1u : 0u, 0u};
+    }
+    uint32_t m = 0;
+    if (lane == 0 && valid) {
+      m = mark[w >> 5];
+      if (m) mark[w >> 5] = 0;
+    }
+    m = __shfl_sync(0xffffffffu, m, 0);
+    if (!valid) return Item{w, 0u, 0u};
+    const uint32_t par = st->t & 1u;
+    const uint32_t c = aux[(size_t)par * g.nwords + w];
+    uint32_t* other = aux + (size_t)(par ^ 1u) * g.nwords + w;
+    if (*other) *other = 0;
+    if (c) grid[w] |= c;
+    const uint32_t keep = ((m >> lane) & 1u) | (c ? 1u : 0u);
+    return Item{w, keep, c};
+  }
+  __device__ uint32_t count(const Item& it) const { return it.bits; }
+  __device__ uint32_t side(const Item& it, int k) const { return k == 1 ? __popc(it.extra) : 0u; }
+  __device__ unsigned long long* side_sum(int k) const {
+    return (k == 1 && mode == kCommitStep) ? &st->claimed : nullptr;
+  }
+  __device__ void emit(const Item& it, unsigned long long off) const { list[off] = it.w; }
+  __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
+};
+
+// The front size |A| of the current grid (solids with a void in-domain
+// 26-neighbour), counted once at the end of a growth call for the
+// statistics.  Warp-cooperative: the 32 lanes hold 32 consecutive words,
+// each neighbour row arrives in one coalesced load and the x-1 / x+1 bits
+// come from the neighbouring lanes.
+struct FrontCountPolicy {
   Geom g;
   RunState* st;
   const uint32_t* grid;
-  uint32_t* aux;  // two claim grids of nwords words each
-  uint2* front;
-  int mode;
   using Item = WordItem;
-  __device__ bool active() const {
-    return mode == kFrontInitial ? true : (mode == kFrontStep ? st->active != 0 : st->trim_pending != 0);
-  }
+  __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  // Warp-cooperative: the 32 lanes hold 32 consecutive words, so each of the
-  // 9 neighbour rows arrives in one coalesced load and the x-1 / x+1 bits
-  // come from the neighbouring lanes (lanes 0 and 31 load the word beyond
-  // the warp).  Idle lanes take part in the shuffles only.
   __device__ Item load(uint32_t w, bool valid) const {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t r = fast_div(w, g.div_W);
@@ -262,28 +304,13 @@ struct FrontPolicy {
         }
       }
     }
-    uint32_t claims = 0;
-    if (valid && mode == kFrontStep) {
-      const uint32_t par = st->t & 1u;
-      claims = aux[(size_t)par * g.nwords + w];
-      aux[(size_t)(par ^ 1u) * g.nwords + w] = 0;
-    }
-    return Item{w, self & ~solid_all, claims};
+    return Item{w, self & ~solid_all, 0u};
   }
-  __device__ uint32_t count(const Item& it) const { return it.bits ? 1u : 0u; }
-  __device__ uint32_t side(const Item& it, int k) const {
-    return k == 0 ? __popc(it.bits) : __popc(it.extra);
-  }
-  __device__ unsigned long long* side_sum(int k) const {
-    if (k == 0) return mode == kFrontStep ? &st->front_acc : &st->front_n;
-    return mode == kFrontStep ? &st->claimed : nullptr;
-  }
-  __device__ void emit(const Item& it, unsigned long long off) const {
-    if (mode != kFrontFinal) front[off] = make_uint2(it.w, it.bits);
-  }
-  __device__ void total(unsigned long long n) const {
-    if (mode != kFrontFinal) st->front_words = (uint32_t)n;
-  }
+  __device__ uint32_t count(const Item&) const { return 0u; }
+  __device__ uint32_t side(const Item& it, int k) const { return k == 0 ? __popc(it.bits) : 0u; }
+  __device__ unsigned long long* side_sum(int k) const { return k == 0 ? &st->front_n : nullptr; }
+  __device__ void emit(const Item&, unsigned long long) const {}
+  __device__ void total(unsigned long long) const {}
 };
 
 // The exact-target trim, once, after the step that overshot Nt.  The claim
@@ -318,8 +345,7 @@ struct TrimPolicy {
     }
     grid[it.w] &= ~drop;
   }
-  // front_n is recounted by the final front pass that follows.
-  __device__ void total(unsigned long long) const { st->front_n = 0; }
+  __device__ void total(unsigned long long) const {}
 };
 
 // Seeds: the accepted candidates in ascending order, capped at Nt, written
@@ -603,20 +629,22 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // The growth step (Sec. 2.3 step 3, Algorithm 3 lines 4-13).  Every front
 // voxel a tries each void in-domain neighbour q = a + e_d with the draw
 // word (d & 3) of Philox block (a, 0, t, 0x200 | d >> 2) against the class
-// threshold of Eq. 1; a success claims q with an atomicOr into the grid, and
-// the thread that flips the bit also records q in the claim grid.  Whether q
-// becomes solid depends only on the start-of-step front and the draws, never
-// on thread order: a thread that already sees q solid skips it, and q is
-// solid either way.
+// threshold of Eq. 1; a success records q in this step's claim grid with a
+// fire-and-forget atomicOr.  The occupancy grid is not written during the
+// kernel, so every thread sees the start-of-step grid: the front, the void
+// targets and the attempt count are those of Algorithm 3 exactly, and the
+// claim grid ends up holding New_t (the commit scan ORs it into the grid).
 //
-// Work layout.  A warp takes 32 entries of the front word list.  Phase 1:
-// each lane builds, bit-parallel over its 32 voxels, the 26 "void target"
-// masks V_d (bit i: voxel i is a front voxel, its d-neighbour is void and
-// inside the domain, and d's class has a positive threshold) and the 7
-// Philox-block masks B_b = OR of V_d over the directions of block b.
-// Phase 2: the lanes queue their (word, block, voxel) pairs in shared
-// memory, then the warp drains the queue one pair per lane -- one Philox
-// call per pair -- so no lane idles while another draws.
+// Work layout.  A warp takes 32 entries of the candidate word list (a
+// superset of the words holding front voxels).  Phase 1: each lane builds,
+// bit-parallel over its 32 voxels, the front bits (solid with a void
+// in-domain neighbour), the 26 "void target" masks V_d (bit i: voxel i is
+// solid, its d-neighbour is void and inside the domain, and d's class has a
+// positive threshold) and the 7 Philox-block masks B_b = OR of V_d over the
+// directions of block b; words that still hold front voxels are marked for
+// the next candidate list.  Phase 2: the lanes queue their (word, block,
+// voxel) pairs in shared memory, then the warp drains the queue one pair per
+// lane -- one Philox call per pair -- so no lane idles while another draws.
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
@@ -640,39 +668,46 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
 }
 
 // V masks of the three directions that land in row (y+DY, z+DZ).
+// V masks of the three directions that land in row (y+DY, z+DZ); `front`
+// collects every void neighbour, live class or not.
 template <int DZ, int DY>
-__device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* grid, uint32_t y,
-                                          uint32_t z, uint32_t r, uint32_t xw, uint32_t src,
-                                          uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7]) {
+__device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
+                                          uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
+                                          uint32_t self, uint32_t live_dirs, uint32_t (&V)[28],
+                                          uint32_t (&Bm)[7], uint32_t& front) {
   const int yy = (int)y + DY, zz = (int)z + DZ;
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
     const uint32_t* row = grid + (size_t)((int)r + DY + (int)g.ny * DZ) * g.W;
-    c = row[xw];
+    c = __ldg(row + xw);
     if (xw == g.W - 1) c |= g.pad_mask;
-    if (xw > 0) l = row[xw - 1];
+    if (xw > 0) l = __ldg(row + xw - 1);
     if (xw + 1 < g.W) {
-      rr = row[xw + 1];
+      rr = __ldg(row + xw + 1);
       if (xw + 1 == g.W - 1) rr |= g.pad_mask;
     }
   }
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
   const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
   constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
-  V[dm] = ~at_minus & src & (0u - ((live_dirs >> dm) & 1u));
+  const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
+  front |= vm | vp;
+  V[dm] = vm & (0u - ((live_dirs >> dm) & 1u));
   Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
-    V[d] = ~c & src & (0u - ((live_dirs >> (d & 31)) & 1u));
+    const uint32_t v0 = ~c & self;
+    front |= v0;
+    V[d] = v0 & (0u - ((live_dirs >> (d & 31)) & 1u));
     Bm[(d >> 2) % 7] |= V[d];
   }
-  V[dp] = ~at_plus & src & (0u - ((live_dirs >> dp) & 1u));
+  V[dp] = vp & (0u - ((live_dirs >> dp) & 1u));
   Bm[dp >> 2] |= V[dp];
 }
 
-__global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geom g, const uint2* __restrict__ front,
-                                                          uint32_t* grid, uint32_t* aux,
-                                                          RunState* st, const PhiloxKeys keys) {
+__global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
+    k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
+           uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys) {
   __shared__ GrowWarpSmem smem[kGrowWarps];
   __shared__ uint4 s_thr[7];  // per block, per direction: T - 1 (success iff r <= it)
   if (!st->active) return;
@@ -694,29 +729,33 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  uint32_t my_live = 0, my_draws = 0;
+  uint32_t my_live = 0, my_draws = 0, my_front = 0;
 
   for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
     // Phase 1: masks of this lane's word.
     uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
     const uint32_t idx = base + lane;
     if (idx < n) {
-      const uint2 e = front[idx];
-      const uint32_t w = e.x, src = e.y;
+      const uint32_t w = cand[idx];
+      const uint32_t self = __ldg(grid + w);
       const uint32_t r = fast_div(w, g.div_W);
       const uint32_t xw = w - r * g.W;
       const uint32_t z = fast_div(r, g.div_ny);
       const uint32_t y = r - z * g.ny;
       uint32_t V[28];
-      row_masks<-1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<-1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<-1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<0, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<0, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<0, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<1, -1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<1, 0>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
-      row_masks<1, 1>(g, grid, y, z, r, xw, src, live_dirs, V, Bm);
+      uint32_t front = 0;
+      row_masks<-1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<-1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<-1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<0, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<0, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<0, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      row_masks<1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+      my_front += __popc(front);
+      // A word holding front voxels now may hold some after the step too.
+      if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
       V[26] = 0;
       V[27] = 0;
 #pragma unroll
@@ -782,7 +821,6 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
           const size_t wq = (size_t)rq * g.W + (xx >> 5);
           const uint32_t bit = 1u << (xx & 31);
           // Fire-and-forget: the claim grid collects New_t; nobody waits.
-          atomicOr(grid + wq, bit);
           atomicOr(claims + wq, bit);
         }
       }
@@ -792,8 +830,10 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS) k_grow(Geo
   }
   const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
   const uint32_t wd = __reduce_add_sync(0xffffffffu, my_draws);
+  const uint32_t wf = __reduce_add_sync(0xffffffffu, my_front);
   if (lane == 0 && wl) atomicAdd(&st->live, (unsigned long long)wl);
   if (lane == 0 && wd) atomicAdd(&st->sum_draws, (unsigned long long)wd);
+  if (lane == 0 && wf) atomicAdd(&st->front_acc, (unsigned long long)wf);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,9 +983,10 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
               ctl);
   // Initial front (Sec. 2.3 step 2) replaces the candidate list.
-  FrontPolicy fp{g, b.st, b.grid, b.aux, reinterpret_cast<uint2*>(b.list), kFrontInitial};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
-              fp, ctl);
+  // Initial candidate words (Sec. 2.3 step 2) replace the candidate list.
+  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitInitial};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
+              cp, ctl);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, (cudaGraphConditionalHandle)0, 0);
   return cudaSuccess;
 }
@@ -954,11 +995,11 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
                         uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
                         cudaGraphConditionalHandle cond, int use_cond) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
-  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.front, b.grid, b.aux, b.st,
-              make_philox_keys((uint64_t)k1 << 32 | k0));
-  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, kFrontStep};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
-              fp, ctl);
+  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.list, b.grid, b.aux, b.mark,
+              b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitStep};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
+              cp, ctl);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);
   return cudaSuccess;
 }
@@ -969,9 +1010,10 @@ cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_l
   TrimPolicy tp{g, b.st, b.grid, b.aux};
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
               ctl);
-  FrontPolicy fp{g, b.st, b.grid, b.aux, b.front, kFrontFinal};
-  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontPolicy>, scan_grid(g.nwords), kScanThreads,
-              fp, ctl);
+  QSGS_LAUNCH(tr, kClsTrim, s, k_zero_front, 1, 1, b.st);
+  FrontCountPolicy fp{g, b.st, b.grid};
+  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontCountPolicy>, scan_grid(g.nwords),
+              kScanThreads, fp, ctl);
   QSGS_LAUNCH(tr, kClsTrim, s, k_trim_done, 1, 1, b.st);
   return cudaSuccess;
 }

@@ -13,7 +13,7 @@ namespace qsgs {
 // Kernel classes of the launch counter and the optional event profiler.
 enum KernelClass : int { kClsSeed, kClsGrow, kClsStepCtl, kClsTrim, kClsFront, kClsFetch, kNumClasses };
 inline const char* kernel_class_name(int c) {
-  static const char* names[kNumClasses] = {"seed", "grow", "step_ctl", "trim", "front", "fetch"};
+  static const char* names[kNumClasses] = {"seed", "grow", "step_ctl", "epilogue", "commit", "fetch"};
   return (c >= 0 && c < kNumClasses) ? names[c] : "?";
 }
 
@@ -112,7 +112,8 @@ struct SeedBuffers {
   unsigned long long* scan_status;
   uint32_t* grid;
   uint32_t* aux;
-  uint32_t* list;        // candidates, then the front
+  uint32_t* list;        // seed candidates, then the candidate word list
+  uint32_t* mark;        // one bit per word (growth kernel -> commit scan)
   uint32_t* cell_count;  // spacing only
   uint32_t* cell_start;
   uint32_t* cell_items;
@@ -127,8 +128,9 @@ struct StepBuffers {
   RunState* st;
   unsigned long long* scan_status;
   uint32_t* grid;
-  uint32_t* aux;  // two claim grids (step parity)
-  uint2* front;   // {word index, front bits} list
+  uint32_t* aux;   // two claim grids (step parity)
+  uint32_t* mark;  // one bit per word: still holds front voxels
+  uint32_t* list;  // candidate word list (ascending)
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
@@ -137,14 +139,14 @@ uint32_t default_grow_blocks();
 cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr);
 cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, cudaStream_t s, Tracer& tr);
-// One growth step: k_grow, the front rebuild (which also counts the
-// step's claims) and the step control.  With use_cond, the step control
+// One growth step: k_grow, the commit scan (claims into the grid, their
+// count, the next candidate list) and the step control.  With use_cond, the step control
 // also sets the graph conditional `cond` (while-loop body).
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
                         cudaGraphConditionalHandle cond, int use_cond);
-// Exact-target trim and final front count; no-ops unless the last step
-// overshot Nt.
+// Exact-target trim (a no-op unless the last step overshot Nt) and the
+// front count of the current grid.
 cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                             cudaStream_t s, Tracer& tr);
 cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
