@@ -446,6 +446,7 @@ int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, doubl
   const uint32_t blocks = (uint32_t)sms * 8u;  // 2048 threads per SM
   const uint64_t threads = (uint64_t)blocks * 256u;
   uint64_t per = (n_blocks + threads - 1) / threads;
+  per = (per + 3) & ~3ull;  // whole groups of independent blocks per thread
   if (per > 0xFFFFFFFFull) return QSGS_ERR_INVALID;
   cudaEvent_t a = nullptr, b = nullptr;
   e = cudaEventCreate(&a);

@@ -841,15 +841,26 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
 // distinct counters and folds them into one word, so nothing is optimised
 // away.  Its rate is the ALU ceiling the growth kernel is compared with.
 // ---------------------------------------------------------------------------
+#ifndef QSGS_PROBE_ILP
+#define QSGS_PROBE_ILP 2  // independent blocks in flight per thread
+#endif
 __global__ void __launch_bounds__(256) k_philox_rate(PhiloxKeys keys, uint32_t per_thread,
                                                      unsigned long long* out) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t acc = 0;
-  for (uint32_t k = 0; k < per_thread; ++k) {
-    const U4 r = philox4x32_10(U4{tid, 0u, k, kGrowTag}, keys);
-    acc ^= r.x ^ r.y ^ r.z ^ r.w;
+  uint32_t acc[QSGS_PROBE_ILP];
+#pragma unroll
+  for (int j = 0; j < QSGS_PROBE_ILP; ++j) acc[j] = 0;
+  for (uint32_t k = 0; k < per_thread; k += QSGS_PROBE_ILP) {
+#pragma unroll
+    for (int j = 0; j < QSGS_PROBE_ILP; ++j) {
+      const U4 r = philox4x32_10(U4{tid, 0u, k + j, kGrowTag}, keys);
+      acc[j] ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
   }
-  const uint32_t wsum = __reduce_add_sync(0xffffffffu, acc & 0xFFFFu);
+  uint32_t a = 0;
+#pragma unroll
+  for (int j = 0; j < QSGS_PROBE_ILP; ++j) a ^= acc[j];
+  const uint32_t wsum = __reduce_add_sync(0xffffffffu, a & 0xFFFFu);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, (unsigned long long)wsum);
 }
 
