@@ -202,6 +202,80 @@ int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, doubl
 /* Releases the handle (host memory only).  NULL is ignored. */
 void qsgs_destroy(qsgs_handle* h);
 
+/* Tuning knob: thread blocks of the growth kernel (0 = 8 per SM).  Results
+ * do not depend on it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
+int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
+
+/* ---- batches ------------------------------------------------------------
+ * A batch advances many realizations (its members: ordinary handles, each
+ * with its own workspace) with the same launches: one growth launch over
+ * the concatenation of all members' candidate lists, one commit scan over
+ * all members' words and one control kernel with a thread per member, per
+ * step, replayed from one CUDA graph until no member has a step left.
+ * Every member gets exactly the result it gets alone (its draws are keyed
+ * by its own seed, step and voxel).  The paper runs one realization at a
+ * time; batching serves the many realizations that uncertainty
+ * quantification needs (Sec. 1).
+ *
+ * Ownership: the caller owns the batch workspace (device) and stream and
+ * the member handles, which must outlive their membership.  A batch holds
+ * host metadata, a few events and kSeedStreams (8) private streams used to
+ * seed members concurrently. */
+typedef struct qsgs_batch qsgs_batch;
+
+/* Device workspace bytes for up to max_members (<= 1024) members whose
+ * words (nz*ny*ceil(nx/32) each, rounded up to 32) total at most max_words
+ * (< 2^32).  0 if the limits are invalid.  Host only. */
+size_t qsgs_batch_workspace_bytes(uint32_t max_members, uint64_t max_words);
+
+/* Creates an empty batch on a caller workspace (256-byte aligned) and
+ * stream (a non-default stream enables the CUDA graph).  Returns QSGS_OK,
+ * QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_NOMEM or QSGS_ERR_CUDA. */
+int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_workspace, size_t bytes,
+                      void* cuda_stream, qsgs_batch** out);
+
+/* Sets the members (host array of n seeded handles; replaces the previous
+ * set).  Members keep their run state: a member may join mid-run and leave
+ * mid-run (qsgs_grow_until on a handle that left rebuilds its candidate
+ * list first).  The batch stream waits for each member's own stream.
+ * Blocks until the member table is on the device.  Must not be called while
+ * an advance is in flight.  Returns QSGS_OK, QSGS_ERR_INVALID,
+ * QSGS_ERR_STATE (a member not seeded), QSGS_ERR_WORKSPACE (too many words)
+ * or QSGS_ERR_CUDA. */
+int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t n);
+
+/* Seeds (or re-seeds) every member, up to 8 at a time on private streams;
+ * the batch stream waits for all.  Asynchronous.  Returns QSGS_OK or an
+ * error. */
+int qsgs_batch_seed(qsgs_batch* b);
+
+/* Enqueues on the batch stream: every running member advances until it is
+ * done, stalls, hits its step limit or has run max_steps more steps (0 = no
+ * per-call limit).  Asynchronous; qsgs_batch_query waits.  Returns QSGS_OK
+ * or QSGS_ERR_CUDA. */
+int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps);
+
+/* Waits for the batch stream, runs the exact-target trim and the final
+ * front count of members whose run has ended, and fills per_member[0..n)
+ * (host array, may be NULL if n = 0) in member order.  Returns QSGS_OK,
+ * QSGS_ERR_TIMEOUT, QSGS_ERR_INVALID or QSGS_ERR_CUDA. */
+int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n);
+
+/* qsgs_batch_seed + qsgs_batch_advance + qsgs_batch_query. */
+int qsgs_batch_run(qsgs_batch* b, uint32_t max_steps, qsgs_stats* per_member, uint32_t n);
+
+/* Tuning knob: thread blocks of the batched growth kernel (0 = 8 per SM). */
+int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks);
+
+/* Event profiler of the batch's own launches (see qsgs_set_profiling);
+ * while on, advances use direct launches instead of the graph. */
+int qsgs_batch_set_profiling(qsgs_batch* b, int enable);
+int qsgs_batch_profile(qsgs_batch* b, qsgs_profile_entry* out, int max_entries);
+
+/* Releases the batch's host metadata, events and private streams (not the
+ * members or the workspace).  NULL is ignored. */
+void qsgs_batch_destroy(qsgs_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstddef>
 #include <new>
+#include <vector>
 
 #include "../../include/qsgs.h"
 #include "qsgs_launch.h"
@@ -128,6 +130,11 @@ struct qsgs_handle {
   cudaGraphExec_t graph_exec;
   bool graph_tried;
   uint32_t iters_seen;
+  // Set while a batch advances the realization: its own candidate list is
+  // out of date and is rebuilt before qsgs_grow_until continues alone.
+  bool list_stale;
+  // The exact-target epilogue has run since the run ended (batch members).
+  bool finalized;
 };
 
 namespace {
@@ -165,6 +172,34 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
 
 StepBuffers step_buffers(const qsgs_handle* h) {
   return StepBuffers{h->st, h->scan_status, h->grid, h->aux, h->mark, h->list};
+}
+
+// Seeding, spacing, the seed cap and the initial candidate list (Sec. 2.1
+// step 2, Sec. 2.3 steps 1-2), enqueued on `stream`.
+int seed_on_stream(qsgs_handle* h, cudaStream_t stream) {
+  const size_t grids = (size_t)h->g.nwords * 4;
+  cudaError_t e = cudaMemsetAsync(h->grid, 0, grids, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->mark, 0, (h->g.nwords / 32 + 1) * 4, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  StateInit init{};
+  init.nt = h->ints.nt;
+  for (int k = 0; k < 3; ++k) init.t_ref[k] = h->ints.t_ref[k];
+  init.t_seed = h->ints.t_seed;
+  init.max_steps = h->p.max_steps ? h->p.max_steps : 0xFFFFFFFFu;
+  e = launch_init_state(h->st, init, stream, h->tracer);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  SeedBuffers b{h->st,         h->scan_status, h->grid,     h->aux,
+                h->list,       h->mark,        h->cell_count,  h->cell_start, h->cell_items,
+                h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
+                h->L.cg};
+  e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, stream, h->tracer);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->seeded = true;
+  h->list_stale = false;
+  h->finalized = false;
+  h->iters_seen = 0;
+  return QSGS_OK;
 }
 
 void destroy_graph(qsgs_handle* h) {
@@ -212,6 +247,116 @@ cudaError_t build_graph(qsgs_handle* h) {
   if (le != cudaSuccess) return le;
   if (e != cudaSuccess) return e;
   return cudaGraphInstantiate(&h->graph_exec, h->graph, 0);
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSeedStreams = 8;  // members seeded concurrently
+
+struct BatchLayout {
+  size_t state, descs, scan_status, list, total;
+};
+
+BatchLayout make_batch_layout(uint32_t max_members, uint64_t max_words) {
+  BatchLayout L{};
+  size_t off = 0;
+  L.state = off; off = align_up(off + sizeof(BatchState));
+  L.descs = off; off = align_up(off + (size_t)max_members * sizeof(MemberDesc));
+  L.scan_status = off; off = align_up(off + (max_words / kScanTile + 2) * sizeof(unsigned long long));
+  L.list = off; off = align_up(off + (max_words ? max_words : 1) * 4);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct qsgs_batch {
+  uint32_t max_members;
+  uint64_t max_words;
+  BatchLayout L;
+  cudaStream_t stream;
+  uint8_t* ws;
+  BatchBuffers buf;
+  std::vector<qsgs_handle*> members;
+  std::vector<MemberDesc> host_descs;
+  std::vector<RunState> host_states;
+  uint32_t grow_blocks;
+  uint32_t iters_seen;
+  cudaGraph_t graph;
+  cudaGraphExec_t graph_exec;
+  bool graph_tried;
+  cudaStream_t seed_streams[kSeedStreams];
+  cudaEvent_t seed_events[kSeedStreams];
+  cudaEvent_t fork;
+  Tracer tracer;
+  cudaError_t last_cuda;
+};
+
+namespace {
+
+void destroy_batch_graph(qsgs_batch* b) {
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->graph_exec = nullptr;
+  b->graph = nullptr;
+}
+
+// [step limits, prologue commit, prologue control] then while (any member
+// active) { batched growth, commit, control }.  Nothing in it depends on
+// the membership, which the kernels read from the workspace.
+cudaError_t build_batch_graph(qsgs_batch* b) {
+  cudaError_t e = cudaGraphCreate(&b->graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle cond;
+  e = cudaGraphConditionalHandleCreate(&cond, b->graph, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  Tracer capture_tracer;
+  e = cudaStreamBeginCaptureToGraph(b->stream, b->graph, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = launch_batch_prologue(b->buf, kSpinLimit, b->stream, capture_tracer, cond, 1);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(b->stream, &captured);
+  if (le != cudaSuccess) return le;
+  if (e != cudaSuccess) return e;
+  // The loop node goes after everything captured so far.
+  size_t n_nodes = 0;
+  e = cudaGraphGetNodes(b->graph, nullptr, &n_nodes);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  e = cudaGraphGetNodes(b->graph, nodes.data(), &n_nodes);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> leaves;
+  for (auto nd : nodes) {
+    size_t n_out = 0;
+    e = cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &n_out);
+    if (e != cudaSuccess) return e;
+    if (n_out == 0) leaves.push_back(nd);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  e = cudaGraphAddNode(&loop, b->graph, leaves.data(), nullptr, leaves.size(), &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  le = launch_batch_step(b->buf, kSpinLimit, b->grow_blocks, b->stream, capture_tracer, cond, 1);
+  e = cudaStreamEndCapture(b->stream, &captured);
+  if (le != cudaSuccess) return le;
+  if (e != cudaSuccess) return e;
+  return cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+}
+
+int batch_fail(qsgs_batch* b, cudaError_t e) {
+  if (b) b->last_cuda = e;
+  return QSGS_ERR_CUDA;
 }
 
 }  // namespace
@@ -293,6 +438,8 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->graph_exec = nullptr;
   h->graph_tried = false;
   h->iters_seen = 0;
+  h->list_stale = false;
+  h->finalized = false;
   // The scan status words must start with flag 0; the run state is set by
   // qsgs_seed.
   cudaError_t e = cudaMemsetAsync(h->ws, 0, L.grid, h->stream);
@@ -306,35 +453,21 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
 
 int qsgs_seed(qsgs_handle* h) {
   if (!h) return QSGS_ERR_INVALID;
-  const size_t grids = (size_t)h->g.nwords * 4;
-  cudaError_t e = cudaMemsetAsync(h->grid, 0, grids, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->mark, 0, (h->g.nwords / 32 + 1) * 4, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e);
-  StateInit init{};
-  init.nt = h->ints.nt;
-  for (int k = 0; k < 3; ++k) init.t_ref[k] = h->ints.t_ref[k];
-  init.t_seed = h->ints.t_seed;
-  init.max_steps = h->p.max_steps ? h->p.max_steps : 0xFFFFFFFFu;
-  e = launch_init_state(h->st, init, h->stream, h->tracer);
-  if (e != cudaSuccess) return cuda_fail(h, e);
-  SeedBuffers b{h->st,         h->scan_status, h->grid,     h->aux,
-                h->list,       h->mark,        h->cell_count,  h->cell_start, h->cell_items,
-                h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
-                h->L.cg};
-  e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, h->stream, h->tracer);
-  if (e != cudaSuccess) return cuda_fail(h, e);
-  h->seeded = true;
-  h->iters_seen = 0;
-  return QSGS_OK;
+  return seed_on_stream(h, h->stream);
 }
 
 int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
   if (!h) return QSGS_ERR_INVALID;
   if (!h->seeded) return QSGS_ERR_STATE;
-  cudaError_t e = launch_set_step_limit(h->st, max_steps, h->stream, h->tracer);
-  if (e != cudaSuccess) return cuda_fail(h, e);
   const StepBuffers b = step_buffers(h);
+  cudaError_t e = cudaSuccess;
+  if (h->list_stale) {
+    e = launch_front_list(h->g, b, kSpinLimit, h->stream, h->tracer);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->list_stale = false;
+  }
+  e = launch_set_step_limit(h->st, max_steps, h->stream, h->tracer);
+  if (e != cudaSuccess) return cuda_fail(h, e);
   RunState s{};
   if (!h->tracer.enabled() && h->stream != nullptr && !h->graph_tried) {
     h->graph_tried = true;
@@ -471,6 +604,245 @@ void qsgs_destroy(qsgs_handle* h) {
   if (!h) return;
   destroy_graph(h);
   delete h;
+}
+
+
+size_t qsgs_batch_workspace_bytes(uint32_t max_members, uint64_t max_words) {
+  if (max_members == 0 || max_members > kMaxBatchMembers || max_words >= (1ull << 32)) return 0;
+  return make_batch_layout(max_members, max_words).total;
+}
+
+int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_workspace, size_t bytes,
+                      void* cuda_stream, qsgs_batch** out) {
+  if (!out) return QSGS_ERR_INVALID;
+  *out = nullptr;
+  if (max_members == 0 || max_members > kMaxBatchMembers || max_words >= (1ull << 32))
+    return QSGS_ERR_INVALID;
+  const BatchLayout L = make_batch_layout(max_members, max_words);
+  if (!dev_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
+    return QSGS_ERR_WORKSPACE;
+  qsgs_batch* b = new (std::nothrow) qsgs_batch();
+  if (!b) return QSGS_ERR_NOMEM;
+  b->max_members = max_members;
+  b->max_words = max_words;
+  b->L = L;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->ws = static_cast<uint8_t*>(dev_workspace);
+  b->buf = BatchBuffers{reinterpret_cast<MemberDesc*>(b->ws + L.descs),
+                        reinterpret_cast<BatchState*>(b->ws + L.state),
+                        reinterpret_cast<unsigned long long*>(b->ws + L.scan_status),
+                        reinterpret_cast<uint32_t*>(b->ws + L.list), max_members, max_words};
+  b->grow_blocks = default_grow_blocks();
+  b->iters_seen = 0;
+  b->graph = nullptr;
+  b->graph_exec = nullptr;
+  b->graph_tried = false;
+  b->last_cuda = cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->seed_streams[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->seed_events[k], cudaEventDisableTiming);
+  }
+  // State and scan tile words start at zero; no members yet.
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ws, 0, L.list, b->stream);
+  if (e != cudaSuccess) {
+    qsgs_batch_destroy(b);
+    return QSGS_ERR_CUDA;
+  }
+  *out = b;
+  return QSGS_OK;
+}
+
+int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t n) {
+  if (!b || (n && !members) || n > b->max_members) return QSGS_ERR_INVALID;
+  std::vector<MemberDesc> descs(n);
+  uint64_t words = 0;
+  for (uint32_t m = 0; m < n; ++m) {
+    qsgs_handle* h = members[m];
+    if (!h) return QSGS_ERR_INVALID;
+    if (!h->seeded) return QSGS_ERR_STATE;
+    MemberDesc& d = descs[m];
+    std::memset(&d, 0, sizeof(d));
+    d.g = h->g;
+    d.grid = h->grid;
+    d.aux = h->aux;
+    d.mark = h->mark;
+    d.st = h->st;
+    d.keys = make_philox_keys(h->p.seed);
+    d.word_base = (uint32_t)words;
+    d.word_end = (uint32_t)(words + h->g.nwords);
+    words += ((uint64_t)h->g.nwords + 31) / 32 * 32;
+  }
+  if (words > b->max_words) return QSGS_ERR_WORKSPACE;
+  // The batch stream waits for each member's own stream (its seeding).
+  cudaError_t e = cudaSuccess;
+  for (uint32_t m = 0; m < n && e == cudaSuccess; ++m) {
+    if (members[m]->stream == b->stream) continue;
+    e = cudaEventRecord(b->fork, members[m]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->fork, 0);
+  }
+  if (e == cudaSuccess && n)
+    e = cudaMemcpyAsync(b->buf.d, descs.data(), n * sizeof(MemberDesc), cudaMemcpyHostToDevice,
+                        b->stream);
+  uint32_t sizes[2] = {n, (uint32_t)words};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(reinterpret_cast<uint8_t*>(b->buf.bs) + offsetof(BatchState, n_members),
+                        sizes, sizeof(sizes), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host copies are staged
+  if (e != cudaSuccess) return batch_fail(b, e);
+  b->members.assign(members, members + n);
+  b->host_descs = descs;
+  for (qsgs_handle* h : b->members) h->list_stale = true;
+  return QSGS_OK;
+}
+
+int qsgs_batch_seed(qsgs_batch* b) {
+  if (!b) return QSGS_ERR_INVALID;
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->seed_streams[k], b->fork, 0);
+  if (e != cudaSuccess) return batch_fail(b, e);
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    const int rc = seed_on_stream(b->members[m], b->seed_streams[m % kSeedStreams]);
+    if (rc != QSGS_OK) return rc;
+    b->members[m]->list_stale = true;
+  }
+  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->seed_events[k], b->seed_streams[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->seed_events[k], 0);
+  }
+  if (e != cudaSuccess) return batch_fail(b, e);
+  return QSGS_OK;
+}
+
+int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps) {
+  if (!b) return QSGS_ERR_INVALID;
+  if (b->members.empty()) return QSGS_OK;
+  cudaError_t e = cudaMemcpyAsync(
+      reinterpret_cast<uint8_t*>(b->buf.bs) + offsetof(BatchState, step_extra), &max_steps,
+      sizeof(max_steps), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return batch_fail(b, e);
+  if (!b->tracer.enabled() && b->stream != nullptr && !b->graph_tried) {
+    b->graph_tried = true;
+    if (build_batch_graph(b) != cudaSuccess) {
+      destroy_batch_graph(b);
+      (void)cudaGetLastError();
+    }
+  }
+  if (!b->tracer.enabled() && b->graph_exec) {
+    e = cudaGraphLaunch(b->graph_exec, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    return QSGS_OK;
+  }
+  e = launch_batch_prologue(b->buf, kSpinLimit, b->stream, b->tracer,
+                            (cudaGraphConditionalHandle)0, 0);
+  if (e != cudaSuccess) return batch_fail(b, e);
+  for (;;) {
+    for (uint32_t k = 0; k < kStepsPerSync; ++k) {
+      e = launch_batch_step(b->buf, kSpinLimit, b->grow_blocks, b->stream, b->tracer,
+                            (cudaGraphConditionalHandle)0, 0);
+      if (e != cudaSuccess) return batch_fail(b, e);
+    }
+    uint32_t any = 0;
+    e = cudaMemcpyAsync(&any, reinterpret_cast<uint8_t*>(b->buf.bs) + offsetof(BatchState, any_active),
+                        sizeof(any), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = b->tracer.collect();
+    if (e != cudaSuccess) return batch_fail(b, e);
+    if (!any) break;
+  }
+  return QSGS_OK;
+}
+
+int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n) {
+  if (!b || (n && !per_member)) return QSGS_ERR_INVALID;
+  const size_t nm = b->members.size();
+  b->host_states.resize(nm);
+  auto read_all = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (size_t m = 0; m < nm && e == cudaSuccess; ++m)
+      e = cudaMemcpyAsync(&b->host_states[m], b->members[m]->st, sizeof(RunState),
+                          cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e;
+  };
+  cudaError_t e = read_all();
+  if (e != cudaSuccess) return batch_fail(b, e);
+  // Members whose run ended: exact-target trim and final front count, once.
+  bool any_final = false;
+  for (size_t m = 0; m < nm; ++m) {
+    qsgs_handle* h = b->members[m];
+    if (b->host_states[m].status != kRunning && !h->finalized) {
+      e = launch_epilogue(h->g, step_buffers(h), kSpinLimit, b->stream, h->tracer);
+      if (e != cudaSuccess) return batch_fail(b, e);
+      h->finalized = true;
+      any_final = true;
+    }
+  }
+  if (any_final) {
+    e = read_all();
+    if (e != cudaSuccess) return batch_fail(b, e);
+  }
+  int rc = QSGS_OK;
+  for (size_t m = 0; m < nm; ++m) {
+    if (b->host_states[m].error & kErrTimeout) rc = QSGS_ERR_TIMEOUT;
+    if (m < n) fill_stats(b->members[m], b->host_states[m], &per_member[m]);
+  }
+  return rc;
+}
+
+int qsgs_batch_run(qsgs_batch* b, uint32_t max_steps, qsgs_stats* per_member, uint32_t n) {
+  int rc = qsgs_batch_seed(b);
+  if (rc == QSGS_OK) rc = qsgs_batch_advance(b, max_steps);
+  if (rc == QSGS_OK) rc = qsgs_batch_query(b, per_member, n);
+  return rc;
+}
+
+int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
+  if (!b) return QSGS_ERR_INVALID;
+  b->grow_blocks = blocks ? blocks : default_grow_blocks();
+  destroy_batch_graph(b);  // the grid size is baked into the graph
+  b->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks) {
+  if (!h) return QSGS_ERR_INVALID;
+  h->grow_blocks = blocks ? blocks : default_grow_blocks();
+  destroy_graph(h);
+  h->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_batch_set_profiling(qsgs_batch* b, int enable) {
+  if (!b) return QSGS_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = b->tracer.collect();
+  if (e == cudaSuccess) e = b->tracer.enable(enable != 0);
+  if (e != cudaSuccess) return batch_fail(b, e);
+  return QSGS_OK;
+}
+
+int qsgs_batch_profile(qsgs_batch* b, qsgs_profile_entry* out, int max_entries) {
+  if (!b || max_entries < 0 || (max_entries > 0 && !out)) return QSGS_ERR_INVALID;
+  for (int c = 0; c < kNumClasses && c < max_entries; ++c) {
+    std::memset(out[c].name, 0, sizeof(out[c].name));
+    std::strncpy(out[c].name, kernel_class_name(c), sizeof(out[c].name) - 1);
+    out[c].launches = b->tracer.count[c];
+    out[c].total_ms = b->tracer.ms[c];
+  }
+  return kNumClasses;
+}
+
+void qsgs_batch_destroy(qsgs_batch* b) {
+  if (!b) return;
+  destroy_batch_graph(b);
+  for (uint32_t k = 0; k < kSeedStreams; ++k) {
+    if (b->seed_streams[k]) cudaStreamDestroy(b->seed_streams[k]);
+    if (b->seed_events[k]) cudaEventDestroy(b->seed_events[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
 }
 
 }  // extern "C"

@@ -245,4 +245,41 @@ struct alignas(256) RunState {
   uint32_t scan_done;            // look-back scan blocks finished
 };
 
+// ---------------------------------------------------------------------------
+// Batches: many realizations advanced by the same launches.  Member m's
+// words occupy [word_base, word_base + nwords) of a batch word space whose
+// ranges start at multiples of 32, so the 32 lanes of a warp that scan 32
+// consecutive batch words always serve one member.  The batch candidate
+// list is the concatenation of the members' candidate lists (local word
+// indices); member m's entries start at list_base.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMaxBatchMembers = 1024;  // one control block, thread per member
+
+struct alignas(16) MemberDesc {
+  Geom g;
+  uint32_t* grid;
+  uint32_t* aux;        // two claim grids
+  uint32_t* mark;
+  RunState* st;
+  PhiloxKeys keys;
+  uint32_t word_base;   // first batch word (multiple of 32)
+  uint32_t word_end;    // word_base + nwords
+  uint32_t list_base;   // first entry in the batch candidate list
+  uint32_t list_n;      // entries of this member
+  uint32_t chunk_base;  // first growth chunk (32 entries) of this member
+  uint32_t pad_[3];
+};
+
+struct BatchState {
+  RunState scan;          // look-back scan control (epoch, dispenser, error)
+  uint32_t n_members;
+  uint32_t total_words;   // end of the batch word space
+  uint32_t list_total;    // entries of the batch candidate list
+  uint32_t total_chunks;  // growth chunks of this step
+  uint32_t any_active;    // some member runs the next step
+  uint32_t step_extra;    // per-member step budget of the current advance (0: none)
+  uint32_t pad_[2];
+};
+
 }  // namespace qsgs
+

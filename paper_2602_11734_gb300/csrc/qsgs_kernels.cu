@@ -78,14 +78,12 @@ __device__ void begin_step(RunState* st) {
   st->active = 1;
 }
 
-// Closes the step that just ran (if one did) and opens the next.  A step
-// without a single attempt of positive probability is a fixed point:
-// stalled, not counted.  Otherwise the claims counted by the front rebuild
-// are added; if they overshoot Nt the solid count is capped and the
-// exact-target trim is left pending (the run ends with this step).  With a
-// graph conditional handle, also tells the enclosing while loop whether to
-// go on.
-__global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, int use_cond) {
+// Closes the step that just ran (if one did).  A step without a single
+// attempt of positive probability is a fixed point: stalled, not counted.
+// Otherwise the claims counted by the commit scan are added; if they
+// overshoot Nt the solid count is capped and the exact-target trim is left
+// pending (the run ends with this step).
+__device__ void close_step(RunState* st) {
   if (st->active) {
     if (st->live == 0) {
       st->status = kStatusStalled;
@@ -108,11 +106,17 @@ __global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, in
   st->claimed = 0;
   st->live = 0;
   st->iters += 1;
+}
+
+// Closes the step that just ran and opens the next.  With a graph
+// conditional handle, also tells the enclosing while loop whether to go on.
+__global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  close_step(st);
   begin_step(st);
   if (use_cond) cudaGraphSetConditional(cond, st->active ? 1u : 0u);
 }
 
-__global__ void k_set_step_limit(RunState* st, uint32_t extra) {
+__device__ void set_step_limit(RunState* st, uint32_t extra) {
   if (extra == 0) {
     st->step_limit = 0xFFFFFFFFu;
   } else {
@@ -121,6 +125,8 @@ __global__ void k_set_step_limit(RunState* st, uint32_t extra) {
   }
   begin_step(st);
 }
+
+__global__ void k_set_step_limit(RunState* st, uint32_t extra) { set_step_limit(st, extra); }
 
 __global__ void k_trim_done(RunState* st) { st->trim_pending = 0; }
 
@@ -705,136 +711,171 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
   Bm[dp >> 2] |= V[dp];
 }
 
+struct GrowCounters {
+  uint32_t live, draws, front;
+};
+
+// Per-direction thresholds of one instance as T - 1 (a draw succeeds iff
+// r <= T - 1), grouped by Philox block, and the mask of live directions
+// (classes with T > 0).  Written by lanes 0..27 of a warp or block.
+__device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr) {
+  if (lane < 28) {
+    const int d = (int)lane;
+    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
+    reinterpret_cast<uint32_t*>(thr)[d] = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+  }
+}
+
+__device__ __forceinline__ uint32_t live_directions(const RunState* st) {
+  uint32_t live_dirs = 0;
+#pragma unroll
+  for (int d = 0; d < 26; ++d)
+    if (st->thr[dir_cls(d)] != 0) live_dirs |= 1u << d;
+  return live_dirs;
+}
+
+// One warp, one chunk of up to 32 candidate words (w = 0xFFFFFFFF: no word
+// for this lane).  All 32 lanes must call it together.
+__device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
+                                           uint32_t* claims, uint32_t* mark, uint32_t w,
+                                           uint32_t t, uint32_t live_dirs, const uint4* thr,
+                                           const PhiloxKeys& keys, GrowWarpSmem& S,
+                                           GrowCounters& cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  // Phase 1: masks of this lane's word.
+  uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (w != 0xFFFFFFFFu) {
+    const uint32_t self = __ldg(grid + w);
+    const uint32_t r = fast_div(w, g.div_W);
+    const uint32_t xw = w - r * g.W;
+    const uint32_t z = fast_div(r, g.div_ny);
+    const uint32_t y = r - z * g.ny;
+    uint32_t V[28];
+    uint32_t front = 0;
+    row_masks<-1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<-1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<-1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<0, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<0, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<0, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    row_masks<1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    cnt.front += __popc(front);
+    // A word holding front voxels now may hold some after the step too.
+    if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
+    V[26] = 0;
+    V[27] = 0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
+    S.r[lane] = r;
+    S.xw[lane] = xw;
+    S.v0[lane] = r * g.nx + xw * 32u;
+  }
+  uint32_t items = 0;
+#pragma unroll
+  for (int b = 0; b < 7; ++b) items += __popc(Bm[b]);
+  uint32_t incl = items;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  const uint32_t excl = incl - items;
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+
+  // Phase 2: drain in rounds of at most kGrowQueue pairs (whole words).
+  uint32_t done = 0;  // pairs of the lanes already drained
+  while (done < total) {
+    // Lanes whose pairs all fit into this round.
+    const bool fits = excl >= done && incl - done <= (uint32_t)kGrowQueue;
+    const uint32_t fit_mask = __ballot_sync(0xffffffffu, fits && items > 0);
+    uint32_t round_end = done;
+    if (fit_mask) round_end = __shfl_sync(0xffffffffu, incl, 31 - __clz(fit_mask));
+    if (fits && items > 0) {
+      uint32_t pos = excl - done;
+#pragma unroll
+      for (int b = 0; b < 7; ++b) {
+        uint32_t m = Bm[b];
+        while (m) {
+          const uint32_t i = __ffs(m) - 1;
+          m &= m - 1;
+          S.Q[pos++] = (uint16_t)((lane << 8) | (b << 5) | i);
+        }
+      }
+    }
+    __syncwarp();
+    const uint32_t round_n = round_end - done;
+    for (uint32_t k = lane; k < round_n; k += 32) {
+      const uint32_t e = S.Q[k];
+      const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
+      const uint32_t v = S.v0[owner] + i;
+      const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
+      ++cnt.draws;
+      const uint4 vm = S.V[owner][b];
+      const uint32_t vb = ((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
+                          (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3);
+      cnt.live += __popc(vb);
+      const uint4 th = thr[b];
+      uint32_t win = (rnd.x <= th.x ? 1u : 0u) | (rnd.y <= th.y ? 2u : 0u) |
+                     (rnd.z <= th.z ? 4u : 0u) | (rnd.w <= th.w ? 8u : 0u);
+      win &= vb;
+      while (win) {
+        const uint32_t j = __ffs(win) - 1;
+        win &= win - 1;
+        const int d = (int)(4u * b + j);
+        const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
+        const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
+        const size_t wq = (size_t)rq * g.W + (xx >> 5);
+        // Fire-and-forget: the claim grid collects New_t; nobody waits.
+        atomicOr(claims + wq, 1u << (xx & 31));
+      }
+    }
+    __syncwarp();  // S.Q is refilled by the next round
+    done = round_end;
+  }
+}
+
+__device__ __forceinline__ void flush_counters(RunState* st, GrowCounters& c) {
+  const uint32_t wl = __reduce_add_sync(0xffffffffu, c.live);
+  const uint32_t wd = __reduce_add_sync(0xffffffffu, c.draws);
+  const uint32_t wf = __reduce_add_sync(0xffffffffu, c.front);
+  if ((threadIdx.x & 31) == 0) {
+    if (wl) atomicAdd(&st->live, (unsigned long long)wl);
+    if (wd) atomicAdd(&st->sum_draws, (unsigned long long)wd);
+    if (wf) atomicAdd(&st->front_acc, (unsigned long long)wf);
+  }
+  c = GrowCounters{0, 0, 0};
+}
+
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
            uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys) {
   __shared__ GrowWarpSmem smem[kGrowWarps];
-  __shared__ uint4 s_thr[7];  // per block, per direction: T - 1 (success iff r <= it)
+  __shared__ uint4 s_thr[7];
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
-  uint32_t live_dirs = 0;
-#pragma unroll
-  for (int d = 0; d < 26; ++d) {
-    const int c = dir_cls(d);
-    if (st->thr[c] != 0) live_dirs |= 1u << d;
-  }
-  if (threadIdx.x < 28) {
-    const int d = threadIdx.x;
-    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
-    reinterpret_cast<uint32_t*>(s_thr)[d] = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
-  }
+  const uint32_t live_dirs = live_directions(st);
+  load_thresholds(st, threadIdx.x, s_thr);
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  GrowWarpSmem& S = smem[warp];
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  uint32_t my_live = 0, my_draws = 0, my_front = 0;
-
+  GrowCounters cnt{0, 0, 0};
   for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
-    // Phase 1: masks of this lane's word.
-    uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
     const uint32_t idx = base + lane;
-    if (idx < n) {
-      const uint32_t w = cand[idx];
-      const uint32_t self = __ldg(grid + w);
-      const uint32_t r = fast_div(w, g.div_W);
-      const uint32_t xw = w - r * g.W;
-      const uint32_t z = fast_div(r, g.div_ny);
-      const uint32_t y = r - z * g.ny;
-      uint32_t V[28];
-      uint32_t front = 0;
-      row_masks<-1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<-1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<-1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<0, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<0, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<0, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      row_masks<1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-      my_front += __popc(front);
-      // A word holding front voxels now may hold some after the step too.
-      if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
-      V[26] = 0;
-      V[27] = 0;
-#pragma unroll
-      for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
-      S.r[lane] = r;
-      S.xw[lane] = xw;
-      S.v0[lane] = r * g.nx + xw * 32u;
-    }
-    uint32_t items = 0;
-#pragma unroll
-    for (int b = 0; b < 7; ++b) items += __popc(Bm[b]);
-    uint32_t incl = items;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= (uint32_t)o) incl += y;
-    }
-    const uint32_t excl = incl - items;
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-
-    // Phase 2: drain in rounds of at most kGrowQueue pairs (whole words).
-    uint32_t done = 0;  // pairs of the lanes already drained
-    while (done < total) {
-      // Lanes whose pairs all fit into this round.
-      const bool fits = excl >= done && incl - done <= (uint32_t)kGrowQueue;
-      const uint32_t fit_mask = __ballot_sync(0xffffffffu, fits && items > 0);
-      uint32_t round_end = done;
-      if (fit_mask) round_end = __shfl_sync(0xffffffffu, incl, 31 - __clz(fit_mask));
-      if (fits && items > 0) {
-        uint32_t pos = excl - done;
-#pragma unroll
-        for (int b = 0; b < 7; ++b) {
-          uint32_t m = Bm[b];
-          while (m) {
-            const uint32_t i = __ffs(m) - 1;
-            m &= m - 1;
-            S.Q[pos++] = (uint16_t)((lane << 8) | (b << 5) | i);
-          }
-        }
-      }
-      __syncwarp();
-      const uint32_t round_n = round_end - done;
-      for (uint32_t k = lane; k < round_n; k += 32) {
-        const uint32_t e = S.Q[k];
-        const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
-        const uint32_t v = S.v0[owner] + i;
-        const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
-        ++my_draws;
-        const uint4 vm = S.V[owner][b];
-        const uint32_t vb = ((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
-                            (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3);
-        my_live += __popc(vb);
-        const uint4 th = s_thr[b];
-        uint32_t win = (rnd.x <= th.x ? 1u : 0u) | (rnd.y <= th.y ? 2u : 0u) |
-                       (rnd.z <= th.z ? 4u : 0u) | (rnd.w <= th.w ? 8u : 0u);
-        win &= vb;
-        while (win) {
-          const uint32_t j = __ffs(win) - 1;
-          win &= win - 1;
-          const int d = (int)(4u * b + j);
-          const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
-          const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
-          const size_t wq = (size_t)rq * g.W + (xx >> 5);
-          const uint32_t bit = 1u << (xx & 31);
-          // Fire-and-forget: the claim grid collects New_t; nobody waits.
-          atomicOr(claims + wq, bit);
-        }
-      }
-      __syncwarp();  // S.Q is refilled by the next round
-      done = round_end;
-    }
+    const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
+    grow_chunk(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
   }
-  const uint32_t wl = __reduce_add_sync(0xffffffffu, my_live);
-  const uint32_t wd = __reduce_add_sync(0xffffffffu, my_draws);
-  const uint32_t wf = __reduce_add_sync(0xffffffffu, my_front);
-  if (lane == 0 && wl) atomicAdd(&st->live, (unsigned long long)wl);
-  if (lane == 0 && wd) atomicAdd(&st->sum_draws, (unsigned long long)wd);
-  if (lane == 0 && wf) atomicAdd(&st->front_acc, (unsigned long long)wf);
+  flush_counters(st, cnt);
 }
+
+}  // namespace qsgs
+
+#include "qsgs_batch.cuh"
+
+namespace qsgs {
 
 // ---------------------------------------------------------------------------
 // Philox throughput probe: every thread draws `per_thread` blocks with
@@ -1047,4 +1088,39 @@ cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, 
 
 uint32_t default_grow_blocks() { return (uint32_t)num_sms() * 8; }
 
+cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
+                              cudaStream_t s, Tracer& tr) {
+  ScanCtl ctl{b.st, b.scan_status, spin_limit};
+  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitInitial};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
+              cp, ctl);
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
+                                  Tracer& tr, cudaGraphConditionalHandle cond, int use_cond) {
+  ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_limits, (b.max_members + 255) / 256, 256, b.d, b.bs);
+  BatchCommitPolicy cp{b.d, b.bs, b.list, 1};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<BatchCommitPolicy>, scan_grid(b.max_words),
+              kScanThreads, cp, ctl);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
+              1);
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32_t grow_blocks,
+                              cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
+                              int use_cond) {
+  ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};
+  QSGS_LAUNCH(tr, kClsGrow, s, k_grow_batch, grow_blocks, kGrowThreads, b.d, b.bs, b.list);
+  BatchCommitPolicy cp{b.d, b.bs, b.list, 0};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<BatchCommitPolicy>, scan_grid(b.max_words),
+              kScanThreads, cp, ctl);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
+              0);
+  return cudaSuccess;
+}
+
 }  // namespace qsgs
+

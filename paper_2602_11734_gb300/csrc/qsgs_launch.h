@@ -150,6 +150,28 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
 cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                             cudaStream_t s, Tracer& tr);
 cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
+// Rebuilds a realization's candidate list from its grid (all solid words).
+cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
+                              cudaStream_t s, Tracer& tr);
+
+struct BatchBuffers {
+  MemberDesc* d;
+  BatchState* bs;
+  unsigned long long* scan_status;
+  uint32_t* list;
+  uint32_t max_members;
+  uint64_t max_words;
+};
+
+// Batch step limits, prologue commit (lists every running member's solid
+// words) and prologue control (which sets the loop condition `cond` when
+// use_cond is set).
+cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
+                                  Tracer& tr, cudaGraphConditionalHandle cond, int use_cond);
+// One step of every member that runs: batched growth, commit and control.
+cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32_t grow_blocks,
+                              cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
+                              int use_cond);
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
                                unsigned long long* out, cudaStream_t s);
 cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,

@@ -93,6 +93,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_bench_philox": ([ctypes.c_uint64, vp, vp, ctypes.POINTER(ctypes.c_double)],
                                       ctypes.c_int),
                 "qsgs_destroy": ([H], None),
+                "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_workspace_bytes": ([ctypes.c_uint32, ctypes.c_uint64], ctypes.c_size_t),
+                "qsgs_batch_create": ([ctypes.c_uint32, ctypes.c_uint64, vp, ctypes.c_size_t, vp,
+                                       ctypes.POINTER(H)], ctypes.c_int),
+                "qsgs_batch_set_members": ([H, ctypes.POINTER(H), ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_seed": ([H], ctypes.c_int),
+                "qsgs_batch_advance": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_query": ([H, S, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_run": ([H, ctypes.c_uint32, S, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_set_profiling": ([H, ctypes.c_int], ctypes.c_int),
+                "qsgs_batch_profile": ([H, ctypes.POINTER(QsgsProfileEntry), ctypes.c_int],
+                                       ctypes.c_int),
+                "qsgs_batch_destroy": ([H], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -203,6 +217,70 @@ def qsgs_destroy(h) -> None:
         load_library().qsgs_destroy(h)
 
 
+def qsgs_set_grow_blocks(h, blocks: int) -> None:
+    rc = load_library().qsgs_set_grow_blocks(h, blocks)
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_set_grow_blocks")
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise QsgsError(rc, where)
+    return rc
+
+
+def qsgs_batch_workspace_bytes(max_members: int, max_words: int) -> int:
+    return int(load_library().qsgs_batch_workspace_bytes(max_members, max_words))
+
+
+def qsgs_batch_create(max_members: int, max_words: int, workspace_ptr: int, nbytes: int,
+                      stream_ptr: int):
+    b = ctypes.c_void_p()
+    _check(load_library().qsgs_batch_create(max_members, max_words, ctypes.c_void_p(workspace_ptr),
+                                            nbytes, ctypes.c_void_p(stream_ptr), ctypes.byref(b)),
+           "qsgs_batch_create")
+    return b
+
+
+def qsgs_batch_set_members(b, handles) -> None:
+    arr = (ctypes.c_void_p * max(1, len(handles)))(*[h.value for h in handles])
+    _check(load_library().qsgs_batch_set_members(b, arr, len(handles)), "qsgs_batch_set_members")
+
+
+def qsgs_batch_seed(b) -> None:
+    _check(load_library().qsgs_batch_seed(b), "qsgs_batch_seed")
+
+
+def qsgs_batch_advance(b, max_steps: int = 0) -> None:
+    _check(load_library().qsgs_batch_advance(b, max_steps), "qsgs_batch_advance")
+
+
+def qsgs_batch_query(b, n: int) -> list[dict]:
+    arr = (QsgsStats * max(1, n))()
+    _check(load_library().qsgs_batch_query(b, arr, n), "qsgs_batch_query")
+    return [arr[i].as_dict() for i in range(n)]
+
+
+def qsgs_batch_set_grow_blocks(b, blocks: int) -> None:
+    _check(load_library().qsgs_batch_set_grow_blocks(b, blocks), "qsgs_batch_set_grow_blocks")
+
+
+def qsgs_batch_set_profiling(b, enable: bool) -> None:
+    _check(load_library().qsgs_batch_set_profiling(b, int(enable)), "qsgs_batch_set_profiling")
+
+
+def qsgs_batch_profile(b) -> dict:
+    buf = (QsgsProfileEntry * 16)()
+    n = _check(load_library().qsgs_batch_profile(b, buf, 16), "qsgs_batch_profile")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(min(n, 16))}
+
+
+def qsgs_batch_destroy(b) -> None:
+    if b:
+        load_library().qsgs_batch_destroy(b)
+
+
 # ---- convenience wrapper ---------------------------------------------------
 @dataclass
 class Stats:
@@ -273,9 +351,79 @@ class Generator:
     def profile(self) -> dict:
         return qsgs_profile(self.handle)
 
+    def set_grow_blocks(self, blocks: int) -> None:
+        qsgs_set_grow_blocks(self.handle, blocks)
+
     def close(self) -> None:
         if getattr(self, "handle", None):
             qsgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def word_count(params: dict) -> int:
+    """Occupancy-grid words of a realization, rounded up to 32 (its share
+    of a batch word space)."""
+    p = make_params(params)
+    words = ((p.nx + 31) // 32) * p.ny * p.nz
+    return (words + 31) // 32 * 32
+
+
+class Batch:
+    """Many realizations advanced by the same launches (see qsgs.h)."""
+
+    def __init__(self, max_members: int, max_words: int, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqsgs needs a CUDA device; there is no CPU fallback")
+        load_library()
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.nbytes = qsgs_batch_workspace_bytes(max_members, max_words)
+        if self.nbytes == 0:
+            raise QsgsError(QSGS_ERR_INVALID, "qsgs_batch_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.handle = qsgs_batch_create(max_members, max_words, self.workspace.data_ptr(),
+                                            self.nbytes, self.stream.cuda_stream)
+        self.members: list[Generator] = []
+
+    def set_members(self, generators) -> None:
+        self.members = list(generators)
+        qsgs_batch_set_members(self.handle, [g.handle for g in self.members])
+
+    def seed(self) -> None:
+        qsgs_batch_seed(self.handle)
+
+    def advance(self, max_steps: int = 0) -> None:
+        qsgs_batch_advance(self.handle, max_steps)
+
+    def query(self) -> list[Stats]:
+        return [Stats(**d) for d in qsgs_batch_query(self.handle, len(self.members))]
+
+    def run(self, max_steps: int = 0) -> list[Stats]:
+        self.seed()
+        self.advance(max_steps)
+        return self.query()
+
+    def set_grow_blocks(self, blocks: int) -> None:
+        qsgs_batch_set_grow_blocks(self.handle, blocks)
+
+    def set_profiling(self, enable: bool = True) -> None:
+        qsgs_batch_set_profiling(self.handle, enable)
+
+    def profile(self) -> dict:
+        return qsgs_batch_profile(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            qsgs_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
