@@ -234,14 +234,12 @@ size_t qsgs_batch_workspace_bytes(uint32_t max_members, uint64_t max_words);
 int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_workspace, size_t bytes,
                       void* cuda_stream, qsgs_batch** out);
 
-/* Sets the members (host array of n seeded handles; replaces the previous
- * set).  Members keep their run state: a member may join mid-run and leave
+/* Sets the members (host array of n handles; replaces the previous set).  Members keep their run state: a member may join mid-run and leave
  * mid-run (qsgs_grow_until on a handle that left rebuilds its candidate
  * list first).  The batch stream waits for each member's own stream.
  * Blocks until the member table is on the device.  Must not be called while
  * an advance is in flight.  Returns QSGS_OK, QSGS_ERR_INVALID,
- * QSGS_ERR_STATE (a member not seeded), QSGS_ERR_WORKSPACE (too many words)
- * or QSGS_ERR_CUDA. */
+ * QSGS_ERR_WORKSPACE (too many words) or QSGS_ERR_CUDA. */
 int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t n);
 
 /* Seeds (or re-seeds) every member, up to 8 at a time on private streams;
@@ -251,8 +249,8 @@ int qsgs_batch_seed(qsgs_batch* b);
 
 /* Enqueues on the batch stream: every running member advances until it is
  * done, stalls, hits its step limit or has run max_steps more steps (0 = no
- * per-call limit).  Asynchronous; qsgs_batch_query waits.  Returns QSGS_OK
- * or QSGS_ERR_CUDA. */
+ * per-call limit).  Asynchronous; qsgs_batch_query waits.  Returns QSGS_OK,
+ * QSGS_ERR_STATE (a member not seeded) or QSGS_ERR_CUDA. */
 int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps);
 
 /* Waits for the batch stream, runs the exact-target trim and the final

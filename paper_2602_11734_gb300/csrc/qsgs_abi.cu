@@ -660,7 +660,6 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   for (uint32_t m = 0; m < n; ++m) {
     qsgs_handle* h = members[m];
     if (!h) return QSGS_ERR_INVALID;
-    if (!h->seeded) return QSGS_ERR_STATE;
     MemberDesc& d = descs[m];
     std::memset(&d, 0, sizeof(d));
     d.g = h->g;
@@ -718,6 +717,8 @@ int qsgs_batch_seed(qsgs_batch* b) {
 int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps) {
   if (!b) return QSGS_ERR_INVALID;
   if (b->members.empty()) return QSGS_OK;
+  for (qsgs_handle* h : b->members)
+    if (!h->seeded) return QSGS_ERR_STATE;
   cudaError_t e = cudaMemcpyAsync(
       reinterpret_cast<uint8_t*>(b->buf.bs) + offsetof(BatchState, step_extra), &max_steps,
       sizeof(max_steps), cudaMemcpyHostToDevice, b->stream);
