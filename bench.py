@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help=">= 1")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
     return ap.parse_args()
 
 
@@ -148,6 +149,61 @@ def run_reference(a):
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
     return 0
+
+
+def bench_batch(Q, torch, dev, repeats: int = 2) -> dict:
+    """96 uneven realizations (edge 128..256, porosity U[0.10,0.30], spacing
+    U{10..40}, cd 2e-4) advanced as one batch, against the same 96 run one
+    after another on the single-realization path.  Device time of seeding
+    through the exact target, L2 flushed before each timed run."""
+    params = workloads.batch_96()
+    gens = [Q.Generator(p, device=dev) for p in params]
+    words = sum(Q.word_count(p) for p in params)
+    batch = Q.Batch(len(params), words, device=dev)
+    batch.set_members(gens)
+    voxels = sum(p["nx"] * p["ny"] * p["nz"] for p in params)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = batch.stream
+
+    def timed(fn, stream):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    batch.run()  # warm-up (builds the graph)
+    batch_ms = min(timed(lambda: batch.run(), s) for _ in range(repeats))
+    stats = batch.query()
+
+    def run_single():
+        for g in gens:
+            g.seed()
+            g.grow()
+    run_single()
+    # The single path runs each member on its own stream with a host wait per
+    # realization; time it on the host around a device synchronisation.
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run_single()
+    torch.cuda.synchronize()
+    single_ms = 1000 * (time.perf_counter() - t0)
+    out = {"workload": "batch_96", "members": len(params), "voxels": voxels,
+           "batch_ms": batch_ms, "realizations_per_s": len(params) / (batch_ms / 1000),
+           "nodes_per_s": voxels / (batch_ms / 1000),
+           "single_path_ms": single_ms,
+           "single_path_realizations_per_s": len(params) / (single_ms / 1000),
+           "speedup_vs_single_path": single_ms / batch_ms,
+           "all_done": all(st.status == Q.QSGS_OK for st in stats)}
+    batch.close()
+    for g in gens:
+        g.close()
+    return out
 
 
 def main():
@@ -261,6 +317,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
+    batched = None
+    if not a.no_batch:
+        del g
+        batched = bench_batch(Q, torch, dev)
 
     if rank == 0:
         print(json.dumps({
@@ -275,7 +335,7 @@ def main():
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_timed, "clocks": clocks,
+            "gpu_launches": launches_timed, "clocks": clocks, "batched": batched,
         }), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
