@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help=">= 1")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving report")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving sweep only: 2000 requests, loads 0.25..1.2 of saturation")
     return ap.parse_args()
 
 
@@ -206,6 +209,39 @@ def bench_batch(Q, torch, dev, repeats: int = 2) -> dict:
     return out
 
 
+def bench_serve(torch, dev, n_requests: int, fractions, quantum: int = 8) -> dict:
+    """Continuous batching on the request mix (edge 64..512 with weights
+    0.3/0.3/0.2/0.15/0.05, porosity U[0.08,0.30], spacing U{0..40}, cd 1e-4):
+    the closed-loop saturation rate first (all requests at t = 0), then
+    Poisson arrivals at the given fractions of it.  Latency = arrival to the
+    phase map in pinned host memory."""
+    from paper_2602_11734_gb300 import serve as S
+    params = workloads.serve_requests(n_requests)
+
+    def run(arrivals):
+        reqs = [S.Request(rid=i, params=p, arrival=float(t))
+                for i, (p, t) in enumerate(zip(params, arrivals))]
+        srv = S.Server(device=dev, max_members=256, step_quantum=quantum, keep_results=False)
+        t0 = time.perf_counter()
+        srv.serve(reqs)
+        wall = time.perf_counter() - t0
+        out = S.summarize(reqs, wall_s=wall)
+        out["rounds"] = srv.rounds
+        srv.batch.close()
+        return out
+
+    run([0.0] * min(32, n_requests))  # warm-up: graph build, allocator
+    sat = run([0.0] * n_requests)
+    points = []
+    for f in fractions:
+        rate = f * sat["requests_per_s"]
+        pt = run(workloads.poisson_arrivals(n_requests, rate))
+        pt.update({"load": f, "arrival_rate_per_s": rate})
+        points.append(pt)
+    return {"workload": "serve_requests", "requests": n_requests, "step_quantum": quantum,
+            "saturation": sat, "sweep": points}
+
+
 def main():
     a = parse()
     a.e2e_steps = max(1, a.e2e_steps)
@@ -217,6 +253,18 @@ def main():
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if a.serve:
+        build.build()
+        Q.load_library()
+        res = bench_serve(torch, dev, 2000, (0.25, 0.5, 0.75, 0.9, 1.0, 1.2))
+        if rank == 0:
+            sat = res["saturation"]
+            print(json.dumps({"metric": "requests/s", "value": sat["requests_per_s"],
+                              "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+                              "data": "synthetic", "dtype": "u32",
+                              "config": {"workload": "serve_requests"}, "served": res}),
+                  flush=True)
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -317,10 +365,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = None
+    batched = served = None
+    del g
     if not a.no_batch:
-        del g
         batched = bench_batch(Q, torch, dev)
+    if not a.no_serve:
+        served = bench_serve(torch, dev, 200, (0.75,))
 
     if rank == 0:
         print(json.dumps({
@@ -336,6 +386,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed, "clocks": clocks, "batched": batched,
+            "served": served,
         }), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
