@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help=">= 1")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving report")
+    ap.add_argument("--edge", type=int, default=400,
+                    help="grid edge of the timed workload (400 = the reported configuration; "
+                         "smaller edges are for profiler captures)")
     ap.add_argument("--serve", action="store_true",
                     help="serving sweep only: 2000 requests, loads 0.25..1.2 of saturation")
     return ap.parse_args()
@@ -275,7 +278,7 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    p = dict(workloads.single_400(), seed=1 + rank)
+    p = dict(workloads.single_400(), seed=1 + rank, nx=a.edge, ny=a.edge, nz=a.edge)
     n_vox = p["nx"] * p["ny"] * p["nz"]
     g = Q.Generator(p, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -378,7 +381,8 @@ def main():
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": 400, "ny": 400, "nz": 400, "cd": p["cd"],
+            "config": {"workload": WORKLOAD if a.edge == 400 else f"single_400 at {a.edge}^3",
+                       "nx": a.edge, "ny": a.edge, "nz": a.edge, "cd": p["cd"],
                        "spacing_s": p["spacing_s"], "g_face": p["g_face"], "g_edge": p["g_edge"],
                        "g_corner": p["g_corner"], "solid_fraction": p["target_solid_fraction"],
                        "growth_steps": st.steps, "seeds": st.n_seeds,
