@@ -36,6 +36,10 @@ L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2: written between timed steps
 CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
 PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
+# DRAM bytes (read + write) per k_grow launch of the 400^3 realization, from
+# the ncu capture summarised in profiles/k_grow_single_400.md; None once the
+# kernel changes.
+K_GROW_TRAFFIC_BYTES = 17.6e6
 
 
 def parse():
@@ -338,7 +342,8 @@ def main():
     achieved = st_prof.sum_draws / (grow_ms / 1000.0) / 1e9
     pk, pk_kind = peaks()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gblock/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_grow",
+                "frac": achieved / peak,
+                "traffic": K_GROW_TRAFFIC_BYTES if a.edge == 400 else None, "kernel": "k_grow",
                 "work": "Philox4x32-10 blocks drawn per second",
                 "peak_kind": "measured (qsgs_bench_philox probe on this GPU)",
                 "draws": st_prof.sum_draws, "launches": grow_launches,
