@@ -37,8 +37,8 @@ CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
 PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
 # DRAM bytes (read + write) per k_grow launch of the 400^3 realization, from
-# the ncu capture summarised in profiles/k_grow_single_400.md; None once the
-# kernel changes.
+# an ncu capture (a 160^3 run, scaled by Philox blocks drawn); to be reset to
+# None whenever the kernel changes.
 K_GROW_TRAFFIC_BYTES = 17.6e6
 
 

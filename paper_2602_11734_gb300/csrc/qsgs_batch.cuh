@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kGrowThreads, 2)
     const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
     const PhiloxKeys keys = md.keys;
     uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
-    GrowCounters cnt{0, 0, 0};
+    GrowCounters cnt{0, 0};
     grow_chunk(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys, smem[warp],
                cnt);
     flush_counters(st, cnt);

@@ -660,8 +660,12 @@ constexpr int kGrowWarps = kGrowThreads / 32;
 constexpr int kGrowQueue = 1024;  // pairs per drain round; a word has at most 7 * 32
 
 struct GrowWarpSmem {
-  uint4 V[32][7];            // per lane word, per block b: V_{4b..4b+3}
-  uint16_t Q[kGrowQueue];    // queued pairs: lane << 8 | block << 5 | bit
+  uint4 V[32][7];  // per lane word, per block b: V_{4b..4b+3}
+  union {
+    uint32_t B[32 * 7];      // per lane word, per block: voxels that draw it (read
+                             // into registers before the queue is filled)
+    uint16_t Q[kGrowQueue];  // queued pairs: lane << 8 | block << 5 | bit
+  };
   uint32_t r[32], xw[32], v0[32];
 };
 
@@ -712,7 +716,7 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
 }
 
 struct GrowCounters {
-  uint32_t live, draws, front;
+  uint32_t draws, front;  // Philox blocks drawn (= attempts with a live void target), |A_t|
 };
 
 // Per-direction thresholds of one instance as T - 1 (a draw succeeds iff
@@ -772,9 +776,19 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     S.xw[lane] = xw;
     S.v0[lane] = r * g.nx + xw * 32u;
   }
-  uint32_t items = 0;
+  // The 224 (word, block) masks are dealt round-robin to the lanes (lane j
+  // takes masks j, j+32, ...), which evens out the queueing work between
+  // dense and sparse words.
 #pragma unroll
-  for (int b = 0; b < 7; ++b) items += __popc(Bm[b]);
+  for (int b = 0; b < 7; ++b) S.B[lane * 7 + b] = Bm[b];
+  __syncwarp();
+  uint32_t mine[7], items = 0;
+#pragma unroll
+  for (int gi = 0; gi < 7; ++gi) {
+    mine[gi] = S.B[lane + 32 * gi];
+    items += __popc(mine[gi]);
+  }
+  __syncwarp();  // S.B is overwritten by the queue below
   uint32_t incl = items;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -783,9 +797,10 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   }
   const uint32_t excl = incl - items;
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  cnt.draws += total;  // one Philox block per pair; every pair has a live void target
 
-  // Phase 2: drain in rounds of at most kGrowQueue pairs (whole words).
-  uint32_t done = 0;  // pairs of the lanes already drained
+  // Phase 2: drain in rounds of at most kGrowQueue pairs.
+  uint32_t done = 0;  // pairs of the lanes already queued and drained
   while (done < total) {
     // Lanes whose pairs all fit into this round.
     const bool fits = excl >= done && incl - done <= (uint32_t)kGrowQueue;
@@ -795,12 +810,14 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     if (fits && items > 0) {
       uint32_t pos = excl - done;
 #pragma unroll
-      for (int b = 0; b < 7; ++b) {
-        uint32_t m = Bm[b];
+      for (int gi = 0; gi < 7; ++gi) {
+        uint32_t m = mine[gi];
+        const uint32_t q = lane + 32u * gi;        // mask index = word * 7 + block
+        const uint32_t tag = ((q / 7u) << 8) | ((q % 7u) << 5);
         while (m) {
           const uint32_t i = __ffs(m) - 1;
           m &= m - 1;
-          S.Q[pos++] = (uint16_t)((lane << 8) | (b << 5) | i);
+          S.Q[pos++] = (uint16_t)(tag | i);
         }
       }
     }
@@ -811,24 +828,25 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
       const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
       const uint32_t v = S.v0[owner] + i;
       const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
-      ++cnt.draws;
       const uint4 vm = S.V[owner][b];
-      const uint32_t vb = ((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
-                          (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3);
-      cnt.live += __popc(vb);
       const uint4 th = thr[b];
-      uint32_t win = (rnd.x <= th.x ? 1u : 0u) | (rnd.y <= th.y ? 2u : 0u) |
-                     (rnd.z <= th.z ? 4u : 0u) | (rnd.w <= th.w ? 8u : 0u);
-      win &= vb;
-      while (win) {
-        const uint32_t j = __ffs(win) - 1;
-        win &= win - 1;
-        const int d = (int)(4u * b + j);
-        const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
-        const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
-        const size_t wq = (size_t)rq * g.W + (xx >> 5);
-        // Fire-and-forget: the claim grid collects New_t; nobody waits.
-        atomicOr(claims + wq, 1u << (xx & 31));
+      const uint32_t bit = 1u << i;
+      const bool w0 = (vm.x & bit) && rnd.x <= th.x;
+      const bool w1 = (vm.y & bit) && rnd.y <= th.y;
+      const bool w2 = (vm.z & bit) && rnd.z <= th.z;
+      const bool w3 = (vm.w & bit) && rnd.w <= th.w;
+      if (w0 | w1 | w2 | w3) {
+        uint32_t win = (w0 ? 1u : 0u) | (w1 ? 2u : 0u) | (w2 ? 4u : 0u) | (w3 ? 8u : 0u);
+        while (win) {
+          const uint32_t j = __ffs(win) - 1;
+          win &= win - 1;
+          const int d = (int)(4u * b + j);
+          const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
+          const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
+          const size_t wq = (size_t)rq * g.W + (xx >> 5);
+          // Fire-and-forget: the claim grid collects New_t; nobody waits.
+          atomicOr(claims + wq, 1u << (xx & 31));
+        }
       }
     }
     __syncwarp();  // S.Q is refilled by the next round
@@ -836,16 +854,19 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   }
 }
 
+// `draws` is warp-uniform (a chunk total); `front` is per lane.  live is
+// the number of Philox blocks drawn: zero exactly when no pair had a void
+// target with a positive threshold (the stall test).
 __device__ __forceinline__ void flush_counters(RunState* st, GrowCounters& c) {
-  const uint32_t wl = __reduce_add_sync(0xffffffffu, c.live);
-  const uint32_t wd = __reduce_add_sync(0xffffffffu, c.draws);
   const uint32_t wf = __reduce_add_sync(0xffffffffu, c.front);
   if ((threadIdx.x & 31) == 0) {
-    if (wl) atomicAdd(&st->live, (unsigned long long)wl);
-    if (wd) atomicAdd(&st->sum_draws, (unsigned long long)wd);
+    if (c.draws) {
+      atomicAdd(&st->live, (unsigned long long)c.draws);
+      atomicAdd(&st->sum_draws, (unsigned long long)c.draws);
+    }
     if (wf) atomicAdd(&st->front_acc, (unsigned long long)wf);
   }
-  c = GrowCounters{0, 0, 0};
+  c = GrowCounters{0, 0};
 }
 
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
@@ -862,7 +883,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  GrowCounters cnt{0, 0, 0};
+  GrowCounters cnt{0, 0};
   for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
     const uint32_t idx = base + lane;
     const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
