@@ -206,6 +206,17 @@ void qsgs_destroy(qsgs_handle* h);
  * do not depend on it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
 
+/* Tuning probe (no counterpart in the paper): replays the growth kernel of
+ * the handle's next step `reps` times with `grow_blocks` thread blocks (0 =
+ * default) and writes the mean milliseconds per launch to *ms (host).  The
+ * realization is left exactly as it was (the step's claims and marks are
+ * idempotent and its counters are restored), so an autotuner can time grid
+ * sizes on the real mid-run state.  The handle must be between steps of a
+ * running realization (after qsgs_grow_until returned QSGS_RUNNING).
+ * Blocks.  Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_STATE or
+ * QSGS_ERR_CUDA. */
+int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* ms);
+
 /* ---- batches ------------------------------------------------------------
  * A batch advances many realizations (its members: ordinary handles, each
  * with its own workspace) with the same launches: one growth launch over

@@ -815,6 +815,39 @@ int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks) {
   return QSGS_OK;
 }
 
+int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* ms) {
+  if (!h || !ms || reps == 0) return QSGS_ERR_INVALID;
+  if (!h->seeded || h->list_stale) return QSGS_ERR_STATE;
+  RunState saved{};
+  int rc = read_state(h, &saved);
+  if (rc != QSGS_OK) return rc;
+  if (saved.status != kRunning || !saved.active) return QSGS_ERR_STATE;
+  const uint32_t blocks = grow_blocks ? grow_blocks : default_grow_blocks();
+  const StepBuffers b = step_buffers(h);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  Tracer quiet;  // probe launches are not counted as the run's launches
+  if (e == cudaSuccess) e = launch_grow_only(h->g, b, h->k0, h->k1, blocks, h->stream, quiet);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  for (uint32_t k = 0; k < reps && e == cudaSuccess; ++k)
+    e = launch_grow_only(h->g, b, h->k0, h->k1, blocks, h->stream, quiet);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  // Put back the counters the replays accumulated; the grid, the claim grid
+  // and the marks are unchanged by repeating the same step.
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->st, &saved, sizeof(RunState), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  *ms = (double)t / reps;
+  return QSGS_OK;
+}
+
 int qsgs_batch_set_profiling(qsgs_batch* b, int enable) {
   if (!b) return QSGS_ERR_INVALID;
   cudaError_t e = cudaStreamSynchronize(b->stream);

@@ -1109,6 +1109,13 @@ cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, 
 
 uint32_t default_grow_blocks() { return (uint32_t)num_sms() * 8; }
 
+cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
+                             uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
+  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.list, b.grid, b.aux, b.mark,
+              b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+  return cudaSuccess;
+}
+
 cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                               cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};

@@ -150,6 +150,10 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
 cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                             cudaStream_t s, Tracer& tr);
 cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, Tracer& tr);
+// The growth kernel alone (the timing probe: it is idempotent on the grid,
+// the claim grid and the marks).
+cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
+                             uint32_t grow_blocks, cudaStream_t s, Tracer& tr);
 // Rebuilds a realization's candidate list from its grid (all solid words).
 cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                               cudaStream_t s, Tracer& tr);

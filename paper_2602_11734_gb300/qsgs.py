@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_int),
                 "qsgs_destroy": ([H], None),
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_time_grow": ([H, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
                 "qsgs_batch_workspace_bytes": ([ctypes.c_uint32, ctypes.c_uint64], ctypes.c_size_t),
                 "qsgs_batch_create": ([ctypes.c_uint32, ctypes.c_uint64, vp, ctypes.c_size_t, vp,
                                        ctypes.POINTER(H)], ctypes.c_int),
@@ -221,6 +223,14 @@ def qsgs_set_grow_blocks(h, blocks: int) -> None:
     rc = load_library().qsgs_set_grow_blocks(h, blocks)
     if rc != QSGS_OK:
         raise QsgsError(rc, "qsgs_set_grow_blocks")
+
+
+def qsgs_time_grow(h, grow_blocks: int = 0, reps: int = 5) -> float:
+    ms = ctypes.c_double()
+    rc = load_library().qsgs_time_grow(h, grow_blocks, reps, ctypes.byref(ms))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_time_grow")
+    return ms.value
 
 
 def _check(rc: int, where: str) -> int:
@@ -353,6 +363,9 @@ class Generator:
 
     def set_grow_blocks(self, blocks: int) -> None:
         qsgs_set_grow_blocks(self.handle, blocks)
+
+    def time_grow(self, grow_blocks: int = 0, reps: int = 5) -> float:
+        return qsgs_time_grow(self.handle, grow_blocks, reps)
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -232,3 +232,23 @@ def test_philox_probe_and_draw_counter(Q):
         assert st.steps <= st.sum_draws <= 7 * st.sum_front
     finally:
         g.close()
+
+
+def test_time_grow_probe_leaves_the_run_unchanged(oracle, Q):
+    p = dict(workloads.small_64(), nx=72, ny=70, nz=68, spacing_s=4)
+    want = oracle.run(p)
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        st = g.grow(5)
+        assert st.status == Q.QSGS_RUNNING
+        for blocks in (0, 64, 1000):
+            assert g.time_grow(blocks, reps=3) > 0
+        g.grow(3)
+        assert g.time_grow(0, reps=2) > 0
+        st = g.grow()
+        assert np.array_equal(g.fetch().cpu().numpy(), want.phase)
+        assert (st.solid_count, st.steps, st.status, st.sum_front) == \
+               (want.solid_count, want.steps, want.status, int(want.log["front"].sum()))
+    finally:
+        g.close()
