@@ -408,6 +408,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   const Layout L = make_layout(params);
   if (!dev_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
     return QSGS_ERR_WORKSPACE;
+  if (prepare_kernels() != cudaSuccess) return QSGS_ERR_CUDA;
   qsgs_handle* h = new (std::nothrow) qsgs_handle();
   if (!h) return QSGS_ERR_NOMEM;
   h->p = *params;
@@ -621,6 +622,7 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
   const BatchLayout L = make_batch_layout(max_members, max_words);
   if (!dev_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
     return QSGS_ERR_WORKSPACE;
+  if (prepare_kernels() != cudaSuccess) return QSGS_ERR_CUDA;
   qsgs_batch* b = new (std::nothrow) qsgs_batch();
   if (!b) return QSGS_ERR_NOMEM;
   b->max_members = max_members;
@@ -821,13 +823,26 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
   RunState saved{};
   int rc = read_state(h, &saved);
   if (rc != QSGS_OK) return rc;
-  if (saved.status != kRunning || !saved.active) return QSGS_ERR_STATE;
+  if (saved.status != kRunning) return QSGS_ERR_STATE;
   const uint32_t blocks = grow_blocks ? grow_blocks : default_grow_blocks();
   const StepBuffers b = step_buffers(h);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
   Tracer quiet;  // probe launches are not counted as the run's launches
+  // A run paused by its step budget has step t listed but not opened: open
+  // it (thresholds of step t) for the replays; the saved state goes back.
+  cudaError_t e = launch_set_step_limit(h->st, 1, h->stream, quiet);
+  RunState open{};
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  rc = read_state(h, &open);
+  if (rc != QSGS_OK) return rc;
+  if (!open.active) {
+    e = cudaMemcpyAsync(h->st, &saved, sizeof(RunState), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? QSGS_ERR_STATE : cuda_fail(h, e);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = launch_grow_only(h->g, b, h->k0, h->k1, blocks, h->stream, quiet);
   if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
   for (uint32_t k = 0; k < reps && e == cudaSuccess; ++k)

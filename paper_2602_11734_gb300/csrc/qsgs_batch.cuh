@@ -36,7 +36,14 @@ struct BatchCommitPolicy {
   BatchState* bs;
   uint32_t* list;
   int prologue;
-  using Item = WordItem;  // w = member-local word, bits = listed, extra = member
+  struct Item {
+    uint32_t w;      // member-local word (0xFFFFFFFF: outside every member)
+    uint32_t bits;   // 1: listed
+    uint32_t extra;  // member index
+    uint32_t c;      // claims of this step in the word
+    uint32_t old;    // the word before the claims
+    uint32_t flags;  // 1: lane 0 clears the warp's mark word; 2: clear the other claim word
+  };
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return bs->total_words; }
@@ -50,29 +57,39 @@ struct BatchCommitPolicy {
     const MemberDesc& md = d[m];
     const uint32_t w = i - md.word_base;
     const bool in_range = valid && i < md.word_end;
-    RunState* st = md.st;
-    uint32_t keep = 0, c = 0;
+    const RunState* st = md.st;
+    uint32_t keep = 0, c = 0, old = 0, flags = 0;
     if (prologue) {
       if (in_range && st->status == kRunning) keep = md.grid[w] ? 1u : 0u;
     } else if (st->active) {
       uint32_t mk = 0;
-      if (lane == 0 && in_range) {
-        mk = md.mark[w >> 5];
-        if (mk) md.mark[w >> 5] = 0;
-      }
+      if (lane == 0 && in_range) mk = md.mark[w >> 5];
       mk = __shfl_sync(0xffffffffu, mk, 0);
       if (in_range) {
         const uint32_t par = st->t & 1u;
         c = md.aux[(size_t)par * md.g.nwords + w];
-        uint32_t* other = md.aux + (size_t)(par ^ 1u) * md.g.nwords + w;
-        if (*other) *other = 0;
-        if (c) md.grid[w] |= c;
+        const uint32_t other = md.aux[(size_t)(par ^ 1u) * md.g.nwords + w];
+        old = md.grid[w];
         keep = ((mk >> lane) & 1u) | (c ? 1u : 0u);
+        flags = (lane == 0 && mk ? 1u : 0u) | (other ? 2u : 0u);
       }
-      const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(c));
-      if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
     }
-    return Item{in_range ? w : 0xFFFFFFFFu, keep, m};
+    return Item{in_range ? w : 0xFFFFFFFFu, keep, m, c, old, flags};
+  }
+  // Claims into the member's grid and their count; marks and the previous
+  // claim grid cleared.  All lanes of a warp serve one member.
+  __device__ void apply(const Item& it, bool) const {
+    if (prologue) return;
+    const MemberDesc& md = d[it.extra];
+    RunState* st = md.st;
+    if (!st->active) return;  // uniform over the warp
+    if (it.w != 0xFFFFFFFFu) {
+      if (it.flags & 1u) md.mark[it.w >> 5] = 0;
+      if (it.flags & 2u) md.aux[(size_t)((st->t & 1u) ^ 1u) * md.g.nwords + it.w] = 0;
+      if (it.c) md.grid[it.w] = it.old | it.c;
+    }
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(it.c));
+    if ((threadIdx.x & 31u) == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
   }
   __device__ uint32_t count(const Item& it) const { return it.bits; }
   __device__ void emit(const Item& it, unsigned long long off) const {
@@ -153,14 +170,16 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
 // Growth over the batch candidate list: warp chunk c belongs to the member
 // whose chunk range holds c, so every warp serves one member at a time.
 __global__ void __launch_bounds__(kGrowThreads, 2)
-    k_grow_batch(const MemberDesc* __restrict__ d, const BatchState* bs,
+    k_grow_batch(const MemberDesc* __restrict__ d, BatchState* bs,
                  const uint32_t* __restrict__ list) {
-  __shared__ GrowWarpSmem smem[kGrowWarps];
+  extern __shared__ uint4 grow_smem_[];
+  GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
   __shared__ uint4 s_thr[kGrowWarps][7];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = bs->total_chunks, n = bs->n_members;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  for (uint32_t c = blockIdx.x * kGrowWarps + warp; c < total; c += nwarps) {
+  for (uint32_t c = blockIdx.x * kGrowWarps + warp; c < total;
+       c = next_chunk(&bs->scan.grow_next, nwarps)) {
     const uint32_t m = find_member(d, n, c, [](const MemberDesc& x) { return x.chunk_base; });
     const MemberDesc& md = d[m];
     RunState* st = md.st;
@@ -178,6 +197,7 @@ __global__ void __launch_bounds__(kGrowThreads, 2)
     flush_counters(st, cnt);
     __syncwarp();  // s_thr[warp] is rewritten by the next chunk
   }
+  finish_dispenser(&bs->scan.grow_next, &bs->scan.grow_done);
 }
 
 }  // namespace qsgs

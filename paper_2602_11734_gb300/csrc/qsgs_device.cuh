@@ -243,6 +243,9 @@ struct alignas(256) RunState {
   uint32_t scan_epoch;           // look-back scan launch counter
   uint32_t scan_tile;            // look-back scan tile dispenser
   uint32_t scan_done;            // look-back scan blocks finished
+  uint32_t grow_next;            // growth chunk dispenser (zero between launches)
+  uint32_t grow_done;            // growth blocks finished (zero between launches)
+  uint32_t list_next;            // entries appended to the next candidate list
 };
 
 // ---------------------------------------------------------------------------

@@ -63,6 +63,9 @@ __global__ void k_init_state(RunState* st, StateInit init) {
   st->trim_parity = 0;
   st->error = 0;
   st->iters = 0;
+  st->grow_next = 0;
+  st->grow_done = 0;
+  st->list_next = 0;
 }
 
 // Decides whether the next step runs.  Exits, tested in order: target
@@ -70,6 +73,7 @@ __global__ void k_init_state(RunState* st, StateInit init) {
 // thresholds of the step from the solid count before it.
 __device__ void begin_step(RunState* st) {
   st->active = 0;
+  st->list_next = 0;
   if (st->status != kRunning) return;
   if (st->solid >= st->nt) { st->status = kStatusDone; return; }
   if (st->t >= st->max_steps) { st->status = kStatusMaxSteps; return; }
@@ -85,6 +89,7 @@ __device__ void begin_step(RunState* st) {
 // pending (the run ends with this step).
 __device__ void close_step(RunState* st) {
   if (st->active) {
+    st->front_words = st->list_next;  // the list k_commit appended
     if (st->live == 0) {
       st->status = kStatusStalled;
     } else {
@@ -170,6 +175,7 @@ struct SeedCompactPolicy {
   using Item = WordItem;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -215,6 +221,8 @@ struct SeedCompactPolicy {
 // kCommitStep (after a growth step): ORs the step's claims into the grid,
 // counts them, emits marked or claimed words, clears the marks and the
 // claim grid of the next step.  The list stays in ascending word order.
+// (The step loop of a single realization uses k_commit below instead: the
+// growth step does not depend on the order of the list.)
 enum : int { kCommitInitial = 0, kCommitStep = 1 };
 
 struct CommitPolicy {
@@ -225,7 +233,13 @@ struct CommitPolicy {
   uint32_t* mark;  // one bit per word, set by the growth kernel
   uint32_t* list;
   int mode;
-  using Item = WordItem;
+  struct Item {
+    uint32_t w;      // word index
+    uint32_t bits;   // 1: listed
+    uint32_t extra;  // claims of this step in the word
+    uint32_t old;    // the word before the claims
+    uint32_t flags;  // 1: lane 0 clears the warp's mark word; 2: clear the other claim word
+  };
   __device__ bool active() const { return mode == kCommitInitial || st->active != 0; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -235,22 +249,26 @@ struct CommitPolicy {
     const uint32_t lane = threadIdx.x & 31u;
     if (mode == kCommitInitial) {
       const uint32_t solid = valid ? grid[w] : 0u;
-      return Item{w, solid ? 1u : 0u, 0u};
+      return Item{w, solid ? 1u : 0u, 0u, 0u, 0u};
     }
     uint32_t m = 0;
-    if (lane == 0 && valid) {
-      m = mark[w >> 5];
-      if (m) mark[w >> 5] = 0;
-    }
+    if (lane == 0 && valid) m = mark[w >> 5];
     m = __shfl_sync(0xffffffffu, m, 0);
-    if (!valid) return Item{w, 0u, 0u};
+    if (!valid) return Item{w, 0u, 0u, 0u, 0u};
     const uint32_t par = st->t & 1u;
     const uint32_t c = aux[(size_t)par * g.nwords + w];
-    uint32_t* other = aux + (size_t)(par ^ 1u) * g.nwords + w;
-    if (*other) *other = 0;
-    if (c) grid[w] |= c;
+    const uint32_t other = aux[(size_t)(par ^ 1u) * g.nwords + w];
+    const uint32_t old = grid[w];
     const uint32_t keep = ((m >> lane) & 1u) | (c ? 1u : 0u);
-    return Item{w, keep, c};
+    return Item{w, keep, c, old, (lane == 0 && m ? 1u : 0u) | (other ? 2u : 0u)};
+  }
+  // Claims into the grid; the marks and the claim grid of the previous step
+  // are cleared for the next step.
+  __device__ void apply(const Item& it, bool valid) const {
+    if (mode == kCommitInitial || !valid) return;
+    if (it.flags & 1u) mark[it.w >> 5] = 0;
+    if (it.flags & 2u) aux[(size_t)((st->t & 1u) ^ 1u) * g.nwords + it.w] = 0;
+    if (it.extra) grid[it.w] = it.old | it.extra;
   }
   __device__ uint32_t count(const Item& it) const { return it.bits; }
   __device__ uint32_t side(const Item& it, int k) const { return k == 1 ? __popc(it.extra) : 0u; }
@@ -260,6 +278,86 @@ struct CommitPolicy {
   __device__ void emit(const Item& it, unsigned long long off) const { list[off] = it.w; }
   __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
 };
+
+// Commit of a growth step without an ordered scan: the same work as
+// CommitPolicy in kCommitStep mode, but the next candidate list is appended
+// in any order (one atomic per block and tile), so no tile waits on
+// another.  The growth step gives the same result for any order of its
+// list: every draw is keyed by (voxel, step, block) and claims are ORed.
+// Thread t of a block takes words base + k * 256 + t (k < 8) of a 2048-word
+// tile; all loads of a tile are issued before its stores.
+constexpr int kCommitThreads = 256;
+constexpr int kCommitItems = 8;
+
+__global__ void __launch_bounds__(kCommitThreads, 3)
+    k_commit(Geom g, RunState* st, uint32_t* grid, uint32_t* aux, uint32_t* mark,
+             uint32_t* list) {
+  constexpr int kWarps = kCommitThreads / 32;
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_base;
+  __shared__ unsigned long long s_claimed;
+  if (!st->active) return;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t par = st->t & 1u;
+  const uint32_t nw = g.nwords;
+  uint32_t* claims = aux + (size_t)par * nw;
+  uint32_t* prev = aux + (size_t)(par ^ 1u) * nw;  // claim grid of the next step
+  if (threadIdx.x == 0) s_claimed = 0;
+  uint32_t claimed = 0;
+  constexpr uint32_t kTile = kCommitThreads * kCommitItems;
+  for (uint32_t base = blockIdx.x * kTile; base < nw; base += gridDim.x * kTile) {
+    uint32_t m[kCommitItems], c[kCommitItems], o[kCommitItems], old[kCommitItems];
+#pragma unroll
+    for (int k = 0; k < kCommitItems; ++k) {
+      const uint32_t w = base + k * kCommitThreads + threadIdx.x;
+      const bool valid = w < nw;
+      m[k] = (lane == 0 && valid) ? mark[w >> 5] : 0u;
+      c[k] = valid ? claims[w] : 0u;
+      o[k] = valid ? prev[w] : 0u;
+      old[k] = valid ? grid[w] : 0u;
+    }
+    uint32_t keep = 0;  // bit k: word k is listed
+#pragma unroll
+    for (int k = 0; k < kCommitItems; ++k) {
+      const uint32_t w = base + k * kCommitThreads + threadIdx.x;
+      if (m[k]) mark[w >> 5] = 0;
+      if (o[k]) prev[w] = 0;
+      if (c[k]) grid[w] = old[k] | c[k];
+      claimed += __popc(c[k]);
+      const uint32_t mk = __shfl_sync(0xffffffffu, m[k], 0);
+      if (((mk >> lane) & 1u) | (c[k] ? 1u : 0u)) keep |= 1u << k;
+    }
+    // Block-wide exclusive offsets of the kept words, one atomic for the tile.
+    const uint32_t mine = __popc(keep);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= (uint32_t)off) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int i = 0; i < kWarps; ++i) {
+        const uint32_t x = s_warp[i];
+        s_warp[i] = run;
+        run += x;
+      }
+      s_base = run ? atomicAdd(&st->list_next, run) : 0u;
+    }
+    __syncthreads();
+    uint32_t pos = s_base + s_warp[warp] + incl - mine;
+#pragma unroll
+    for (int k = 0; k < kCommitItems; ++k)
+      if (keep & (1u << k)) list[pos++] = base + k * kCommitThreads + threadIdx.x;
+    __syncthreads();  // s_warp / s_base are reused by the next tile
+  }
+  const uint32_t wc = __reduce_add_sync(0xffffffffu, claimed);
+  if (lane == 0 && wc) atomicAdd(&s_claimed, (unsigned long long)wc);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_claimed) atomicAdd(&st->claimed, s_claimed);
+}
 
 // The front size |A| of the current grid (solids with a void in-domain
 // 26-neighbour), counted once at the end of a growth call for the
@@ -271,6 +369,7 @@ struct FrontCountPolicy {
   RunState* st;
   const uint32_t* grid;
   using Item = WordItem;
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -331,6 +430,7 @@ struct TrimPolicy {
   using Item = WordItem;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return st->trim_pending != 0; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
@@ -368,6 +468,7 @@ struct AcceptPolicy {
   };
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return st->cand_n; }
@@ -401,6 +502,7 @@ struct CellOffsetPolicy {
   };
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return ncells; }
@@ -512,6 +614,7 @@ struct ConflictOffsetPolicy {
   };
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
+  __device__ void apply(const Item&, bool) const {}
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return true; }
   __device__ uint32_t n_items() const { return st->cand_n; }
@@ -632,7 +735,7 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 }
 
 // ---------------------------------------------------------------------------
-// The growth step (Sec. 2.3 step 3, Algorithm 3 lines 4-13).  Every front
+// The growth step (Sec. 2.3 step 3, Algorithm 3).  Every front
 // voxel a tries each void in-domain neighbour q = a + e_d with the draw
 // word (d & 3) of Philox block (a, 0, t, 0x200 | d >> 2) against the class
 // threshold of Eq. 1; a success records q in this step's claim grid with a
@@ -649,15 +752,17 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // positive threshold) and the 7 Philox-block masks B_b = OR of V_d over the
 // directions of block b; words that still hold front voxels are marked for
 // the next candidate list.  Phase 2: the lanes queue their (word, block,
-// voxel) pairs in shared memory, then the warp drains the queue one pair per
-// lane -- one Philox call per pair -- so no lane idles while another draws.
+// voxel) pairs in shared memory, then the warp drains the queue two pairs
+// per lane at a time -- one Philox call per pair -- so no lane idles while
+// another draws; passing draws are buffered and claimed by full warps.
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
 #ifndef QSGS_GROW_MIN_BLOCKS
 #define QSGS_GROW_MIN_BLOCKS 3  // resident blocks per SM the register budget aims for
 #endif
-constexpr int kGrowQueue = 1024;  // pairs per drain round; a word has at most 7 * 32
+constexpr int kGrowQueue = 2048;  // pairs per drain round; a word has at most 7 * 32
+constexpr int kGrowWins = 256;    // deferred claims buffered per warp
 
 struct GrowWarpSmem {
   uint4 V[32][7];  // per lane word, per block b: V_{4b..4b+3}
@@ -666,8 +771,11 @@ struct GrowWarpSmem {
                              // into registers before the queue is filled)
     uint16_t Q[kGrowQueue];  // queued pairs: lane << 8 | block << 5 | bit
   };
-  uint32_t r[32], xw[32], v0[32];
+  uint32_t w[32], v0[32];    // per lane: word index, voxel index of its bit 0
+  uint32_t win[kGrowWins];   // draws that passed a threshold: pair | pass bits << 16
 };
+// Dynamic shared memory of a growth block (one GrowWarpSmem per warp).
+constexpr size_t kGrowSmemBytes = sizeof(GrowWarpSmem) * kGrowWarps;
 
 // Direction index of offset (dx, dy, dz), evaluated at compile time.
 __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
@@ -738,6 +846,29 @@ __device__ __forceinline__ uint32_t live_directions(const RunState* st) {
   return live_dirs;
 }
 
+// Claims of buffered draws: a draw's direction j wins when it passed its
+// threshold and its target is a void in-domain neighbour (bit i of V_{4b+j}).
+__device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, const GrowWarpSmem& S,
+                                           uint32_t nwin, uint32_t lane) {
+  for (uint32_t k = lane; k < nwin; k += 32) {
+    const uint32_t x = S.win[k];
+    const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
+    const uint4 vm = S.V[owner][b];
+    uint32_t win = (x >> 16) & (((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
+                                (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3));
+    const int wo = (int)S.w[owner];
+    while (win) {
+      const uint32_t j = __ffs(win) - 1;
+      win &= win - 1;
+      const int d = (int)(4u * b + j);
+      const int xi = (int)i + dir_dx(d);  // -1 .. 32: target bit, word carry
+      const int wq = wo + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5);
+      // Fire-and-forget: the claim grid collects New_t; nobody waits.
+      atomicOr(claims + (uint32_t)wq, 1u << (xi & 31));
+    }
+  }
+}
+
 // One warp, one chunk of up to 32 candidate words (w = 0xFFFFFFFF: no word
 // for this lane).  All 32 lanes must call it together.
 __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
@@ -772,8 +903,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     V[27] = 0;
 #pragma unroll
     for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
-    S.r[lane] = r;
-    S.xw[lane] = xw;
+    S.w[lane] = w;
     S.v0[lane] = r * g.nx + xw * 32u;
   }
   // The 224 (word, block) masks are dealt round-robin to the lanes (lane j
@@ -815,40 +945,50 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
         const uint32_t q = lane + 32u * gi;        // mask index = word * 7 + block
         const uint32_t tag = ((q / 7u) << 8) | ((q % 7u) << 5);
         while (m) {
-          const uint32_t i = __ffs(m) - 1;
-          m &= m - 1;
+          const uint32_t lsb = m & (0u - m);
+          const uint32_t i = __popc(lsb - 1u);  // index of the lowest set bit
+          m ^= lsb;
           S.Q[pos++] = (uint16_t)(tag | i);
         }
       }
     }
     __syncwarp();
     const uint32_t round_n = round_end - done;
-    for (uint32_t k = lane; k < round_n; k += 32) {
-      const uint32_t e = S.Q[k];
-      const uint32_t owner = e >> 8, b = (e >> 5) & 7u, i = e & 31u;
-      const uint32_t v = S.v0[owner] + i;
-      const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
-      const uint4 vm = S.V[owner][b];
-      const uint4 th = thr[b];
-      const uint32_t bit = 1u << i;
-      const bool w0 = (vm.x & bit) && rnd.x <= th.x;
-      const bool w1 = (vm.y & bit) && rnd.y <= th.y;
-      const bool w2 = (vm.z & bit) && rnd.z <= th.z;
-      const bool w3 = (vm.w & bit) && rnd.w <= th.w;
-      if (w0 | w1 | w2 | w3) {
-        uint32_t win = (w0 ? 1u : 0u) | (w1 ? 2u : 0u) | (w2 ? 4u : 0u) | (w3 ? 8u : 0u);
-        while (win) {
-          const uint32_t j = __ffs(win) - 1;
-          win &= win - 1;
-          const int d = (int)(4u * b + j);
-          const uint32_t xx = (uint32_t)((int)(S.xw[owner] * 32u + i) + dir_dx(d));
-          const uint32_t rq = (uint32_t)((int)S.r[owner] + dir_dy(d) + (int)g.ny * dir_dz(d));
-          const size_t wq = (size_t)rq * g.W + (xx >> 5);
-          // Fire-and-forget: the claim grid collects New_t; nobody waits.
-          atomicOr(claims + wq, 1u << (xx & 31));
-        }
+    // Each lane draws two pairs per iteration (two independent Philox chains
+    // in flight hide the multiply latency).  Draws that pass a threshold (a
+    // few per cent) are buffered and claimed together, so the claim work
+    // runs on full warps instead of one or two lanes of every iteration.
+    uint32_t nwin = 0;
+    for (uint32_t k0 = 0; k0 < round_n; k0 += 64) {
+      const uint32_t ka = k0 + lane, kb = ka + 32;
+      const bool va = ka < round_n, vb = kb < round_n;
+      const uint32_t ea = va ? S.Q[ka] : 0u, eb = vb ? S.Q[kb] : 0u;
+      const uint32_t ba = (ea >> 5) & 7u, bb = (eb >> 5) & 7u;
+      const U4 ra = philox4x32_10(U4{S.v0[ea >> 8] + (ea & 31u), 0u, t, kGrowTag | ba}, keys);
+      const U4 rb = philox4x32_10(U4{S.v0[eb >> 8] + (eb & 31u), 0u, t, kGrowTag | bb}, keys);
+      const uint4 tha = thr[ba], thb = thr[bb];
+      uint32_t pa = (ra.x <= tha.x ? 1u : 0u) | (ra.y <= tha.y ? 2u : 0u) | (ra.z <= tha.z ? 4u : 0u) |
+                    (ra.w <= tha.w ? 8u : 0u);
+      uint32_t pb = (rb.x <= thb.x ? 1u : 0u) | (rb.y <= thb.y ? 2u : 0u) | (rb.z <= thb.z ? 4u : 0u) |
+                    (rb.w <= thb.w ? 8u : 0u);
+      pa = va ? pa : 0u;
+      pb = vb ? pb : 0u;
+      const uint32_t lt = (1u << lane) - 1u;
+      const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
+      const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
+      if (pa) S.win[nwin + __popc(bala & lt)] = ea | (pa << 16);
+      nwin += __popc(bala);
+      if (pb) S.win[nwin + __popc(balb & lt)] = eb | (pb << 16);
+      nwin += __popc(balb);
+      if (nwin > (uint32_t)kGrowWins - 64u) {
+        __syncwarp();
+        claim_wins(g, claims, S, nwin, lane);
+        __syncwarp();
+        nwin = 0;
       }
     }
+    __syncwarp();
+    claim_wins(g, claims, S, nwin, lane);
     __syncwarp();  // S.Q is refilled by the next round
     done = round_end;
   }
@@ -869,10 +1009,33 @@ __device__ __forceinline__ void flush_counters(RunState* st, GrowCounters& c) {
   c = GrowCounters{0, 0};
 }
 
+// Chunk dispenser of the growth kernels: a warp's first chunk is its global
+// warp index, later ones come from an atomic counter, so warps that drew
+// cheap chunks take more.  The last block to finish puts the counters back
+// to zero, which leaves every launch (a graph replay included) starting
+// from a clean dispenser.
+__device__ __forceinline__ uint32_t next_chunk(uint32_t* next, uint32_t nwarps) {
+  uint32_t c = 0;
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(next, 1u) + nwarps;
+  return __shfl_sync(0xffffffffu, c, 0);
+}
+
+__device__ __forceinline__ void finish_dispenser(uint32_t* next, uint32_t* done) {
+  __syncthreads();  // every warp of the block has taken its last chunk
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      *next = 0;
+      *done = 0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
            uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys) {
-  __shared__ GrowWarpSmem smem[kGrowWarps];
+  extern __shared__ uint4 grow_smem_[];
+  GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
   __shared__ uint4 s_thr[7];
   if (!st->active) return;
   const uint32_t n = st->front_words;
@@ -883,13 +1046,15 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
+  const uint32_t nchunks = (n + 31) / 32;
   GrowCounters cnt{0, 0};
-  for (uint32_t base = (blockIdx.x * kGrowWarps + warp) * 32u; base < n; base += nwarps * 32u) {
-    const uint32_t idx = base + lane;
+  for (uint32_t c = blockIdx.x * kGrowWarps + warp; c < nchunks; c = next_chunk(&st->grow_next, nwarps)) {
+    const uint32_t idx = c * 32u + lane;
     const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
     grow_chunk(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
   }
   flush_counters(st, cnt);
+  finish_dispenser(&st->grow_next, &st->grow_done);
 }
 
 }  // namespace qsgs
@@ -984,6 +1149,14 @@ static uint32_t scan_grid(uint64_t max_items) {
   return (uint32_t)(blocks ? blocks : 1);
 }
 
+static uint32_t commit_grid(uint64_t nwords) {
+  constexpr uint64_t kTile = kCommitThreads * kCommitItems;
+  const uint64_t tiles = (nwords + kTile - 1) / kTile;
+  uint64_t blocks = (uint64_t)num_sms() * 3;
+  if (blocks > tiles) blocks = tiles;
+  return (uint32_t)(blocks ? blocks : 1);
+}
+
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz) {
   Geom g{};
   g.nx = nx;
@@ -1003,16 +1176,42 @@ Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz) {
 
 // Every launch goes through LAUNCH so that the tracer counts (and, when
 // profiling, times) it.
-#define QSGS_LAUNCH(tr, cls, s, kernel, grid, block, ...)       \
-  do {                                                          \
-    cudaError_t e_ = (tr).before((cls), (s));                   \
-    if (e_ != cudaSuccess) return e_;                           \
-    kernel<<<(grid), (block), 0, (s)>>>(__VA_ARGS__);           \
-    e_ = cudaGetLastError();                                    \
-    if (e_ != cudaSuccess) return e_;                           \
-    e_ = (tr).after((s));                                       \
-    if (e_ != cudaSuccess) return e_;                           \
+#define QSGS_LAUNCH_SMEM(tr, cls, s, kernel, grid, block, smem, ...) \
+  do {                                                               \
+    cudaError_t e_ = (tr).before((cls), (s));                        \
+    if (e_ != cudaSuccess) return e_;                                \
+    kernel<<<(grid), (block), (smem), (s)>>>(__VA_ARGS__);           \
+    e_ = cudaGetLastError();                                         \
+    if (e_ != cudaSuccess) return e_;                                \
+    e_ = (tr).after((s));                                            \
+    if (e_ != cudaSuccess) return e_;                                \
   } while (0)
+#define QSGS_LAUNCH(tr, cls, s, kernel, grid, block, ...) \
+  QSGS_LAUNCH_SMEM(tr, cls, s, kernel, grid, block, 0, __VA_ARGS__)
+
+// The growth kernels use more than the default 48 KB of shared memory; the
+// opt-in is a per-device function attribute, set once per device before
+// their first launch (handle creation does it, outside any stream capture).
+cudaError_t prepare_kernels() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_grow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
 
 cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr) {
   QSGS_LAUNCH(tr, kClsSeed, s, k_init_state, 1, 1, st, init);
@@ -1067,12 +1266,11 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
                         cudaGraphConditionalHandle cond, int use_cond) {
-  ScanCtl ctl{b.st, b.scan_status, spin_limit};
-  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.list, b.grid, b.aux, b.mark,
-              b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
-  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitStep};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
-              cp, ctl);
+  (void)spin_limit;  // no waits in a step of the single-realization path
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
+                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+  QSGS_LAUNCH(tr, kClsFront, s, k_commit, commit_grid(g.nwords), kCommitThreads, g, b.st, b.grid,
+              b.aux, b.mark, b.list);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);
   return cudaSuccess;
 }
@@ -1111,8 +1309,8 @@ uint32_t default_grow_blocks() { return (uint32_t)num_sms() * 8; }
 
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
-  QSGS_LAUNCH(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, g, b.list, b.grid, b.aux, b.mark,
-              b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
+                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
   return cudaSuccess;
 }
 
@@ -1141,7 +1339,8 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond) {
   ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};
-  QSGS_LAUNCH(tr, kClsGrow, s, k_grow_batch, grow_blocks, kGrowThreads, b.d, b.bs, b.list);
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch, grow_blocks, kGrowThreads, kGrowSmemBytes,
+                   b.d, b.bs, b.list);
   BatchCommitPolicy cp{b.d, b.bs, b.list, 0};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<BatchCommitPolicy>, scan_grid(b.max_words),
               kScanThreads, cp, ctl);

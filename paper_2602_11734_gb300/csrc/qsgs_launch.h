@@ -135,6 +135,9 @@ struct StepBuffers {
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
 uint32_t default_grow_blocks();
+// Per-device function attributes (shared-memory opt-in) of the growth
+// kernels; call before their first launch on the current device.
+cudaError_t prepare_kernels();
 
 cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t s, Tracer& tr);
 cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,

@@ -43,7 +43,12 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 //                                           together (lane l gets item base+l,
 //                                           so warp-cooperative loaders may use
 //                                           shuffles); invalid lanes get
-//                                           i = n_items and must not touch it
+//                                           i = n_items and must not touch it;
+//                                           reads only (no stores)
+//   void apply(const Item&, bool valid) const
+//                                        -- the item's side effects (stores),
+//                                           called by all lanes after every
+//                                           load of the tile was issued
 //   uint32_t count(const Item&) const    -- outputs of the item
 //   void emit(const Item&, unsigned long long prefix) const
 //   bool emit_empty() const              -- also emit items with count 0
@@ -56,7 +61,9 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned long long flag,
 // items base + k * kScanThreads + t for k < kScanItems, so every warp works
 // on 32 consecutive items at a time (coalesced loads).  The order of the
 // outputs is the order of the items: offsets are taken over (k, warp, lane)
-// in that nesting.
+// in that nesting.  The loads of all kScanItems items are issued before any
+// store of the tile (side effects, shared-memory offsets), so a thread has
+// all of them in flight at once instead of one memory round trip per item.
 template <class Policy>
 __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, ScanCtl ctl) {
   constexpr int kWarps = kScanThreads / 32;
@@ -87,6 +94,16 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_lookback_scan(Policy pol, S
       const unsigned long long i = base + (unsigned long long)k * kScanThreads;
       const bool valid = i < n_items;
       it[k] = pol.load(valid ? (uint32_t)i : n_items, valid);
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned long long i = base + (unsigned long long)k * kScanThreads;
+      pol.apply(it[k], i < n_items);
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned long long i = base + (unsigned long long)k * kScanThreads;
+      const bool valid = i < n_items;
       cnt[k] = valid ? pol.count(it[k]) : 0u;
       if (valid) {
         side0 += pol.side(it[k], 0);
