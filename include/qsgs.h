@@ -217,6 +217,35 @@ int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
  * QSGS_ERR_CUDA. */
 int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* ms);
 
+/* Front size of a packed grid, without any allocation (no counterpart in the
+ * paper).  Counts the solid voxels with a void in-domain 26-neighbour (the
+ * front |A| of Sec. 2.3, the front_size qsgs_query reports at the end of a
+ * run) of a grid in the library's packed layout: bit x of word
+ * (z * ny + y) * ceil(nx / 32) + x / 32, pad bits zero.
+ *
+ * For callers that may not allocate device memory: code inside a stream
+ * capture or a pool-only allocator region (cudaMalloc would break the
+ * capture or bypass the pool), or a real-time path where an allocation may
+ * block or fail.  The call uses 64 KiB of scratch that lives in the
+ * library's own device image (a static __device__ array) and allocates
+ * nothing, on the device or the host.
+ *   dev_grid     device, read only, ceil(nx/32) * ny * nz words
+ *   nx, ny, nz   grid size (nx * ny * nz < 2^32)
+ *   cuda_stream  stream to run on (NULL = legacy default stream)
+ *   front_out    host: receives the count
+ * Limit: at most 16,707,584 words (e.g. 800^3 fits, 1024^3 does not);
+ * larger grids return QSGS_ERR_WORKSPACE before touching the device.
+ * The first call on a device looks up the scratch address (this may load
+ * the library's device code), so make it before any stream capture.  Each
+ * call zeroes the scratch it uses (run state and tile status words) on the
+ * stream before the count.  Calls share the one scratch per device:
+ * overlapping calls (other streams or host threads) race and must be
+ * serialised by the caller.  Blocks until the count is in *front_out.
+ * Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_TIMEOUT or
+ * QSGS_ERR_CUDA. */
+int qsgs_front_count_static(const uint32_t* dev_grid, uint32_t nx, uint32_t ny, uint32_t nz,
+                            void* cuda_stream, uint64_t* front_out);
+
 /* ---- batches ------------------------------------------------------------
  * A batch advances many realizations (its members: ordinary handles, each
  * with its own workspace) with the same launches: one growth launch over

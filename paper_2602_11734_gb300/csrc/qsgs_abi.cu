@@ -863,6 +863,24 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
   return QSGS_OK;
 }
 
+int qsgs_front_count_static(const uint32_t* dev_grid, uint32_t nx, uint32_t ny, uint32_t nz,
+                            void* cuda_stream, uint64_t* front_out) {
+  if (!dev_grid || !front_out || nx == 0 || ny == 0 || nz == 0) return QSGS_ERR_INVALID;
+  const uint64_t words = (uint64_t)((nx + 31u) / 32u) * ny * nz;
+  if ((uint64_t)nx * ny * nz > 0xFFFFFFFFull) return QSGS_ERR_INVALID;
+  if (words > front_scratch_max_words()) return QSGS_ERR_WORKSPACE;
+  const Geom g = make_geom(nx, ny, nz);
+  unsigned long long front = 0;
+  uint32_t error = 0;
+  const cudaError_t e =
+      front_count_static(g, dev_grid, kSpinLimit, static_cast<cudaStream_t>(cuda_stream), &front,
+                         &error);
+  if (e != cudaSuccess) return QSGS_ERR_CUDA;
+  if (error & kErrTimeout) return QSGS_ERR_TIMEOUT;
+  *front_out = front;
+  return QSGS_OK;
+}
+
 int qsgs_batch_set_profiling(qsgs_batch* b, int enable) {
   if (!b) return QSGS_ERR_INVALID;
   cudaError_t e = cudaStreamSynchronize(b->stream);

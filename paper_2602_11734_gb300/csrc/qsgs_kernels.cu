@@ -1323,6 +1323,64 @@ cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Front count on library-owned static scratch (no allocation anywhere): the
+// look-back scan of FrontCountPolicy with its run state and tile status
+// words in a file-scope device array instead of a caller workspace.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_front_scratch[kFrontScratchBytes];
+
+uint64_t front_scratch_max_words() {
+  const uint64_t tiles = (kFrontScratchBytes - sizeof(RunState)) / sizeof(unsigned long long) - 2;
+  return tiles * kScanTile;
+}
+
+// The device address of the scratch, looked up once per device with that
+// device current (the lookup may load the module: not inside a capture).
+static cudaError_t front_scratch(void** ptr) {
+  static void* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_front_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t front_count_static(const Geom& g, const uint32_t* grid, uint32_t spin_limit,
+                               cudaStream_t s, unsigned long long* front, uint32_t* error) {
+  void* base = nullptr;
+  cudaError_t e = front_scratch(&base);
+  if (e != cudaSuccess) return e;
+  RunState* st = static_cast<RunState*>(base);
+  unsigned long long* status =
+      reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(base) + sizeof(RunState));
+  // What must start at zero: the run state (front count, tile dispenser,
+  // epoch, error) and the status word of every tile this grid uses.
+  const uint64_t tiles = ((uint64_t)g.nwords + kScanTile - 1) / kScanTile + 2;
+  e = cudaMemsetAsync(base, 0, sizeof(RunState) + tiles * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  Tracer quiet;
+  ScanCtl ctl{st, status, spin_limit};
+  FrontCountPolicy fp{g, st, grid};
+  const uint64_t blocks64 = (uint64_t)num_sms() * 4 < tiles ? (uint64_t)num_sms() * 4 : tiles;
+  const uint32_t blocks = (uint32_t)(blocks64 ? blocks64 : 1);
+  QSGS_LAUNCH(quiet, kClsTrim, s, k_lookback_scan<FrontCountPolicy>, blocks, kScanThreads, fp, ctl);
+  RunState host{};
+  e = cudaMemcpyAsync(&host, st, sizeof(RunState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  *front = host.front_n;
+  *error = host.error;
+  return cudaSuccess;
+}
+
 cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
                                   Tracer& tr, cudaGraphConditionalHandle cond, int use_cond) {
   ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};

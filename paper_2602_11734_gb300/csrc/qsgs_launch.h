@@ -135,6 +135,13 @@ struct StepBuffers {
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
 uint32_t default_grow_blocks();
+// Front count with library-owned static scratch (kFrontScratchBytes of
+// device memory in the library image; no allocation).  Serves grids of up
+// to front_scratch_max_words() words; concurrent calls share the scratch.
+constexpr size_t kFrontScratchBytes = 64 * 1024;
+uint64_t front_scratch_max_words();
+cudaError_t front_count_static(const Geom& g, const uint32_t* grid, uint32_t spin_limit,
+                               cudaStream_t s, unsigned long long* front, uint32_t* error);
 // Per-device function attributes (shared-memory opt-in) of the growth
 // kernels; call before their first launch on the current device.
 cudaError_t prepare_kernels();

@@ -96,6 +96,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_time_grow": ([H, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+                "qsgs_front_count_static": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
                 "qsgs_batch_workspace_bytes": ([ctypes.c_uint32, ctypes.c_uint64], ctypes.c_size_t),
                 "qsgs_batch_create": ([ctypes.c_uint32, ctypes.c_uint64, vp, ctypes.c_size_t, vp,
                                        ctypes.POINTER(H)], ctypes.c_int),
@@ -231,6 +234,16 @@ def qsgs_time_grow(h, grow_blocks: int = 0, reps: int = 5) -> float:
     if rc != QSGS_OK:
         raise QsgsError(rc, "qsgs_time_grow")
     return ms.value
+
+
+def qsgs_front_count_static(grid_ptr: int, nx: int, ny: int, nz: int, stream_ptr: int = 0) -> int:
+    """Front size of a packed device grid; allocates nothing (static scratch)."""
+    out = ctypes.c_uint64()
+    rc = load_library().qsgs_front_count_static(ctypes.c_void_p(grid_ptr), nx, ny, nz,
+                                                ctypes.c_void_p(stream_ptr), ctypes.byref(out))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_front_count_static")
+    return out.value
 
 
 def _check(rc: int, where: str) -> int:
