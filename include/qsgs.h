@@ -202,8 +202,9 @@ int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, doubl
 /* Releases the handle (host memory only).  NULL is ignored. */
 void qsgs_destroy(qsgs_handle* h);
 
-/* Tuning knob: thread blocks of the growth kernel (0 = 8 per SM).  Results
- * do not depend on it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
+/* Tuning knob: thread blocks of the growth kernel (0 = one wave: as many
+ * blocks as all SMs hold at once).  Results do not depend on it.  Returns
+ * QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
 
 /* Tuning probe (no counterpart in the paper): replays the growth kernel of
@@ -302,7 +303,8 @@ int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n);
 /* qsgs_batch_seed + qsgs_batch_advance + qsgs_batch_query. */
 int qsgs_batch_run(qsgs_batch* b, uint32_t max_steps, qsgs_stats* per_member, uint32_t n);
 
-/* Tuning knob: thread blocks of the batched growth kernel (0 = 8 per SM). */
+/* Tuning knob: thread blocks of the batched growth kernel (0 = one wave: as
+ * many blocks as all SMs hold at once). */
 int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks);
 
 /* Event profiler of the batch's own launches (see qsgs_set_profiling);

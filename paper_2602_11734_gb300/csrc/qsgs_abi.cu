@@ -634,7 +634,7 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
                         reinterpret_cast<BatchState*>(b->ws + L.state),
                         reinterpret_cast<unsigned long long*>(b->ws + L.scan_status),
                         reinterpret_cast<uint32_t*>(b->ws + L.list), max_members, max_words};
-  b->grow_blocks = default_grow_blocks();
+  b->grow_blocks = default_batch_grow_blocks();
   b->iters_seen = 0;
   b->graph = nullptr;
   b->graph_exec = nullptr;
@@ -803,7 +803,7 @@ int qsgs_batch_run(qsgs_batch* b, uint32_t max_steps, qsgs_stats* per_member, ui
 
 int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
   if (!b) return QSGS_ERR_INVALID;
-  b->grow_blocks = blocks ? blocks : default_grow_blocks();
+  b->grow_blocks = blocks ? blocks : default_batch_grow_blocks();
   destroy_batch_graph(b);  // the grid size is baked into the graph
   b->graph_tried = false;
   return QSGS_OK;

@@ -944,11 +944,14 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
         uint32_t m = mine[gi];
         const uint32_t q = lane + 32u * gi;        // mask index = word * 7 + block
         const uint32_t tag = ((q / 7u) << 8) | ((q % 7u) << 5);
-        while (m) {
-          const uint32_t lsb = m & (0u - m);
-          const uint32_t i = __popc(lsb - 1u);  // index of the lowest set bit
-          m ^= lsb;
-          S.Q[pos++] = (uint16_t)(tag | i);
+        while (m) {  // two pairs per pass: half the passes of the densest mask
+          const uint32_t l1 = m & (0u - m);
+          m ^= l1;
+          const uint32_t l2 = m & (0u - m);
+          m ^= l2;
+          S.Q[pos] = (uint16_t)(tag | __popc(l1 - 1u));
+          if (l2) S.Q[pos + 1] = (uint16_t)(tag | __popc(l2 - 1u));
+          pos += l2 ? 2u : 1u;
         }
       }
     }
@@ -1305,7 +1308,32 @@ cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, 
   return cudaSuccess;
 }
 
-uint32_t default_grow_blocks() { return (uint32_t)num_sms() * 8; }
+// Resident blocks per SM of a growth kernel (its registers and shared
+// memory decide); the default grids are exactly one wave of them, since the
+// kernels take their chunks from a dispenser.
+template <class K>
+static uint32_t grow_wave(K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGrowThreads,
+                                                    kGrowSmemBytes) != cudaSuccess ||
+      per_sm <= 0) {
+    (void)cudaGetLastError();
+    per_sm = 2;
+  }
+  return (uint32_t)num_sms() * (uint32_t)per_sm;
+}
+
+uint32_t default_grow_blocks() {
+  static uint32_t blocks = 0;
+  if (!blocks) blocks = grow_wave(k_grow);
+  return blocks;
+}
+
+uint32_t default_batch_grow_blocks() {
+  static uint32_t blocks = 0;
+  if (!blocks) blocks = grow_wave(k_grow_batch);
+  return blocks;
+}
 
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {

@@ -134,7 +134,8 @@ struct StepBuffers {
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
-uint32_t default_grow_blocks();
+uint32_t default_grow_blocks();        // one wave of k_grow (after prepare_kernels)
+uint32_t default_batch_grow_blocks();  // one wave of k_grow_batch
 // Front count with library-owned static scratch (kFrontScratchBytes of
 // device memory in the library image; no allocation).  Serves grids of up
 // to front_scratch_max_words() words; concurrent calls share the scratch.
