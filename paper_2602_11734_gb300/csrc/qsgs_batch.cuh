@@ -25,79 +25,141 @@ __device__ __forceinline__ uint32_t find_member(const MemberDesc* d, uint32_t n,
   return lo;
 }
 
-// Commit over the batch word space (see CommitPolicy).  Prologue mode lists
-// every solid word of each running member (a superset of its front, used
-// when the batch starts or its membership changed); step mode ORs the
-// claims of the members that ran a step into their grids, counts them per
-// member, and lists marked or claimed words.  Also records where each
-// member's entries start in the batch list.
-struct BatchCommitPolicy {
-  MemberDesc* d;
-  BatchState* bs;
-  uint32_t* list;
-  int prologue;
-  struct Item {
-    uint32_t w;      // member-local word (0xFFFFFFFF: outside every member)
-    uint32_t bits;   // 1: listed
-    uint32_t extra;  // member index
-    uint32_t c;      // claims of this step in the word
-    uint32_t old;    // the word before the claims
-    uint32_t flags;  // 1: lane 0 clears the warp's mark word; 2: clear the other claim word
-  };
-  __device__ bool active() const { return true; }
-  __device__ bool emit_empty() const { return true; }
-  __device__ uint32_t n_items() const { return bs->total_words; }
-  __device__ uint32_t side(const Item&, int) const { return 0; }
-  __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ Item load(uint32_t i, bool valid) const {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t n = bs->n_members;
-    const uint32_t m = find_member(d, n, valid ? i : 0u,
-                                   [](const MemberDesc& x) { return x.word_base; });
-    const MemberDesc& md = d[m];
-    const uint32_t w = i - md.word_base;
-    const bool in_range = valid && i < md.word_end;
-    const RunState* st = md.st;
-    uint32_t keep = 0, c = 0, old = 0, flags = 0;
-    if (prologue) {
-      if (in_range && st->status == kRunning) keep = md.grid[w] ? 1u : 0u;
-    } else if (st->active) {
-      uint32_t mk = 0;
-      if (lane == 0 && in_range) mk = md.mark[w >> 5];
-      mk = __shfl_sync(0xffffffffu, mk, 0);
-      if (in_range) {
-        const uint32_t par = st->t & 1u;
-        c = md.aux[(size_t)par * md.g.nwords + w];
-        const uint32_t other = md.aux[(size_t)(par ^ 1u) * md.g.nwords + w];
-        old = md.grid[w];
-        keep = ((mk >> lane) & 1u) | (c ? 1u : 0u);
-        flags = (lane == 0 && mk ? 1u : 0u) | (other ? 2u : 0u);
+// Commit over the batch word space (the work of k_commit, per member).
+// Prologue mode lists every solid word of each running member (a superset
+// of its front, used when the batch starts or its membership changed);
+// step mode ORs the claims of the members that ran a step into their grids,
+// counts them, and lists marked or claimed words.  Member m's list entries
+// (member-local word indices, any order) go to the batch list from
+// word_base(m) on, counted by its run state's list_next.  A warp takes 8
+// consecutive 32-word groups per iteration (all loads first); groups of one
+// member share one atomic per counter.
+constexpr int kBatchCommitGroups = 8;
+
+// One 32-word group of member md (the slow path, at member boundaries).
+__device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_t gs, bool valid,
+                                                   uint32_t* list, int prologue) {
+  const uint32_t lane = threadIdx.x & 31u;
+  RunState* st = md.st;
+  const uint32_t w = gs + lane - md.word_base;
+  const bool in = valid && gs + lane < md.word_end;
+  bool keep = false;
+  uint32_t c = 0;
+  if (prologue) {
+    keep = in && st->status == kRunning && md.grid[w] != 0;
+  } else if (st->active) {
+    const uint32_t par = st->t & 1u;
+    uint32_t mk = 0;
+    if (lane == 0 && valid) mk = md.mark[(gs - md.word_base) >> 5];
+    if (in) {
+      c = md.aux[(size_t)par * md.g.nwords + w];
+      const uint32_t o = md.aux[(size_t)(par ^ 1u) * md.g.nwords + w];
+      const uint32_t old = md.grid[w];
+      if (o) md.aux[(size_t)(par ^ 1u) * md.g.nwords + w] = 0;
+      if (c) md.grid[w] = old | c;
+    }
+    if (mk) md.mark[(gs - md.word_base) >> 5] = 0;
+    mk = __shfl_sync(0xffffffffu, mk, 0);
+    keep = in && (((mk >> lane) & 1u) || c != 0);
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(c));
+    if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+  uint32_t base = 0;
+  if (lane == 0 && bal) base = atomicAdd(&st->list_next, (uint32_t)__popc(bal));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) list[md.word_base + base + __popc(bal & ((1u << lane) - 1u))] = w;
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_batch_commit(const MemberDesc* __restrict__ d, const BatchState* bs, uint32_t* list,
+                   int prologue) {
+  constexpr int G = kBatchCommitGroups;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = bs->n_members;
+  if (n == 0) return;
+  const uint32_t ngroups = bs->total_words / 32u;  // member ranges are 32-aligned
+  const uint32_t nsuper = (ngroups + G - 1) / G;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nsuper; sg += nwarps) {
+    const uint32_t g0 = sg * G;
+    const uint32_t glast = min(g0 + G, ngroups) - 1;
+    // Members of the first and the last group, searched by two lanes at once.
+    uint32_t mm = 0;
+    if (lane < 2)
+      mm = find_member(d, n, (lane ? glast : g0) * 32u,
+                       [](const MemberDesc& x) { return x.word_base; });
+    const uint32_t m0 = __shfl_sync(0xffffffffu, mm, 0);
+    const uint32_t m1 = __shfl_sync(0xffffffffu, mm, 1);
+    if (m0 != m1) {
+      // A member boundary inside: group by group.
+      uint32_t m = m0;
+      for (uint32_t gi = g0; gi <= glast; ++gi) {
+        while (m + 1 < n && d[m + 1].word_base <= gi * 32u) ++m;  // uniform
+        batch_commit_group(d[m], gi * 32u, true, list, prologue);
       }
+      continue;
     }
-    return Item{in_range ? w : 0xFFFFFFFFu, keep, m, c, old, flags};
-  }
-  // Claims into the member's grid and their count; marks and the previous
-  // claim grid cleared.  All lanes of a warp serve one member.
-  __device__ void apply(const Item& it, bool) const {
-    if (prologue) return;
-    const MemberDesc& md = d[it.extra];
+    // Common case: every group of this warp belongs to one member.
+    const MemberDesc& md = d[m0];
     RunState* st = md.st;
-    if (!st->active) return;  // uniform over the warp
-    if (it.w != 0xFFFFFFFFu) {
-      if (it.flags & 1u) md.mark[it.w >> 5] = 0;
-      if (it.flags & 2u) md.aux[(size_t)((st->t & 1u) ^ 1u) * md.g.nwords + it.w] = 0;
-      if (it.c) md.grid[it.w] = it.old | it.c;
+    const uint32_t* grid = md.grid;
+    const uint32_t lw0 = g0 * 32u - md.word_base;  // member-local first word
+    const uint32_t nloc = md.word_end - md.word_base;
+    uint32_t bal[G];
+    if (prologue) {
+      if (st->status != kRunning) continue;
+      uint32_t v[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const uint32_t w = lw0 + j * 32u + lane;
+        v[j] = (g0 + j <= glast && w < nloc) ? grid[w] : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < G; ++j) bal[j] = __ballot_sync(0xffffffffu, v[j] != 0);
+    } else {
+      if (!st->active) continue;
+      const uint32_t par = st->t & 1u;
+      uint32_t* cur = md.aux + (size_t)par * md.g.nwords;
+      uint32_t* nxt = md.aux + (size_t)(par ^ 1u) * md.g.nwords;
+      uint32_t c[G], o[G], old[G], mk = 0;
+      if (lane < (uint32_t)G && g0 + lane <= glast) mk = md.mark[(lw0 >> 5) + lane];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const uint32_t w = lw0 + j * 32u + lane;
+        const bool in = g0 + j <= glast && w < nloc;
+        c[j] = in ? cur[w] : 0u;
+        o[j] = in ? nxt[w] : 0u;
+        old[j] = in ? grid[w] : 0u;
+      }
+      if (mk) md.mark[(lw0 >> 5) + lane] = 0;
+      uint32_t claims = 0;
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const uint32_t w = lw0 + j * 32u + lane;
+        if (o[j]) nxt[w] = 0;
+        if (c[j]) md.grid[w] = old[j] | c[j];
+        claims += (uint32_t)__popc(c[j]);
+        const uint32_t mkw = __shfl_sync(0xffffffffu, mk, j);
+        bal[j] = __ballot_sync(0xffffffffu, ((mkw >> lane) & 1u) || c[j] != 0);
+      }
+      const uint32_t wc = __reduce_add_sync(0xffffffffu, claims);
+      if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
     }
-    const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(it.c));
-    if ((threadIdx.x & 31u) == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
+    uint32_t total = 0;
+#pragma unroll
+    for (int j = 0; j < G; ++j) total += (uint32_t)__popc(bal[j]);
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(&st->list_next, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      if ((bal[j] >> lane) & 1u) list[md.word_base + base + __popc(bal[j] & lt)] = lw0 + j * 32u + lane;
+      base += (uint32_t)__popc(bal[j]);
+    }
   }
-  __device__ uint32_t count(const Item& it) const { return it.bits; }
-  __device__ void emit(const Item& it, unsigned long long off) const {
-    if (it.w == 0) d[it.extra].list_base = (uint32_t)off;
-    if (it.bits) list[off] = it.w;
-  }
-  __device__ void total(unsigned long long n) const { bs->list_total = (uint32_t)n; }
-};
+}
 
 // Thread per member: per-member step budget of this advance.
 __global__ void k_batch_limits(MemberDesc* d, BatchState* bs) {
@@ -122,6 +184,7 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
   uint32_t chunks = 0;
   if (m < n) {
     RunState* st = d[m].st;
+    const uint32_t list_n = st->list_next;  // appended by the commit just before
     if (prologue) {
       st->front_acc = 0;
       st->claimed = 0;
@@ -129,9 +192,8 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
     } else {
       close_step(st);
     }
-    begin_step(st);
-    const uint32_t next = m + 1 < n ? d[m + 1].list_base : bs->list_total;
-    const uint32_t list_n = next - d[m].list_base;
+    begin_step(st);  // resets list_next for the next commit
+    d[m].list_base = d[m].word_base;
     d[m].list_n = list_n;
     if (st->active) {
       chunks = (list_n + 31u) / 32u;
@@ -169,7 +231,9 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
 
 // Growth over the batch candidate list: warp chunk c belongs to the member
 // whose chunk range holds c, so every warp serves one member at a time.
-__global__ void __launch_bounds__(kGrowThreads, 2)
+// Three blocks per SM like k_grow (the register cap costs a few spilled
+// bytes; measured faster than two blocks per SM).
+__global__ void __launch_bounds__(kGrowThreads, 3)
     k_grow_batch(const MemberDesc* __restrict__ d, BatchState* bs,
                  const uint32_t* __restrict__ list) {
   extern __shared__ uint4 grow_smem_[];

@@ -1160,6 +1160,15 @@ static uint32_t commit_grid(uint64_t nwords) {
   return (uint32_t)(blocks ? blocks : 1);
 }
 
+static uint32_t batch_commit_grid(uint64_t max_words) {
+  const uint64_t supers = (max_words / 32 + kBatchCommitGroups - 1) / kBatchCommitGroups;
+  const uint64_t warps_needed = supers ? supers : 1;
+  uint64_t blocks = (warps_needed + 7) / 8;
+  const uint64_t cap = (uint64_t)num_sms() * 4;
+  if (blocks > cap) blocks = cap;
+  return (uint32_t)(blocks ? blocks : 1);
+}
+
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz) {
   Geom g{};
   g.nx = nx;
@@ -1411,11 +1420,10 @@ cudaError_t front_count_static(const Geom& g, const uint32_t* grid, uint32_t spi
 
 cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
                                   Tracer& tr, cudaGraphConditionalHandle cond, int use_cond) {
-  ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};
+  (void)spin_limit;  // no waits in the batch commit
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_limits, (b.max_members + 255) / 256, 256, b.d, b.bs);
-  BatchCommitPolicy cp{b.d, b.bs, b.list, 1};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<BatchCommitPolicy>, scan_grid(b.max_words),
-              kScanThreads, cp, ctl);
+  QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
+              b.list, 1);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
               1);
   return cudaSuccess;
@@ -1424,12 +1432,11 @@ cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cu
 cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32_t grow_blocks,
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond) {
-  ScanCtl ctl{&b.bs->scan, b.scan_status, spin_limit};
+  (void)spin_limit;
   QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch, grow_blocks, kGrowThreads, kGrowSmemBytes,
                    b.d, b.bs, b.list);
-  BatchCommitPolicy cp{b.d, b.bs, b.list, 0};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<BatchCommitPolicy>, scan_grid(b.max_words),
-              kScanThreads, cp, ctl);
+  QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
+              b.list, 0);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
               0);
   return cudaSuccess;
