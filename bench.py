@@ -41,6 +41,9 @@ PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
 # Philox blocks, scaled by the 1.569e9 blocks of the 400^3 run); to be reset
 # to None whenever the kernel changes.
 K_GROW_TRAFFIC_BYTES = 17.7e6
+# L2 load of the same kernel: lts__throughput of its mid-run launches (ncu
+# --set full, launches 31-32 of the 400^3 run); reset to None with the above.
+K_GROW_L2_PCT = 7.9
 
 
 def parse():
@@ -53,6 +56,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help=">= 1")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving report")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 500^3 sweep report")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="library default launch shapes instead of the autotuner's")
     ap.add_argument("--edge", type=int, default=400,
                     help="grid edge of the timed workload (400 = the reported configuration; "
                          "smaller edges are for profiler captures)")
@@ -162,15 +168,70 @@ def run_reference(a):
     return 0
 
 
-def bench_batch(Q, torch, dev, repeats: int = 2) -> dict:
+def tuned_single(Q, params: dict, enabled: bool) -> dict:
+    """Autotuned growth shape for realizations like ``params`` (cached)."""
+    if not enabled:
+        return {"blocks": 0, "tile": 1, "cached": None}
+    from paper_2602_11734_gb300 import tune
+    return tune.tune_single(params)
+
+
+def bench_sweep(Q, torch, dev, tune_on: bool) -> dict:
+    """The 500^3 sweep: porosity {0.08..0.25} x spacing {10..50}, 25
+    realizations, each single-instance.  Device time of seeding through the
+    exact target per realization, L2 flushed before each."""
+    from paper_2602_11734_gb300 import tune
+    params = workloads.sweep_500()
+    shape = tuned_single(Q, params[0], tune_on)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    g0 = Q.Generator(params[0], device=dev)
+    tune.apply_single(g0, shape)
+    g0.seed()
+    g0.grow()  # warm-up (graph build)
+    g0.close()
+    times, voxels = [], 0
+    for p in params:
+        g = Q.Generator(p, device=dev)
+        tune.apply_single(g, shape)
+        s = g.stream
+        with torch.cuda.stream(s):
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.seed()
+        st = g.grow()
+        e1.record(s)
+        e1.synchronize()
+        assert st.status == Q.QSGS_OK, st
+        times.append(e0.elapsed_time(e1))
+        voxels += p["nx"] * p["ny"] * p["nz"]
+        g.close()
+    return {"workload": "sweep_500", "realizations": len(params),
+            "nodes_per_s": voxels / (sum(times) / 1000.0),
+            "median_ms": statistics.median(times), "max_ms": max(times),
+            "grow_shape": {k: shape[k] for k in ("blocks", "tile", "cached")}}
+
+
+def bench_batch(Q, torch, dev, tune_on: bool, repeats: int = 2) -> dict:
     """96 uneven realizations (edge 128..256, porosity U[0.10,0.30], spacing
     U{10..40}, cd 2e-4) advanced as one batch, against the same 96 run one
     after another on the single-realization path.  Device time of seeding
     through the exact target, L2 flushed before each timed run."""
+    from paper_2602_11734_gb300 import tune
     params = workloads.batch_96()
+    bshape = tune.tune_batch(params) if tune_on else {"blocks": 0, "tile": 1, "cached": None}
     gens = [Q.Generator(p, device=dev) for p in params]
+    # The single path gets the autotuned shape of each member's size class.
+    sshapes = {}
+    for gen, p in zip(gens, params):
+        key = Q.word_count(p).bit_length()
+        if key not in sshapes:
+            sshapes[key] = tuned_single(Q, p, tune_on)
+        tune.apply_single(gen, sshapes[key])
     words = sum(Q.word_count(p) for p in params)
     batch = Q.Batch(len(params), words, device=dev)
+    tune.apply_batch(batch, bshape)
     batch.set_members(gens)
     voxels = sum(p["nx"] * p["ny"] * p["nz"] for p in params)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -210,7 +271,8 @@ def bench_batch(Q, torch, dev, repeats: int = 2) -> dict:
            "single_path_ms": single_ms,
            "single_path_realizations_per_s": len(params) / (single_ms / 1000),
            "speedup_vs_single_path": single_ms / batch_ms,
-           "all_done": all(st.status == Q.QSGS_OK for st in stats)}
+           "all_done": all(st.status == Q.QSGS_OK for st in stats),
+           "grow_shape": {k: bshape.get(k) for k in ("blocks", "tile", "cached")}}
     batch.close()
     for g in gens:
         g.close()
@@ -283,9 +345,12 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    from paper_2602_11734_gb300 import tune
     p = dict(workloads.single_400(), seed=1 + rank, nx=a.edge, ny=a.edge, nz=a.edge)
     n_vox = p["nx"] * p["ny"] * p["nz"]
+    shape = tuned_single(Q, p, not a.no_tune)  # before the timed region (cached per device)
     g = Q.Generator(p, device=dev)
+    tune.apply_single(g, shape)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     s = g.stream
 
@@ -350,7 +415,12 @@ def main():
                 "draws": st_prof.sum_draws, "launches": grow_launches,
                 "mean_launch_ms": grow_ms / max(1, grow_launches),
                 "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
+                "l2_throughput_pct": K_GROW_L2_PCT if a.edge == 400 else None,
                 "phases_ms": {k: round(v[1], 4) for k, v in prof.items()}}
+    growth_ms = sum(prof[k][1] for k in ("grow", "commit", "step_ctl", "epilogue"))
+    rates = {"growth_only_nodes_per_s": n_vox / (growth_ms / 1000.0),
+             "front_voxel_updates_per_s": st_prof.sum_front / (grow_ms / 1000.0),
+             "philox_blocks_per_s": st_prof.sum_draws / (grow_ms / 1000.0)}
 
     # End to end through the C ABI with host buffers: create, seed, grow and
     # copy the uint8 phase map to pinned host memory, every step.
@@ -361,6 +431,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = Q.qsgs_create(p, ws.data_ptr(), ws.numel(), s.cuda_stream)
+        Q.qsgs_set_grow_blocks(h, shape["blocks"])
+        Q.qsgs_set_grow_tile(h, shape["tile"])
         Q.qsgs_seed(h)
         rc, _ = Q.qsgs_grow_until(h, 0)
         Q.qsgs_fetch(h, host.data_ptr(), n_vox, Q.QSGS_FMT_U8, False)
@@ -374,10 +446,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = served = None
+    batched = served = sweep = None
     del g
+    if not a.no_sweep and a.edge == 400:
+        sweep = bench_sweep(Q, torch, dev, not a.no_tune)
     if not a.no_batch:
-        batched = bench_batch(Q, torch, dev)
+        batched = bench_batch(Q, torch, dev, not a.no_tune)
     if not a.no_serve:
         served = bench_serve(torch, dev, 200, (0.75,))
 
@@ -393,10 +467,11 @@ def main():
                        "g_corner": p["g_corner"], "solid_fraction": p["target_solid_fraction"],
                        "growth_steps": st.steps, "seeds": st.n_seeds,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "grow_shape": {k: shape[k] for k in ("blocks", "tile", "cached")},
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_timed, "clocks": clocks, "batched": batched,
-            "served": served,
+            "roofline": roofline, "rates": rates, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_timed, "clocks": clocks, "sweep_500": sweep,
+            "batched": batched, "served": served,
         }), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -207,6 +207,13 @@ void qsgs_destroy(qsgs_handle* h);
  * QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
 
+/* Tuning knob: front tile of the growth kernel -- the number of 32-word
+ * chunks of the candidate list a warp takes per grab from the kernel's
+ * chunk dispenser (1..16; 0 = 1).  Larger tiles mean fewer dispenser
+ * atomics and coarser load balance.  Results do not depend on it.  Returns
+ * QSGS_OK or QSGS_ERR_INVALID. */
+int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks);
+
 /* Tuning probe (no counterpart in the paper): replays the growth kernel of
  * the handle's next step `reps` times with `grow_blocks` thread blocks (0 =
  * default) and writes the mean milliseconds per launch to *ms (host).  The
@@ -306,6 +313,10 @@ int qsgs_batch_run(qsgs_batch* b, uint32_t max_steps, qsgs_stats* per_member, ui
 /* Tuning knob: thread blocks of the batched growth kernel (0 = one wave: as
  * many blocks as all SMs hold at once). */
 int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks);
+
+/* Tuning knob: front tile of the batched growth kernel (as
+ * qsgs_set_grow_tile; 1..16, 0 = 1). */
+int qsgs_batch_set_grow_tile(qsgs_batch* b, uint32_t chunks);
 
 /* Event profiler of the batch's own launches (see qsgs_set_profiling);
  * while on, advances use direct launches instead of the graph. */

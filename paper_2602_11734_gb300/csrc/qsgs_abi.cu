@@ -119,6 +119,7 @@ struct qsgs_handle {
   uint8_t* decision;
   uint32_t k0, k1;
   uint32_t grow_blocks;
+  uint32_t grow_tile;
   bool seeded;
   cudaError_t last_cuda;
   Tracer tracer;
@@ -233,8 +234,9 @@ cudaError_t build_graph(qsgs_handle* h) {
   e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, h->grow_blocks, h->stream,
-                               capture_tracer, cond, 1);
+  cudaError_t le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit,
+                               GrowShape{h->grow_blocks, h->grow_tile}, h->stream, capture_tracer,
+                               cond, 1);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(h->stream, &captured);
   if (le != cudaSuccess) return le;
@@ -283,6 +285,7 @@ struct qsgs_batch {
   std::vector<MemberDesc> host_descs;
   std::vector<RunState> host_states;
   uint32_t grow_blocks;
+  uint32_t grow_tile;
   uint32_t iters_seen;
   cudaGraph_t graph;
   cudaGraphExec_t graph_exec;
@@ -347,7 +350,8 @@ cudaError_t build_batch_graph(qsgs_batch* b) {
   e = cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  le = launch_batch_step(b->buf, kSpinLimit, b->grow_blocks, b->stream, capture_tracer, cond, 1);
+  le = launch_batch_step(b->buf, kSpinLimit, GrowShape{b->grow_blocks, b->grow_tile}, b->stream,
+                         capture_tracer, cond, 1);
   e = cudaStreamEndCapture(b->stream, &captured);
   if (le != cudaSuccess) return le;
   if (e != cudaSuccess) return e;
@@ -433,6 +437,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->k0 = (uint32_t)params->seed;
   h->k1 = (uint32_t)(params->seed >> 32);
   h->grow_blocks = default_grow_blocks();
+  h->grow_tile = 1;
   h->seeded = false;
   h->last_cuda = cudaSuccess;
   h->graph = nullptr;
@@ -489,7 +494,8 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
   } else {
     for (;;) {
       for (uint32_t k = 0; k < kStepsPerSync; ++k) {
-        e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, h->grow_blocks, h->stream, h->tracer,
+        e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, GrowShape{h->grow_blocks, h->grow_tile},
+                        h->stream, h->tracer,
                         (cudaGraphConditionalHandle)0, 0);
         if (e != cudaSuccess) return cuda_fail(h, e);
       }
@@ -635,6 +641,7 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
                         reinterpret_cast<unsigned long long*>(b->ws + L.scan_status),
                         reinterpret_cast<uint32_t*>(b->ws + L.list), max_members, max_words};
   b->grow_blocks = default_batch_grow_blocks();
+  b->grow_tile = 1;
   b->iters_seen = 0;
   b->graph = nullptr;
   b->graph_exec = nullptr;
@@ -742,7 +749,8 @@ int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps) {
   if (e != cudaSuccess) return batch_fail(b, e);
   for (;;) {
     for (uint32_t k = 0; k < kStepsPerSync; ++k) {
-      e = launch_batch_step(b->buf, kSpinLimit, b->grow_blocks, b->stream, b->tracer,
+      e = launch_batch_step(b->buf, kSpinLimit, GrowShape{b->grow_blocks, b->grow_tile}, b->stream,
+                            b->tracer,
                             (cudaGraphConditionalHandle)0, 0);
       if (e != cudaSuccess) return batch_fail(b, e);
     }
@@ -809,6 +817,22 @@ int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
   return QSGS_OK;
 }
 
+int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks) {
+  if (!h || chunks > kMaxGrowTile) return QSGS_ERR_INVALID;
+  h->grow_tile = chunks ? chunks : 1;
+  destroy_graph(h);  // the tile is baked into the graph
+  h->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_batch_set_grow_tile(qsgs_batch* b, uint32_t chunks) {
+  if (!b || chunks > kMaxGrowTile) return QSGS_ERR_INVALID;
+  b->grow_tile = chunks ? chunks : 1;
+  destroy_batch_graph(b);
+  b->graph_tried = false;
+  return QSGS_OK;
+}
+
 int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks) {
   if (!h) return QSGS_ERR_INVALID;
   h->grow_blocks = blocks ? blocks : default_grow_blocks();
@@ -843,10 +867,11 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e == cudaSuccess) e = launch_grow_only(h->g, b, h->k0, h->k1, blocks, h->stream, quiet);
+  const GrowShape shape{blocks, h->grow_tile};
+  if (e == cudaSuccess) e = launch_grow_only(h->g, b, h->k0, h->k1, shape, h->stream, quiet);
   if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
   for (uint32_t k = 0; k < reps && e == cudaSuccess; ++k)
-    e = launch_grow_only(h->g, b, h->k0, h->k1, blocks, h->stream, quiet);
+    e = launch_grow_only(h->g, b, h->k0, h->k1, shape, h->stream, quiet);
   if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float t = 0.f;

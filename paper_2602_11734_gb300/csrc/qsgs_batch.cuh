@@ -235,31 +235,35 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
 // bytes; measured faster than two blocks per SM).
 __global__ void __launch_bounds__(kGrowThreads, 3)
     k_grow_batch(const MemberDesc* __restrict__ d, BatchState* bs,
-                 const uint32_t* __restrict__ list) {
+                 const uint32_t* __restrict__ list, uint32_t tile) {
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
   __shared__ uint4 s_thr[kGrowWarps][7];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = bs->total_chunks, n = bs->n_members;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
-  for (uint32_t c = blockIdx.x * kGrowWarps + warp; c < total;
-       c = next_chunk(&bs->scan.grow_next, nwarps)) {
-    const uint32_t m = find_member(d, n, c, [](const MemberDesc& x) { return x.chunk_base; });
-    const MemberDesc& md = d[m];
-    RunState* st = md.st;
-    const uint32_t t = st->t;
-    const uint32_t live_dirs = live_directions(st);
-    load_thresholds(st, lane, s_thr[warp]);
-    __syncwarp();
-    const uint32_t j = (c - md.chunk_base) * 32u + lane;
-    const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
-    const PhiloxKeys keys = md.keys;
-    uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
-    GrowCounters cnt{0, 0};
-    grow_chunk(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys, smem[warp],
-               cnt);
-    flush_counters(st, cnt);
-    __syncwarp();  // s_thr[warp] is rewritten by the next chunk
+  const uint32_t ntiles = (total + tile - 1) / tile;
+  for (uint32_t ti = blockIdx.x * kGrowWarps + warp; ti < ntiles;
+       ti = next_chunk(&bs->scan.grow_next, nwarps)) {
+    const uint32_t c_end = min(ti * tile + tile, total);
+    for (uint32_t c = ti * tile; c < c_end; ++c) {
+      const uint32_t m = find_member(d, n, c, [](const MemberDesc& x) { return x.chunk_base; });
+      const MemberDesc& md = d[m];
+      RunState* st = md.st;
+      const uint32_t t = st->t;
+      const uint32_t live_dirs = live_directions(st);
+      load_thresholds(st, lane, s_thr[warp]);
+      __syncwarp();
+      const uint32_t j = (c - md.chunk_base) * 32u + lane;
+      const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
+      const PhiloxKeys keys = md.keys;
+      uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
+      GrowCounters cnt{0, 0};
+      grow_chunk(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys, smem[warp],
+                 cnt);
+      flush_counters(st, cnt);
+      __syncwarp();  // s_thr[warp] is rewritten by the next chunk
+    }
   }
   finish_dispenser(&bs->scan.grow_next, &bs->scan.grow_done);
 }

@@ -1012,9 +1012,9 @@ __device__ __forceinline__ void flush_counters(RunState* st, GrowCounters& c) {
   c = GrowCounters{0, 0};
 }
 
-// Chunk dispenser of the growth kernels: a warp's first chunk is its global
-// warp index, later ones come from an atomic counter, so warps that drew
-// cheap chunks take more.  The last block to finish puts the counters back
+// Chunk dispenser of the growth kernels: a warp's first tile (of `tile`
+// consecutive 32-word chunks) is its global warp index, later ones come from
+// an atomic counter, so warps that drew cheap tiles take more.  The last block to finish puts the counters back
 // to zero, which leaves every launch (a graph replay included) starting
 // from a clean dispenser.
 __device__ __forceinline__ uint32_t next_chunk(uint32_t* next, uint32_t nwarps) {
@@ -1036,7 +1036,7 @@ __device__ __forceinline__ void finish_dispenser(uint32_t* next, uint32_t* done)
 
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
-           uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys) {
+           uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys, uint32_t tile) {
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
   __shared__ uint4 s_thr[7];
@@ -1050,11 +1050,16 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
   const uint32_t nchunks = (n + 31) / 32;
+  const uint32_t ntiles = (nchunks + tile - 1) / tile;
   GrowCounters cnt{0, 0};
-  for (uint32_t c = blockIdx.x * kGrowWarps + warp; c < nchunks; c = next_chunk(&st->grow_next, nwarps)) {
-    const uint32_t idx = c * 32u + lane;
-    const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
-    grow_chunk(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
+  for (uint32_t ti = blockIdx.x * kGrowWarps + warp; ti < ntiles;
+       ti = next_chunk(&st->grow_next, nwarps)) {
+    const uint32_t c_end = min(ti * tile + tile, nchunks);
+    for (uint32_t c = ti * tile; c < c_end; ++c) {
+      const uint32_t idx = c * 32u + lane;
+      const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
+      grow_chunk(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
+    }
   }
   flush_counters(st, cnt);
   finish_dispenser(&st->grow_next, &st->grow_done);
@@ -1276,11 +1281,12 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
 }
 
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
+                        uint32_t spin_limit, GrowShape shape, cudaStream_t s, Tracer& tr,
                         cudaGraphConditionalHandle cond, int use_cond) {
   (void)spin_limit;  // no waits in a step of the single-realization path
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
-                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
+                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0),
+                   shape.tile);
   QSGS_LAUNCH(tr, kClsFront, s, k_commit, commit_grid(g.nwords), kCommitThreads, g, b.st, b.grid,
               b.aux, b.mark, b.list);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);
@@ -1345,9 +1351,10 @@ uint32_t default_batch_grow_blocks() {
 }
 
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                             uint32_t grow_blocks, cudaStream_t s, Tracer& tr) {
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, grow_blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
-                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0));
+                             GrowShape shape, cudaStream_t s, Tracer& tr) {
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
+                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0),
+                   shape.tile);
   return cudaSuccess;
 }
 
@@ -1429,12 +1436,12 @@ cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cu
   return cudaSuccess;
 }
 
-cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32_t grow_blocks,
+cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowShape shape,
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond) {
   (void)spin_limit;
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch, grow_blocks, kGrowThreads, kGrowSmemBytes,
-                   b.d, b.bs, b.list);
+  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch, shape.blocks, kGrowThreads, kGrowSmemBytes,
+                   b.d, b.bs, b.list, shape.tile);
   QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
               b.list, 0);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,

@@ -134,6 +134,13 @@ struct StepBuffers {
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
+// Launch shape of a growth kernel: thread blocks, and chunks of 32
+// candidate words a warp takes per dispenser grab (its "front tile").
+struct GrowShape {
+  uint32_t blocks;
+  uint32_t tile;
+};
+constexpr uint32_t kMaxGrowTile = 16;
 uint32_t default_grow_blocks();        // one wave of k_grow (after prepare_kernels)
 uint32_t default_batch_grow_blocks();  // one wave of k_grow_batch
 // Front count with library-owned static scratch (kFrontScratchBytes of
@@ -154,7 +161,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
 // count, the next candidate list) and the step control.  With use_cond, the step control
 // also sets the graph conditional `cond` (while-loop body).
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                        uint32_t spin_limit, uint32_t grow_blocks, cudaStream_t s, Tracer& tr,
+                        uint32_t spin_limit, GrowShape shape, cudaStream_t s, Tracer& tr,
                         cudaGraphConditionalHandle cond, int use_cond);
 // Exact-target trim (a no-op unless the last step overshot Nt) and the
 // front count of the current grid.
@@ -164,7 +171,7 @@ cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, 
 // The growth kernel alone (the timing probe: it is idempotent on the grid,
 // the claim grid and the marks).
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
-                             uint32_t grow_blocks, cudaStream_t s, Tracer& tr);
+                             GrowShape shape, cudaStream_t s, Tracer& tr);
 // Rebuilds a realization's candidate list from its grid (all solid words).
 cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                               cudaStream_t s, Tracer& tr);
@@ -184,7 +191,7 @@ struct BatchBuffers {
 cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
                                   Tracer& tr, cudaGraphConditionalHandle cond, int use_cond);
 // One step of every member that runs: batched growth, commit and control.
-cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, uint32_t grow_blocks,
+cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowShape shape,
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond);
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,

@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_int),
                 "qsgs_destroy": ([H], None),
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_time_grow": ([H, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
                 "qsgs_front_count_static": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_batch_query": ([H, S, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_batch_run": ([H, ctypes.c_uint32, S, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_batch_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_batch_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_batch_set_profiling": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_batch_profile": ([H, ctypes.POINTER(QsgsProfileEntry), ctypes.c_int],
                                        ctypes.c_int),
@@ -246,6 +248,10 @@ def qsgs_front_count_static(grid_ptr: int, nx: int, ny: int, nz: int, stream_ptr
     return out.value
 
 
+def qsgs_version() -> int:
+    return load_library().qsgs_version()
+
+
 def _check(rc: int, where: str) -> int:
     if rc < 0:
         raise QsgsError(rc, where)
@@ -286,6 +292,14 @@ def qsgs_batch_query(b, n: int) -> list[dict]:
 
 def qsgs_batch_set_grow_blocks(b, blocks: int) -> None:
     _check(load_library().qsgs_batch_set_grow_blocks(b, blocks), "qsgs_batch_set_grow_blocks")
+
+
+def qsgs_set_grow_tile(h, chunks: int) -> None:
+    _check(load_library().qsgs_set_grow_tile(h, chunks), "qsgs_set_grow_tile")
+
+
+def qsgs_batch_set_grow_tile(b, chunks: int) -> None:
+    _check(load_library().qsgs_batch_set_grow_tile(b, chunks), "qsgs_batch_set_grow_tile")
 
 
 def qsgs_batch_set_profiling(b, enable: bool) -> None:
@@ -377,6 +391,9 @@ class Generator:
     def set_grow_blocks(self, blocks: int) -> None:
         qsgs_set_grow_blocks(self.handle, blocks)
 
+    def set_grow_tile(self, chunks: int) -> None:
+        qsgs_set_grow_tile(self.handle, chunks)
+
     def time_grow(self, grow_blocks: int = 0, reps: int = 5) -> float:
         return qsgs_time_grow(self.handle, grow_blocks, reps)
 
@@ -440,6 +457,9 @@ class Batch:
 
     def set_grow_blocks(self, blocks: int) -> None:
         qsgs_batch_set_grow_blocks(self.handle, blocks)
+
+    def set_grow_tile(self, chunks: int) -> None:
+        qsgs_batch_set_grow_tile(self.handle, chunks)
 
     def set_profiling(self, enable: bool = True) -> None:
         qsgs_batch_set_profiling(self.handle, enable)

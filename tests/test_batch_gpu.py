@@ -151,3 +151,23 @@ def test_batch_96_instances_golden(Q):
         b.close()
         for g in gens:
             g.close()
+
+
+def test_batch_tile_and_grid_do_not_change_results(oracle, Q, tmp_path, monkeypatch):
+    from paper_2602_11734_gb300 import tune
+    monkeypatch.setenv("QSGS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    rng = np.random.default_rng(11)
+    params = [workloads.random_small(rng, max_edge=28) for _ in range(6)]
+    shape = tune.tune_batch(params, subset=3, repeats=1)
+    assert shape["members_timed"] == 3 and not shape["cached"]
+    for blocks, tile in ((shape["blocks"], shape["tile"]), (40, 16)):
+        b, gens = make_batch(Q, params)
+        try:
+            tune.apply_batch(b, {"blocks": blocks, "tile": tile})
+            stats = b.run()
+            for g, st, p in zip(gens, stats, params):
+                check_member(oracle, g, st, p)
+        finally:
+            b.close()
+            for g in gens:
+                g.close()

@@ -252,3 +252,25 @@ def test_time_grow_probe_leaves_the_run_unchanged(oracle, Q):
                (want.solid_count, want.steps, want.status, int(want.log["front"].sum()))
     finally:
         g.close()
+
+
+def test_autotuned_shape_keeps_results(oracle, Q, tmp_path, monkeypatch):
+    from paper_2602_11734_gb300 import tune
+    monkeypatch.setenv("QSGS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    p = dict(workloads.small_64(), nx=96, ny=90, nz=88, spacing_s=5, seed=17)
+    shape = tune.tune_single(p, reps=2)
+    assert not shape["cached"] and shape["tile"] in tune.TILES
+    assert len(shape["timings_ms"]) == len(tune.candidate_shapes(torch.cuda.get_device_properties(0).multi_processor_count))
+    assert tune.tune_single(p)["cached"]
+    want = oracle.run(p)
+    for blocks, tile in ((shape["blocks"], shape["tile"]), (152, 8), (0, 3)):
+        g = Q.Generator(p)
+        try:
+            tune.apply_single(g, {"blocks": blocks, "tile": tile})
+            g.seed()
+            st = g.grow()
+            assert np.array_equal(g.fetch().cpu().numpy(), want.phase), (blocks, tile)
+            assert (st.solid_count, st.steps, st.sum_front) == \
+                   (want.solid_count, want.steps, int(want.log["front"].sum()))
+        finally:
+            g.close()
