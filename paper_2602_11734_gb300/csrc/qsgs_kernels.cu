@@ -171,7 +171,7 @@ struct SeedCompactPolicy {
   Geom g;
   RunState* st;
   uint32_t* cand;
-  uint32_t k0, k1;
+  PhiloxKeys keys;
   using Item = WordItem;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
@@ -187,17 +187,20 @@ struct SeedCompactPolicy {
       const uint32_t r = fast_div(w, g.div_W);
       const uint32_t xw = w - r * g.W;
       const uint32_t x0 = xw * 32u;
-      const uint32_t len = min(32u, g.nx - x0);
+      const int len = (int)min(32u, g.nx - x0);
       const uint32_t v0 = r * g.nx + x0;
-      uint32_t gcur = v0 >> 2;
-      U4 blk = philox4x32_10(U4{gcur, 0u, 0xFFFFFFFFu, kSeedTag}, k0, k1);
-      for (uint32_t i = 0; i < len; ++i) {
-        const uint32_t v = v0 + i;
-        if ((v >> 2) != gcur) {
-          gcur = v >> 2;
-          blk = philox4x32_10(U4{gcur, 0u, 0xFFFFFFFFu, kSeedTag}, k0, k1);
+      const uint32_t g0 = v0 >> 2;        // first Philox block of the word
+      const int s0 = (int)(v0 & 3u);      // bit i is voxel 4 * (g0 + j) + q with i = 4j + q - s0
+      // The word's 32 voxels touch blocks g0 .. g0 + 8 (g0 + 7 when aligned).
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        if (j == 8 && s0 == 0) break;
+        const U4 blk = philox4x32_10(U4{g0 + (uint32_t)j, 0u, 0xFFFFFFFFu, kSeedTag}, keys);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * j + q - s0;
+          if (i >= 0 && i < len && (unsigned long long)u4_word(blk, q) < t_seed) bits |= 1u << i;
         }
-        if ((unsigned long long)u4_word(blk, (int)(v & 3)) < t_seed) bits |= 1u << i;
       }
     }
     return Item{w, bits, 0u};
@@ -563,46 +566,67 @@ __global__ void k_cell_fill(Geom g, CellGeom cg, const RunState* st, const uint3
 }
 
 // Earlier conflicts of candidate i: candidates j < i at L1 distance < s,
-// found in the 27 cells around i.  count_only: just count them.
-__device__ __forceinline__ uint32_t scan_conflicts(const Geom& g, const CellGeom& cg,
-                                                   const uint32_t* cand, const uint32_t* start,
-                                                   const uint32_t* items, uint32_t i,
-                                                   uint32_t* out) {
+// found in the 27 cells around i.  One warp per candidate: lane c < 27 scans
+// cell c.  Returns the count to every lane; with `out`, the conflicts are
+// written to out[0 .. count) (grouped by cell; the rounds below do not
+// depend on their order).  All 32 lanes must call it together.
+__device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const CellGeom& cg,
+                                                        const uint32_t* cand,
+                                                        const uint32_t* start,
+                                                        const uint32_t* items, uint32_t i,
+                                                        uint32_t* out) {
+  const uint32_t lane = threadIdx.x & 31u;
   uint32_t x, y, z;
   decode_xyz(g, cand[i], x, y, z);
-  const int cx = (int)(x / cg.s), cy = (int)(y / cg.s), cz = (int)(z / cg.s);
-  uint32_t n = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = cz + dz;
-    if (zz < 0 || zz >= (int)cg.ncz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = cy + dy;
-      if (yy < 0 || yy >= (int)cg.ncy) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = cx + dx;
-        if (xx < 0 || xx >= (int)cg.ncx) continue;
-        const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
-        for (uint32_t k = start[cell]; k < start[cell + 1]; ++k) {
-          const uint32_t j = items[k];
-          if (j >= i) continue;
-          uint32_t xj, yj, zj;
-          decode_xyz(g, cand[j], xj, yj, zj);
-          const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
-          if (l1 >= (int)cg.s) continue;
-          if (out) out[n] = j;
-          ++n;
-        }
-      }
+  uint32_t k0 = 0, k1 = 0;
+  if (lane < 27) {
+    const int xx = (int)(x / cg.s) + (int)(lane % 3u) - 1;
+    const int yy = (int)(y / cg.s) + (int)((lane / 3u) % 3u) - 1;
+    const int zz = (int)(z / cg.s) + (int)(lane / 9u) - 1;
+    if (xx >= 0 && xx < (int)cg.ncx && yy >= 0 && yy < (int)cg.ncy && zz >= 0 &&
+        zz < (int)cg.ncz) {
+      const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
+      k0 = start[cell];
+      k1 = start[cell + 1];
     }
   }
-  return n;
+  auto conflicts = [&](uint32_t k, uint32_t& j) {
+    j = items[k];
+    if (j >= i) return false;
+    uint32_t xj, yj, zj;
+    decode_xyz(g, cand[j], xj, yj, zj);
+    const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
+    return l1 < (int)cg.s;
+  };
+  uint32_t mine = 0;
+  for (uint32_t k = k0; k < k1; ++k) {
+    uint32_t j;
+    if (conflicts(k, j)) ++mine;
+  }
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += v;
+  }
+  if (out != nullptr && mine) {
+    uint32_t pos = incl - mine;
+    for (uint32_t k = k0; k < k1; ++k) {
+      uint32_t j;
+      if (conflicts(k, j)) out[pos++] = j;
+    }
+  }
+  return __shfl_sync(0xffffffffu, incl, 31);
 }
 
 __global__ void k_conflict_count(Geom g, CellGeom cg, const RunState* st, const uint32_t* cand,
                                  const uint32_t* start, const uint32_t* items, uint32_t* cnt) {
   const uint32_t n = st->cand_n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    cnt[i] = scan_conflicts(g, cg, cand, start, items, i, nullptr);
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+    const uint32_t c = scan_conflicts_warp(g, cg, cand, start, items, i, nullptr);
+    if ((threadIdx.x & 31u) == 0) cnt[i] = c;
+  }
 }
 
 // Exclusive offsets of the conflict lists (in place: counts -> offsets).
@@ -635,36 +659,44 @@ __global__ void k_conflict_fill(Geom g, CellGeom cg, const RunState* st, const u
                                 uint32_t* adj, unsigned long long cap) {
   if (st->adj_n > cap) return;
   const uint32_t n = st->cand_n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    scan_conflicts(g, cg, cand, start, items, i, adj + off[i]);
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps)
+    scan_conflicts_warp(g, cg, cand, start, items, i, adj + off[i]);
 }
 
 // Rounds over the conflict lists (one block).  Each round settles at least
-// the lowest undecided candidate, so cand_n + 1 rounds always suffice.
+// the lowest undecided candidate, so cand_n + 1 rounds always suffice.  The
+// decisions live in shared memory while they fit (kSpacingSmem candidates),
+// else in the global array; they are copied out at the end.
+constexpr uint32_t kSpacingSmem = 64 * 1024;
+
 __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
                                                             const uint32_t* off,
                                                             const uint32_t* adj,
                                                             uint8_t* decision,
                                                             unsigned long long cap) {
+  extern __shared__ uint8_t s_decision[];
   __shared__ uint32_t s_undecided;
   if (st->adj_n > cap) return;
   const uint32_t n = st->cand_n;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = 0;
+  const bool in_smem = n <= kSpacingSmem;
+  uint8_t* dec = in_smem ? s_decision : decision;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dec[i] = 0;
   __syncthreads();
   for (uint32_t round = 0; round <= n; ++round) {
     if (threadIdx.x == 0) s_undecided = 0;
     __syncthreads();
     uint32_t mine = 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      if (((volatile uint8_t*)decision)[i] != 0) continue;
+      if (((volatile uint8_t*)dec)[i] != 0) continue;
       bool pending = false, rejected = false;
       for (uint32_t k = off[i]; k < off[i + 1]; ++k) {
-        const uint8_t dj = ((volatile uint8_t*)decision)[adj[k]];
+        const uint8_t dj = ((volatile uint8_t*)dec)[adj[k]];
         if (dj == 1) { rejected = true; break; }
         if (dj == 0) pending = true;
       }
-      if (rejected) decision[i] = 2;
-      else if (!pending) decision[i] = 1;
+      if (rejected) dec[i] = 2;
+      else if (!pending) dec[i] = 1;
       else ++mine;
     }
     if (mine) atomicAdd(&s_undecided, mine);
@@ -673,6 +705,8 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
     __syncthreads();
     if (left == 0) break;
   }
+  if (in_smem)
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = s_decision[i];
 }
 
 // Fallback when the conflict lists exceed their buffer: one block runs all
@@ -1221,6 +1255,9 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_spacing_rounds_csr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSpacingSmem);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
@@ -1239,7 +1276,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
                         uint32_t spin_limit, cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
   // Candidates (ascending) into the list buffer.
-  SeedCompactPolicy sp{g, b.st, b.list, k0, k1};
+  SeedCompactPolicy sp{g, b.st, b.list, make_philox_keys((uint64_t)k1 << 32 | k0)};
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<SeedCompactPolicy>, scan_grid(g.nwords),
               kScanThreads, sp, ctl);
   const uint8_t* decision = nullptr;
@@ -1262,8 +1299,8 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
                 kScanThreads, op, ctl);
     QSGS_LAUNCH(tr, kClsSeed, s, k_conflict_fill, blocks, 256, g, cg, b.st, b.list, b.cell_start,
                 b.cell_items, b.conf_off, b.adj, b.adj_cap);
-    QSGS_LAUNCH(tr, kClsSeed, s, k_spacing_rounds_csr, 1, 1024, b.st, b.conf_off, b.adj,
-                b.decision, b.adj_cap);
+    QSGS_LAUNCH_SMEM(tr, kClsSeed, s, k_spacing_rounds_csr, 1, 1024, kSpacingSmem, b.st,
+                     b.conf_off, b.adj, b.decision, b.adj_cap);
     QSGS_LAUNCH(tr, kClsSeed, s, k_spacing_rounds, 1, 1024, g, cg, b.st, b.list, b.cell_start,
                 b.cell_items, b.decision, b.adj_cap);
     decision = b.decision;
@@ -1271,7 +1308,6 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
   AcceptPolicy ap{g, b.st, b.grid, b.list, decision};
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
               ctl);
-  // Initial front (Sec. 2.3 step 2) replaces the candidate list.
   // Initial candidate words (Sec. 2.3 step 2) replace the candidate list.
   CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitInitial};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
