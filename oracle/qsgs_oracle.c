@@ -25,7 +25,7 @@
  *   R4  Directions: the 26 neighbours (6 face, 12 edge, 8 corner) with one
  *       reference probability per class.
  *   R5  Front update: A_{t+1} = prune(A_t U New_t) (Sec. 1 and Sec. 2.3
- *       "appended"), not prune(New_t) alone (the literal Algorithm 3 line).
+ *       "appended"), not prune(New_t) alone (Algorithm 3 read literally).
  *   R6  Non-periodic domain: neighbours outside the grid are neither
  *       candidates (Algorithm 3, "inside domain") nor void.
  *   R7  Seed spacing: candidates are visited in ascending index; one is kept
@@ -273,33 +273,34 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
   uint32_t* merged = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
   if (!A || !A_new || !merged) { free(A); free(A_new); free(merged); return OQ_ERR_NOMEM; }
 
-  /* line 1: the active set (solids with a void neighbour, step 2 of Sec. 2.3) */
+  /* Algorithm 3 starts from the active set: solids with a void neighbour
+   * (step 2 of Sec. 2.3). */
   uint64_t a_n = oq_front(p, phase, A);
   uint32_t t = 0;
   int32_t status;
-  /* line 2: while phi_a < phi_s and A not empty (R10 for the order of the
-   * three exits) */
+  /* Loop while phi_a < phi_s and A is not empty (R10 for the order of the
+   * three exits). */
   for (;;) {
     if (c >= nt) { status = OQ_DONE; break; }
     if (t >= max_steps) { status = OQ_MAX_STEPS; break; }
     uint64_t thr[3];
     for (int k = 0; k < 3; ++k) thr[k] = oq_threshold(t_ref[k], nt, c); /* Eq. 1 */
-    uint64_t new_n = 0, live = 0;                                        /* line 3 */
-    for (int d = 0; d < 26; ++d) {                                       /* line 4 */
+    uint64_t new_n = 0, live = 0;  /* A_new starts empty each step */
+    for (int d = 0; d < 26; ++d) {   /* every direction of every front voxel */
       for (uint64_t i = 0; i < a_n; ++i) {
         uint64_t a = A[i], q;
-        /* line 5: neighbours inside the domain; line 6: still void */
+        /* neighbours inside the domain that are still void */
         if (!neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q)) continue;
         if (phase[q] != 0) continue;
         if (thr[cls[d]] == 0) continue; /* this attempt cannot succeed */
         ++live;
-        /* line 8: an independent draw for this (source, step, direction) */
+        /* an independent draw for this (source, step, direction) */
         uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
         uint32_t r[4];
         oq_philox4x32_10(ctr, key, r);
         if ((uint64_t)r[d & 3] < thr[cls[d]]) {
-          phase[q] = 1;                 /* line 9  */
-          A_new[new_n++] = (uint32_t)q; /* line 10 */
+          phase[q] = 1;  /* the void becomes solid ... */
+          A_new[new_n++] = (uint32_t)q;  /* ... and joins A_new */
         }
       }
     }
@@ -313,15 +314,16 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
       log[t].claimed = new_n;
       for (int k = 0; k < 3; ++k) log[t].thr[k] = thr[k];
     }
-    /* line 14: prune(A U A_new) -- duplicates cannot occur, A_new is sorted
-     * so that the exact-target trim (R8) keeps its lowest indices. */
+    /* The next front is prune(A U A_new) (R1) -- duplicates cannot occur;
+     * A_new is sorted so that the exact-target trim (R8) keeps its lowest
+     * indices. */
     qsort(A_new, (size_t)new_n, sizeof(uint32_t), cmp_u32);
     if (c + new_n > nt) {
       uint64_t keep = nt - c;
       for (uint64_t i = keep; i < new_n; ++i) phase[A_new[i]] = 0;
       new_n = keep;
     }
-    c += new_n; /* line 15: phi_a from the updated phase array */
+    c += new_n; /* phi_a of the updated phase array */
     uint64_t i = 0, j = 0, m = 0;
     while (i < a_n || j < new_n) {
       uint32_t v;
