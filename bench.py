@@ -72,6 +72,28 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def rank_workload(rank: int, edge: int) -> dict:
+    """The 400^3 parameters (at ``edge``^3) with this rank's own seed:
+    ranks generate independent realizations (replicas, weak scaling)."""
+    return dict(workloads.single_400(), seed=1 + rank, nx=edge, ny=edge, nz=edge)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value (timing is max over ranks); no-op on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the max time."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -346,7 +368,7 @@ def main():
             torch.distributed.barrier()
 
     from paper_2602_11734_gb300 import tune
-    p = dict(workloads.single_400(), seed=1 + rank, nx=a.edge, ny=a.edge, nz=a.edge)
+    p = rank_workload(rank, a.edge)
     n_vox = p["nx"] * p["ny"] * p["nz"]
     shape = tuned_single(Q, p, not a.no_tune)  # before the timed region (cached per device)
     g = Q.Generator(p, device=dev)
@@ -384,12 +406,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     del launches0
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n_vox * a.steps * world / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(times), world, dev)
+    value = job_rate(n_vox * a.steps, world, total_ms)
 
     # Kernel-level pass with the library's event profiler (not timed above).
     # k_grow is bound by integer ALU work: one Philox4x32-10 block per
