@@ -172,10 +172,10 @@ constexpr uint64_t kDyPacked = pack_dir_field(1);
 constexpr uint64_t kDzPacked = pack_dir_field(2);
 constexpr uint64_t kClsPacked = pack_dir_field(3);
 
-__host__ __device__ __forceinline__ int dir_dx(int d) { return (int)((kDxPacked >> (2 * d)) & 3) - 1; }
-__host__ __device__ __forceinline__ int dir_dy(int d) { return (int)((kDyPacked >> (2 * d)) & 3) - 1; }
-__host__ __device__ __forceinline__ int dir_dz(int d) { return (int)((kDzPacked >> (2 * d)) & 3) - 1; }
-__host__ __device__ __forceinline__ int dir_cls(int d) { return (int)((kClsPacked >> (2 * d)) & 3); }
+__host__ __device__ constexpr int dir_dx(int d) { return (int)((kDxPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ constexpr int dir_dy(int d) { return (int)((kDyPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ constexpr int dir_dz(int d) { return (int)((kDzPacked >> (2 * d)) & 3) - 1; }
+__host__ __device__ constexpr int dir_cls(int d) { return (int)((kClsPacked >> (2 * d)) & 3); }
 
 __host__ __device__ __forceinline__ int nb_pos(int dx, int dy, int dz) {
   return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);

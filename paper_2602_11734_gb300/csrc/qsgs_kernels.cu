@@ -825,8 +825,8 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
 template <int DZ, int DY>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
-                                          uint32_t self, uint32_t live_dirs, uint32_t (&V)[28],
-                                          uint32_t (&Bm)[7], uint32_t& front) {
+                                          uint32_t self, const uint32_t (&live)[3],
+                                          uint32_t (&V)[28], uint32_t (&Bm)[7], uint32_t& front) {
   const int yy = (int)y + DY, zz = (int)z + DZ;
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
@@ -844,16 +844,16 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
   constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
   front |= vm | vp;
-  V[dm] = vm & (0u - ((live_dirs >> dm) & 1u));
+  V[dm] = vm & live[dir_cls(dm)];
   Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
     const uint32_t v0 = ~c & self;
     front |= v0;
-    V[d] = v0 & (0u - ((live_dirs >> (d & 31)) & 1u));
+    V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
     Bm[(d >> 2) % 7] |= V[d];
   }
-  V[dp] = vp & (0u - ((live_dirs >> dp) & 1u));
+  V[dp] = vp & live[dir_cls(dp)];
   Bm[dp >> 2] |= V[dp];
 }
 
@@ -921,15 +921,18 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     const uint32_t y = r - z * g.ny;
     uint32_t V[28];
     uint32_t front = 0;
-    row_masks<-1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<-1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<-1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<0, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<0, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<0, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<1, -1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<1, 0>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
-    row_masks<1, 1>(g, grid, y, z, r, xw, self, live_dirs, V, Bm, front);
+    // Per class: all ones if its threshold is positive (live), else zero.
+    const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
+                              0u - ((live_dirs >> 18) & 1u)};
+    row_masks<-1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
     cnt.front += __popc(front);
     // A word holding front voxels now may hold some after the step too.
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
