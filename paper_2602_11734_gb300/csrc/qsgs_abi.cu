@@ -30,6 +30,8 @@ struct Layout {
   size_t state, scan_status, grid, aux, mark, list, cell_count, cell_start, cell_items, decision;
   size_t conf_off, adj, total;
   uint64_t adj_cap;
+  uint64_t cand_cap;  // seed candidates the workspace holds
+  uint64_t list_bytes;  // size of the list area (also the u8 fetch staging slab)
   uint64_t ntiles;
   CellGeomHost cg;
 };
@@ -63,11 +65,23 @@ int check_params(const qsgs_params* p, Ints* out) {
   return QSGS_OK;
 }
 
+// Seed candidates a workspace provides for: the number of candidates is
+// Binomial(N, P) with P = floor(cd 2^32) / 2^32, so the mean plus eight
+// standard deviations plus 4096 (capped at N) is exceeded with probability
+// below 1e-15; a run that exceeds it reports QSGS_ERR_WORKSPACE.
+uint64_t candidate_capacity(uint64_t n, double cd) {
+  const double pr = std::floor(cd * 4294967296.0) / 4294967296.0;
+  const double mean = (double)n * pr;
+  const double cap = mean + 8.0 * std::sqrt(mean * (1.0 - pr)) + 4096.0;
+  return cap >= (double)n ? n : (uint64_t)std::ceil(cap);
+}
+
 Layout make_layout(const qsgs_params* p) {
   Layout L{};
   const uint64_t n = (uint64_t)p->nx * p->ny * p->nz;
   const uint64_t W = (p->nx + 31) / 32;
   const uint64_t nwords = W * p->ny * p->nz;
+  L.cand_cap = candidate_capacity(n, p->cd);
   uint64_t ncells = 0;
   if (p->spacing_s >= 2) {
     const uint32_t s = p->spacing_s;
@@ -83,17 +97,19 @@ Layout make_layout(const qsgs_params* p) {
   L.grid = off; off = align_up(off + nwords * 4);
   L.aux = off; off = align_up(off + 2 * nwords * 4);  // claim grids of even / odd steps
   L.mark = off; off = align_up(off + (nwords / 32 + 1) * 4);
-  // Seed candidates (at most N), then the candidate word list (at most
-  // nwords); u32 entries.
-  const uint64_t list_bytes = (n > nwords ? n : nwords) * 4;
-  L.list = off; off = align_up(off + list_bytes);
+  // Seed candidates (at most cand_cap), then the candidate word list (at
+  // most nwords); u32 entries.
+  L.list_bytes = (L.cand_cap > nwords ? L.cand_cap : nwords) * 4;
+  L.list = off; off = align_up(off + L.list_bytes);
   if (ncells) {
+    const uint64_t cap = L.cand_cap;
     L.cell_count = off; off = align_up(off + ncells * 4);
     L.cell_start = off; off = align_up(off + (ncells + 1) * 4);
-    L.cell_items = off; off = align_up(off + n * 4);
-    L.decision = off; off = align_up(off + n);
-    L.conf_off = off; off = align_up(off + (n + 1) * 4);
-    L.adj_cap = n;
+    L.cell_items = off; off = align_up(off + cap * 4);
+    L.decision = off; off = align_up(off + cap);
+    L.conf_off = off; off = align_up(off + (cap + 1) * 4);
+    // Conflict lists: 16 per candidate (more: the list-free fallback runs).
+    L.adj_cap = 16 * cap < n ? 16 * cap : n;
     L.adj = off; off = align_up(off + L.adj_cap * 4);
   }
   L.total = off;
@@ -153,6 +169,7 @@ int read_state(qsgs_handle* h, RunState* out) {
   e = h->tracer.collect();
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (out->error & kErrTimeout) return QSGS_ERR_TIMEOUT;
+  if (out->error & kErrOverflow) return QSGS_ERR_WORKSPACE;
   return QSGS_OK;
 }
 
@@ -193,7 +210,7 @@ int seed_on_stream(qsgs_handle* h, cudaStream_t stream) {
   SeedBuffers b{h->st,         h->scan_status, h->grid,     h->aux,
                 h->list,       h->mark,        h->cell_count,  h->cell_start, h->cell_items,
                 h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
-                h->L.cg};
+                h->L.cand_cap, h->L.cg};
   e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->seeded = true;
@@ -534,15 +551,23 @@ int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_devi
   } else if (fmt == QSGS_FMT_U8) {
     if (bytes < n) return QSGS_ERR_INVALID;
     if (dst_is_device) {
-      e = launch_unpack_u8(h->g, h->grid, static_cast<uint8_t*>(dst), h->stream, h->tracer);
+      e = launch_unpack_u8(h->g, h->grid, static_cast<uint8_t*>(dst), 0, n, h->stream,
+                           h->tracer);
     } else {
       RunState s{};
       const int rc = read_state(h, &s);
       if (rc != QSGS_OK) return rc;
       if (s.status == kRunning) return QSGS_ERR_STATE;  // the front area is still live
+      // Staged through the candidate-list area in slabs of its size (the
+      // stream orders each slab's copy before the next slab's unpack).
       uint8_t* staging = reinterpret_cast<uint8_t*>(h->list);
-      e = launch_unpack_u8(h->g, h->grid, staging, h->stream, h->tracer);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(dst, staging, n, kind, h->stream);
+      const size_t slab = (size_t)(h->L.list_bytes & ~(uint64_t)15);
+      for (size_t vb = 0; vb < n && e == cudaSuccess; vb += slab) {
+        const size_t ve = vb + slab < n ? vb + slab : n;
+        e = launch_unpack_u8(h->g, h->grid, staging, vb, ve, h->stream, h->tracer);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(static_cast<uint8_t*>(dst) + vb, staging, ve - vb, kind, h->stream);
+      }
     }
   } else {
     return QSGS_ERR_INVALID;
@@ -797,6 +822,7 @@ int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n) {
   int rc = QSGS_OK;
   for (size_t m = 0; m < nm; ++m) {
     if (b->host_states[m].error & kErrTimeout) rc = QSGS_ERR_TIMEOUT;
+    if (b->host_states[m].error & kErrOverflow) rc = QSGS_ERR_WORKSPACE;
     if (m < n) fill_stats(b->members[m], b->host_states[m], &per_member[m]);
   }
   return rc;

@@ -171,6 +171,7 @@ struct SeedCompactPolicy {
   Geom g;
   RunState* st;
   uint32_t* cand;
+  unsigned long long cap;  // entries cand can hold
   PhiloxKeys keys;
   using Item = WordItem;
   __device__ uint32_t side(const Item&, int) const { return 0; }
@@ -206,8 +207,15 @@ struct SeedCompactPolicy {
     return Item{w, bits, 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
-  __device__ void emit(const Item& it, unsigned long long off) const { emit_word_bits(g, it, cand, off); }
-  __device__ void total(unsigned long long n) const { st->cand_n = (uint32_t)n; }
+  __device__ void emit(const Item& it, unsigned long long off) const {
+    if (off + __popc(it.bits) <= cap) emit_word_bits(g, it, cand, off);
+  }
+  // More candidates than the workspace holds (probability < 1e-15): the run
+  // reports an overflow and keeps going on the first cap candidates.
+  __device__ void total(unsigned long long n) const {
+    if (n > cap) atomicOr(&st->error, kErrOverflow);
+    st->cand_n = (uint32_t)(n > cap ? cap : n);
+  }
 };
 
 // The candidate word list that drives the growth kernel: words that may
@@ -1145,29 +1153,31 @@ cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thre
 // ---------------------------------------------------------------------------
 // Fetch: bit grid -> uint8 phase map (x fastest), 16 voxels per thread.
 // ---------------------------------------------------------------------------
-__global__ void k_unpack_u8(Geom g, const uint32_t* grid, uint8_t* out) {
-  const unsigned long long n = g.n;
+__global__ void k_unpack_u8(Geom g, const uint32_t* grid, uint8_t* out, unsigned long long vb,
+                            unsigned long long ve) {
+  // Voxels [vb, ve) of the grid into out[0 .. ve - vb).
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x * 16ull;
-  for (unsigned long long v0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * 16ull;
-       v0 < n; v0 += stride) {
+  for (unsigned long long v0 = vb + ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * 16ull;
+       v0 < ve; v0 += stride) {
     uint32_t r = fast_div((uint32_t)v0, g.div_nx);
     uint32_t x = (uint32_t)v0 - r * g.nx;
     uint8_t b[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       b[k] = 0;
-      if (v0 + k < n) b[k] = (uint8_t)((grid[(size_t)r * g.W + (x >> 5)] >> (x & 31)) & 1u);
+      if (v0 + k < ve) b[k] = (uint8_t)((grid[(size_t)r * g.W + (x >> 5)] >> (x & 31)) & 1u);
       if (++x == g.nx) { x = 0; ++r; }
     }
-    if (v0 + 16 <= n && ((reinterpret_cast<uintptr_t>(out + v0) & 15u) == 0)) {
+    uint8_t* o = out + (v0 - vb);
+    if (v0 + 16 <= ve && ((reinterpret_cast<uintptr_t>(o) & 15u) == 0)) {
       uint4 pk;
       pk.x = b[0] | (b[1] << 8) | (b[2] << 16) | ((uint32_t)b[3] << 24);
       pk.y = b[4] | (b[5] << 8) | (b[6] << 16) | ((uint32_t)b[7] << 24);
       pk.z = b[8] | (b[9] << 8) | (b[10] << 16) | ((uint32_t)b[11] << 24);
       pk.w = b[12] | (b[13] << 8) | (b[14] << 16) | ((uint32_t)b[15] << 24);
-      *reinterpret_cast<uint4*>(out + v0) = pk;
+      *reinterpret_cast<uint4*>(o) = pk;
     } else {
-      for (int k = 0; k < 16 && v0 + k < n; ++k) out[v0 + k] = b[k];
+      for (int k = 0; k < 16 && v0 + k < ve; ++k) o[k] = b[k];
     }
   }
 }
@@ -1279,7 +1289,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
                         uint32_t spin_limit, cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
   // Candidates (ascending) into the list buffer.
-  SeedCompactPolicy sp{g, b.st, b.list, make_philox_keys((uint64_t)k1 << 32 | k0)};
+  SeedCompactPolicy sp{g, b.st, b.list, b.cand_cap, make_philox_keys((uint64_t)k1 << 32 | k0)};
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<SeedCompactPolicy>, scan_grid(g.nwords),
               kScanThreads, sp, ctl);
   const uint8_t* decision = nullptr;
@@ -1351,14 +1361,15 @@ cudaError_t launch_set_step_limit(RunState* st, uint32_t extra, cudaStream_t s, 
   return cudaSuccess;
 }
 
-cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
-                             Tracer& tr) {
-  const uint64_t chunks = ((uint64_t)g.n + 15) / 16;
+cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint64_t vb,
+                             uint64_t ve, cudaStream_t s, Tracer& tr) {
+  const uint64_t chunks = (ve - vb + 15) / 16;
   uint64_t blocks = (chunks + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  QSGS_LAUNCH(tr, kClsFetch, s, k_unpack_u8, (uint32_t)blocks, 256, g, grid, out);
+  QSGS_LAUNCH(tr, kClsFetch, s, k_unpack_u8, (uint32_t)blocks, 256, g, grid, out,
+              (unsigned long long)vb, (unsigned long long)ve);
   return cudaSuccess;
 }
 

@@ -121,6 +121,7 @@ struct SeedBuffers {
   uint32_t* conf_off;            // cand_n + 1 conflict-list offsets
   uint32_t* adj;                 // conflict lists
   unsigned long long adj_cap;    // entries adj can hold
+  unsigned long long cand_cap;   // seed candidates list, cell_items and decision hold
   CellGeomHost cg;
 };
 
@@ -196,7 +197,8 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowSh
                               int use_cond);
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
                                unsigned long long* out, cudaStream_t s);
-cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, cudaStream_t s,
-                             Tracer& tr);
+// Voxels [vb, ve) of the grid as one byte each into out[0 .. ve - vb).
+cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint64_t vb,
+                             uint64_t ve, cudaStream_t s, Tracer& tr);
 
 }  // namespace qsgs

@@ -34,6 +34,20 @@ def single_400() -> dict:
     return _base(400, 1e-4, 30, 0.80, 1)
 
 
+# Size sweep in the setting of the paper's throughput figure (Sec. 3.2,
+# Fig. 3): seed probability 2e-4, one reference probability 8e-4 for every
+# direction class, porosity 0.20, diamond spacing s = 15 (Fig. 3a) or none
+# (Fig. 3b), edges 200 .. 1000.
+FIG3_EDGES = (200, 300, 400, 500, 600, 700, 800, 900, 1000)
+
+
+def fig3_size(n: int, spacing: bool, seed: int = 1) -> dict:
+    """One realization of the size sweep at n^3 (spacing s = 15 or 0)."""
+    return dict(nx=n, ny=n, nz=n, cd=2e-4, g_face=8e-4, g_edge=8e-4, g_corner=8e-4,
+                spacing_s=15 if spacing else 0, target_solid_fraction=0.80, target_count=0,
+                seed=seed, max_steps=0)
+
+
 SWEEP_POROSITY = (0.08, 0.12, 0.16, 0.20, 0.25)
 SWEEP_SPACING = (10, 20, 30, 40, 50)
 

@@ -67,12 +67,24 @@ def test_invalid_params_rejected(lib, bad):
 
 
 def test_workspace_bytes(lib):
+    def words(p):
+        return ((p["nx"] + 31) // 32) * p["ny"] * p["nz"]
+
+    for p in (workloads.small_64(), workloads.single_400(), workloads.fig3_size(1000, True),
+              workloads.fig3_size(1000, False)):
+        b = Q.qsgs_workspace_bytes(p)
+        # grid + two claim grids + the candidate word list, 4 B per word each
+        assert b >= 16 * words(p), p
+        # nothing per voxel: the seed arrays scale with the candidate count
+        n = p["nx"] * p["ny"] * p["nz"]
+        cand = n * p["cd"] + 8 * (n * p["cd"]) ** 0.5 + 4096
+        assert b <= 17 * words(p) + 40 * cand + 8 * (n // max(2, p["spacing_s"]) ** 3) + (1 << 20), p
     small = Q.qsgs_workspace_bytes(workloads.small_64())
-    assert small >= 4 * 64**3
-    big = Q.qsgs_workspace_bytes(workloads.single_400())
-    assert big >= 4 * 400**3 + 2 * 4 * 13 * 400 * 400
     with_spacing = Q.qsgs_workspace_bytes(dict(workloads.small_64(), spacing_s=5))
     assert with_spacing > small
+    # every voxel a candidate (cd = 1): the capacity is N itself
+    dense = dict(workloads.small_64(), cd=1.0, spacing_s=3)
+    assert Q.qsgs_workspace_bytes(dense) >= 64**3 * (4 + 4 + 1 + 4)
 
 
 def test_create_rejects_bad_workspace_without_touching_the_device(lib):

@@ -274,3 +274,22 @@ def test_autotuned_shape_keeps_results(oracle, Q, tmp_path, monkeypatch):
                    (want.solid_count, want.steps, int(want.log["front"].sum()))
         finally:
             g.close()
+
+
+def test_host_u8_fetch_in_slabs(oracle, Q):
+    # The host u8 fetch is staged through the candidate-list area, which is
+    # smaller than the grid in bytes: several slabs, ragged last one.
+    p = dict(workloads.small_64(), nx=77, ny=45, nz=61, cd=0.001, spacing_s=4, seed=23)
+    assert Q.word_count(p) * 4 < p["nx"] * p["ny"] * p["nz"]
+    want = oracle.run(p)
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        g.grow()
+        host = torch.empty(g.shape, dtype=torch.uint8, pin_memory=True)
+        g.fetch(out=host)
+        dev = g.fetch()
+        assert np.array_equal(host.numpy(), want.phase)
+        assert torch.equal(dev.cpu(), host)
+    finally:
+        g.close()
