@@ -131,9 +131,13 @@ int qsgs_check_params(const qsgs_params* params, uint64_t* nt, uint64_t* t_seed,
                       uint64_t t_ref[3]);
 
 /* Device workspace bytes needed for params (0 if params are invalid).  The
- * workspace holds the run state, two bit grids of nz*ny*ceil(nx/32) words,
- * the front list (N words) and, when spacing_s >= 2, the spacing scratch.
- * Host only. */
+ * workspace holds the run state, the bit grid and two claim grids of
+ * nz*ny*ceil(nx/32) words each, the candidate list (the larger of that word
+ * count and the seed-candidate capacity) and, when spacing_s >= 2, the
+ * spacing scratch.  Seed arrays are sized for the Bernoulli candidate count
+ * (N cd plus eight standard deviations plus 4096, at most N): a realization
+ * with more candidates -- probability below 1e-15 -- makes qsgs_grow_until
+ * and qsgs_query return QSGS_ERR_WORKSPACE.  Host only. */
 size_t qsgs_workspace_bytes(const qsgs_params* params);
 
 /* Binds a realization to a caller-allocated device workspace.
@@ -160,7 +164,8 @@ int qsgs_seed(qsgs_handle* h);
  * steps have run in this call (0 = no per-call limit).  Blocks until the
  * stream has finished them and fills *out (may be NULL).
  * Returns the status (QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING)
- * or QSGS_ERR_STATE (not seeded), QSGS_ERR_CUDA, QSGS_ERR_TIMEOUT. */
+ * or QSGS_ERR_STATE (not seeded), QSGS_ERR_CUDA, QSGS_ERR_TIMEOUT,
+ * QSGS_ERR_WORKSPACE (more seed candidates than the workspace holds). */
 int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out);
 
 /* Copies the phase map out.
@@ -170,12 +175,14 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out);
  *   fmt            QSGS_FMT_U8 or QSGS_FMT_PACKED
  * Blocks until the copy is complete.  Returns QSGS_OK, QSGS_ERR_INVALID
  * (fmt or size), QSGS_ERR_STATE or QSGS_ERR_CUDA.  A U8 fetch to the host
- * stages through the front-list area of the workspace, so it is only
- * allowed when the realization has finished (status != QSGS_RUNNING). */
+ * stages through the candidate-list area of the workspace in slabs of its
+ * size, so it is only allowed when the realization has finished (status !=
+ * QSGS_RUNNING). */
 int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_device);
 
 /* Synchronises the handle's stream and fills *out.  Returns QSGS_OK,
- * QSGS_ERR_CUDA or QSGS_ERR_TIMEOUT (a device wait gave up). */
+ * QSGS_ERR_CUDA, QSGS_ERR_TIMEOUT (a device wait gave up) or
+ * QSGS_ERR_WORKSPACE (more seed candidates than the workspace holds). */
 int qsgs_query(qsgs_handle* h, qsgs_stats* out);
 
 /* Turns the event profiler on (enable != 0) or off and clears its totals.
