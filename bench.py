@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving report")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 500^3 sweep report")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the 200^3..1000^3 size sweep in the paper's Fig. 3 setting")
     ap.add_argument("--no-tune", action="store_true",
                     help="library default launch shapes instead of the autotuner's")
     ap.add_argument("--edge", type=int, default=400,
@@ -233,6 +235,41 @@ def bench_sweep(Q, torch, dev, tune_on: bool) -> dict:
             "nodes_per_s": voxels / (sum(times) / 1000.0),
             "median_ms": statistics.median(times), "max_ms": max(times),
             "grow_shape": {k: shape[k] for k in ("blocks", "tile", "cached")}}
+
+
+def bench_sizes(Q, torch, dev) -> dict:
+    """The setting of the paper's throughput figure (Sec. 3.2, Fig. 3): cd
+    2e-4, G_ref 8e-4 for every class, porosity 0.20, edges 200..1000, with
+    diamond spacing s = 15 and without.  One realization per point, device
+    time of seeding through the exact target after an untimed run of the
+    same point, L2 flushed before it; library default launch shape."""
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    points = []
+    for spacing in (True, False):
+        for n in workloads.FIG3_EDGES:
+            p = workloads.fig3_size(n, spacing)
+            g = Q.Generator(p, device=dev)
+            g.seed()
+            g.grow()  # untimed: graph build
+            s = g.stream
+            with torch.cuda.stream(s):
+                flush.fill_(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.seed()
+            st = g.grow()
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            points.append({"edge": n, "spacing_s": p["spacing_s"], "ms": round(ms, 3),
+                           "nodes_per_s": n**3 / (ms / 1000.0), "steps": st.steps,
+                           "exact_target": st.solid_count == st.target_count,
+                           "workspace_mb": round(g.nbytes / 1e6, 1)})
+            g.close()
+    return {"workload": "fig3_sizes", "points": points,
+            "paper_context": "RTX 4060, FP32: s = 15 peak 1.51e7 nodes/s at 600^3; "
+                             "no spacing peak 2.70e7 nodes/s at 800^3 (Fig. 3)"}
 
 
 def bench_batch(Q, torch, dev, tune_on: bool, repeats: int = 2) -> dict:
@@ -464,10 +501,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = served = sweep = None
+    batched = served = sweep = sizes = None
     del g
     if not a.no_sweep and a.edge == 400:
         sweep = bench_sweep(Q, torch, dev, not a.no_tune)
+    if not a.no_sizes and a.edge == 400:
+        sizes = bench_sizes(Q, torch, dev)
     if not a.no_batch:
         batched = bench_batch(Q, torch, dev, not a.no_tune)
     if not a.no_serve:
@@ -489,6 +528,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "rates": rates, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed, "clocks": clocks, "sweep_500": sweep,
+            "size_sweep": sizes,
             "batched": batched, "served": served,
         }), flush=True)
     if world > 1:
