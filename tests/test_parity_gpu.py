@@ -293,3 +293,13 @@ def test_host_u8_fetch_in_slabs(oracle, Q):
         assert torch.equal(dev.cpu(), host)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("spacing", [True, False])
+def test_fig3_setting_small(oracle, Q, spacing):
+    # The size sweep's parameters (one G_ref for every class) on a small box.
+    p = dict(workloads.fig3_size(72, spacing), ny=66, nz=70)
+    want = oracle.run(p)
+    out, st = Q.generate(p)
+    assert np.array_equal(out.cpu().numpy(), want.phase)
+    assert (st.solid_count, st.steps, st.status) == (want.solid_count, want.steps, want.status)
