@@ -275,7 +275,7 @@ cudaError_t build_graph(qsgs_handle* h) {
 constexpr uint32_t kSeedStreams = 8;  // members seeded concurrently
 
 struct BatchLayout {
-  size_t state, descs, scan_status, list, total;
+  size_t state, descs, list, total;
 };
 
 BatchLayout make_batch_layout(uint32_t max_members, uint64_t max_words) {
@@ -283,7 +283,6 @@ BatchLayout make_batch_layout(uint32_t max_members, uint64_t max_words) {
   size_t off = 0;
   L.state = off; off = align_up(off + sizeof(BatchState));
   L.descs = off; off = align_up(off + (size_t)max_members * sizeof(MemberDesc));
-  L.scan_status = off; off = align_up(off + (max_words / kScanTile + 2) * sizeof(unsigned long long));
   L.list = off; off = align_up(off + (max_words ? max_words : 1) * 4);
   L.total = off;
   return L;
@@ -663,7 +662,6 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
   b->ws = static_cast<uint8_t*>(dev_workspace);
   b->buf = BatchBuffers{reinterpret_cast<MemberDesc*>(b->ws + L.descs),
                         reinterpret_cast<BatchState*>(b->ws + L.state),
-                        reinterpret_cast<unsigned long long*>(b->ws + L.scan_status),
                         reinterpret_cast<uint32_t*>(b->ws + L.list), max_members, max_words};
   b->grow_blocks = default_batch_grow_blocks();
   b->grow_tile = 1;

@@ -274,14 +274,13 @@ struct alignas(16) MemberDesc {
 };
 
 struct BatchState {
-  RunState scan;          // look-back scan control (epoch, dispenser, error)
+  RunState scan;          // growth chunk dispenser, control-launch counter (iters)
   uint32_t n_members;
   uint32_t total_words;   // end of the batch word space
-  uint32_t list_total;    // entries of the batch candidate list
   uint32_t total_chunks;  // growth chunks of this step
   uint32_t any_active;    // some member runs the next step
   uint32_t step_extra;    // per-member step budget of the current advance (0: none)
-  uint32_t pad_[2];
+  uint32_t pad_[3];
 };
 
 }  // namespace qsgs

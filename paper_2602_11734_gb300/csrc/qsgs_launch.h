@@ -180,7 +180,6 @@ cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin
 struct BatchBuffers {
   MemberDesc* d;
   BatchState* bs;
-  unsigned long long* scan_status;
   uint32_t* list;
   uint32_t max_members;
   uint64_t max_words;
