@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-member batch report")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving report")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 500^3 sweep report")
+    ap.add_argument("--no-fullfield", action="store_true",
+                    help="skip the full-field (Algorithm 2) comparator")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the 200^3..1000^3 size sweep in the paper's Fig. 3 setting")
     ap.add_argument("--no-tune", action="store_true",
@@ -235,6 +237,42 @@ def bench_sweep(Q, torch, dev, tune_on: bool) -> dict:
             "nodes_per_s": voxels / (sum(times) / 1000.0),
             "median_ms": statistics.median(times), "max_ms": max(times),
             "grow_shape": {k: shape[k] for k in ("blocks", "tile", "cached")}}
+
+
+def bench_fullfield(Q, torch, dev, shape: dict) -> dict:
+    """Comparator on the same 400^3 workload: the full-field sweep of
+    Algorithm 2 (every voxel draws every direction block each step) against
+    the list-driven step, same realization bit for bit.  Device time of
+    seeding through the exact target, L2 flushed before each run."""
+    from paper_2602_11734_gb300 import tune
+    p = rank_workload(0, 400)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    out = {}
+    for name, mode in (("lists", Q.QSGS_MODE_LIETS), ("fullfield", Q.QSGS_MODE_FULLFIELD)):
+        g = Q.Generator(p, device=dev)
+        tune.apply_single(g, shape)
+        g.set_mode(mode)
+        g.seed()
+        g.grow()  # untimed: graph build
+        s = g.stream
+        with torch.cuda.stream(s):
+            flush.fill_(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.seed()
+        st = g.grow()
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": round(ms, 3), "nodes_per_s": 400**3 / (ms / 1000.0),
+                     "philox_blocks": st.sum_draws, "solid": st.solid_count, "steps": st.steps}
+        g.close()
+    out["speedup_lists_over_fullfield"] = out["fullfield"]["ms"] / out["lists"]["ms"]
+    out["same_realization"] = all(out["lists"][k] == out["fullfield"][k] for k in ("solid", "steps"))
+    out["paper_context"] = ("RTX 4060: LIETS 24 s vs vectorized GPU QSGS 6 min at 400^3 "
+                            "(Sec. 3.2), i.e. ~15x")
+    return out
 
 
 def bench_sizes(Q, torch, dev) -> dict:
@@ -501,8 +539,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = served = sweep = sizes = None
+    batched = served = sweep = sizes = fullfield = None
     del g
+    if not a.no_fullfield and a.edge == 400:
+        fullfield = bench_fullfield(Q, torch, dev, shape)
     if not a.no_sweep and a.edge == 400:
         sweep = bench_sweep(Q, torch, dev, not a.no_tune)
     if not a.no_sizes and a.edge == 400:
@@ -528,7 +568,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "rates": rates, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed, "clocks": clocks, "sweep_500": sweep,
-            "size_sweep": sizes,
+            "size_sweep": sizes, "fullfield_comparator": fullfield,
             "batched": batched, "served": served,
         }), flush=True)
     if world > 1:

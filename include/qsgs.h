@@ -55,6 +55,10 @@ extern "C" {
 #define QSGS_ERR_NOMEM -6     /* host allocation failed                      */
 
 /* ---- fetch formats ---------------------------------------------------- */
+/* Step kernels of a single realization (qsgs_set_mode). */
+#define QSGS_MODE_LIETS 0     /* growth from the front list only (Algorithm 3) */
+#define QSGS_MODE_FULLFIELD 1 /* comparator: full-field sweep (Algorithm 2)   */
+
 #define QSGS_FMT_U8 0     /* uint8[N], 1 = solid, 0 = void, x fastest        */
 #define QSGS_FMT_PACKED 1 /* uint32[nz*ny*W], W = ceil(nx/32): bit (x & 31)
                              of word (y + ny z) W + (x >> 5); bits at
@@ -220,6 +224,17 @@ int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks);
  * atomics and coarser load balance.  Results do not depend on it.  Returns
  * QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks);
+
+/* Comparator switch (Algorithm 2 of Sec. 2.2 against the list-driven
+ * Algorithm 3).  QSGS_MODE_FULLFIELD makes every later growth step of this
+ * handle a full-field sweep: every voxel draws every Philox block each step
+ * (the work of the vectorized procedure, which generates a random field per
+ * direction over the whole grid) and the successes are claimed as in the
+ * list-driven step, so the realization is the same bit for bit; only its
+ * cost and stats.sum_draws (every block drawn) differ.  QSGS_MODE_LIETS
+ * (the default) switches back.  Batches always use the list-driven step;
+ * qsgs_time_grow always times it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
+int qsgs_set_mode(qsgs_handle* h, int mode);
 
 /* Tuning probe (no counterpart in the paper): replays the growth kernel of
  * the handle's next step `reps` times with `grow_blocks` thread blocks (0 =

@@ -136,6 +136,7 @@ struct qsgs_handle {
   uint32_t k0, k1;
   uint32_t grow_blocks;
   uint32_t grow_tile;
+  int mode;  // QSGS_MODE_LIETS or QSGS_MODE_FULLFIELD
   bool seeded;
   cudaError_t last_cuda;
   Tracer tracer;
@@ -253,7 +254,7 @@ cudaError_t build_graph(qsgs_handle* h) {
   if (e != cudaSuccess) return e;
   cudaError_t le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit,
                                GrowShape{h->grow_blocks, h->grow_tile}, h->stream, capture_tracer,
-                               cond, 1);
+                               cond, 1, h->mode == QSGS_MODE_FULLFIELD);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(h->stream, &captured);
   if (le != cudaSuccess) return le;
@@ -454,6 +455,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->k1 = (uint32_t)(params->seed >> 32);
   h->grow_blocks = default_grow_blocks();
   h->grow_tile = 1;
+  h->mode = QSGS_MODE_LIETS;
   h->seeded = false;
   h->last_cuda = cudaSuccess;
   h->graph = nullptr;
@@ -511,8 +513,8 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
     for (;;) {
       for (uint32_t k = 0; k < kStepsPerSync; ++k) {
         e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, GrowShape{h->grow_blocks, h->grow_tile},
-                        h->stream, h->tracer,
-                        (cudaGraphConditionalHandle)0, 0);
+                        h->stream, h->tracer, (cudaGraphConditionalHandle)0, 0,
+                        h->mode == QSGS_MODE_FULLFIELD);
         if (e != cudaSuccess) return cuda_fail(h, e);
       }
       const int rc = read_state(h, &s);
@@ -838,6 +840,16 @@ int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
   b->grow_blocks = blocks ? blocks : default_batch_grow_blocks();
   destroy_batch_graph(b);  // the grid size is baked into the graph
   b->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_set_mode(qsgs_handle* h, int mode) {
+  if (!h || (mode != QSGS_MODE_LIETS && mode != QSGS_MODE_FULLFIELD)) return QSGS_ERR_INVALID;
+  if (mode != h->mode) {
+    h->mode = mode;
+    destroy_graph(h);  // the step kernel is baked into the graph
+    h->graph_tried = false;
+  }
   return QSGS_OK;
 }
 

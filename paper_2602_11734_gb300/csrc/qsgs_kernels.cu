@@ -911,6 +911,34 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
   }
 }
 
+// Bit-parallel over the 32 voxels of word w: the 26 void-target masks V_d
+// (V[26], V[27] zero), the 7 Philox-block masks and the front bits; also the
+// word's row r and word-in-row xw.
+__device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid,
+                                           uint32_t w, uint32_t live_dirs, uint32_t (&V)[28],
+                                           uint32_t (&Bm)[7], uint32_t& front, uint32_t& r,
+                                           uint32_t& xw) {
+  const uint32_t self = __ldg(grid + w);
+  r = fast_div(w, g.div_W);
+  xw = w - r * g.W;
+  const uint32_t z = fast_div(r, g.div_ny);
+  const uint32_t y = r - z * g.ny;
+  // Per class: all ones if its threshold is positive (live), else zero.
+  const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
+                            0u - ((live_dirs >> 18) & 1u)};
+  row_masks<-1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<-1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<-1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  V[26] = 0;
+  V[27] = 0;
+}
+
 // One warp, one chunk of up to 32 candidate words (w = 0xFFFFFFFF: no word
 // for this lane).  All 32 lanes must call it together.
 __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
@@ -922,30 +950,11 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   // Phase 1: masks of this lane's word.
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
   if (w != 0xFFFFFFFFu) {
-    const uint32_t self = __ldg(grid + w);
-    const uint32_t r = fast_div(w, g.div_W);
-    const uint32_t xw = w - r * g.W;
-    const uint32_t z = fast_div(r, g.div_ny);
-    const uint32_t y = r - z * g.ny;
-    uint32_t V[28];
-    uint32_t front = 0;
-    // Per class: all ones if its threshold is positive (live), else zero.
-    const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
-                              0u - ((live_dirs >> 18) & 1u)};
-    row_masks<-1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    uint32_t V[28], front = 0, r, xw;
+    word_masks(g, grid, w, live_dirs, V, Bm, front, r, xw);
     cnt.front += __popc(front);
     // A word holding front voxels now may hold some after the step too.
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
-    V[26] = 0;
-    V[27] = 0;
 #pragma unroll
     for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
     S.w[lane] = w;
@@ -1108,6 +1117,74 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   }
   flush_counters(st, cnt);
   finish_dispenser(&st->grow_next, &st->grow_done);
+}
+
+// ---------------------------------------------------------------------------
+// Comparator: the full-field sweep of Algorithm 2 (Sec. 2.2) with the same
+// keyed draws.  Every voxel draws every Philox block each step -- the cost
+// model of the vectorized procedure, which generates a random field per
+// direction over the whole grid -- and the successes are claimed exactly as
+// in the list-driven step, so the result is the same bit for bit (the
+// oracle pins Algorithm 2 == Algorithm 3).  A thread takes one word, a warp
+// 32 consecutive words.  Counters: |A_t| and the live pairs as in k_grow;
+// sum_draws counts every block drawn.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_grow_fullfield(Geom g, const uint32_t* __restrict__ grid, uint32_t* aux, uint32_t* mark,
+                     RunState* st, const PhiloxKeys keys) {
+  __shared__ uint4 s_thr[7];
+  if (!st->active) return;
+  const uint32_t t = st->t;
+  const uint32_t live_dirs = live_directions(st);
+  load_thresholds(st, threadIdx.x, s_thr);
+  __syncthreads();
+  uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t rounds = (g.nwords + stride - 1) / stride;  // uniform: every lane loops alike
+  uint32_t front_n = 0, live_n = 0;
+  unsigned long long drawn = 0;
+  for (uint32_t k = 0; k < rounds; ++k) {
+    const uint32_t w = k * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= g.nwords) continue;
+    uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
+    word_masks(g, grid, w, live_dirs, V, Bm, front, r, xw);
+    front_n += __popc(front);
+    if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
+    const uint32_t x0 = xw * 32u;
+    const uint32_t len = min(32u, g.nx - x0);
+    const uint32_t v0 = r * g.nx + x0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b) {
+      live_n += __popc(Bm[b]);
+      const uint4 th = s_thr[b];
+      for (uint32_t i = 0; i < len; ++i) {
+        const U4 rnd = philox4x32_10(U4{v0 + i, 0u, t, kGrowTag | (uint32_t)b}, keys);
+        uint32_t win = (((V[4 * b] >> i) & 1u) & (rnd.x <= th.x ? 1u : 0u)) |
+                       ((((V[4 * b + 1] >> i) & 1u) & (rnd.y <= th.y ? 1u : 0u)) << 1) |
+                       ((((V[4 * b + 2] >> i) & 1u) & (rnd.z <= th.z ? 1u : 0u)) << 2) |
+                       ((((V[4 * b + 3] >> i) & 1u) & (rnd.w <= th.w ? 1u : 0u)) << 3);
+        while (win) {
+          const uint32_t j = __ffs(win) - 1;
+          win &= win - 1;
+          const int d = 4 * b + (int)j;
+          const int xi = (int)i + dir_dx(d);
+          const int wq = (int)w + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5);
+          atomicOr(claims + (uint32_t)wq, 1u << (xi & 31));
+        }
+      }
+    }
+    drawn += 7ull * len;
+  }
+  const uint32_t wf = __reduce_add_sync(0xffffffffu, front_n);
+  const uint32_t wl = __reduce_add_sync(0xffffffffu, live_n);
+  unsigned long long wd = drawn;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) wd += __shfl_xor_sync(0xffffffffu, wd, o);
+  if ((threadIdx.x & 31) == 0) {
+    if (wl) atomicAdd(&st->live, (unsigned long long)wl);
+    if (wd) atomicAdd(&st->sum_draws, wd);
+    if (wf) atomicAdd(&st->front_acc, (unsigned long long)wf);
+  }
 }
 
 }  // namespace qsgs
@@ -1331,11 +1408,19 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
 
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, GrowShape shape, cudaStream_t s, Tracer& tr,
-                        cudaGraphConditionalHandle cond, int use_cond) {
+                        cudaGraphConditionalHandle cond, int use_cond, int fullfield) {
   (void)spin_limit;  // no waits in a step of the single-realization path
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
-                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0),
-                   shape.tile);
+  if (fullfield) {
+    const uint64_t need = ((uint64_t)g.nwords + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    const uint32_t blocks = (uint32_t)(need < cap ? (need ? need : 1) : cap);
+    QSGS_LAUNCH(tr, kClsGrow, s, k_grow_fullfield, blocks, 256, g, b.grid, b.aux, b.mark, b.st,
+                make_philox_keys((uint64_t)k1 << 32 | k0));
+  } else {
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g,
+                     b.list, b.grid, b.aux, b.mark, b.st,
+                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+  }
   QSGS_LAUNCH(tr, kClsFront, s, k_commit, commit_grid(g.nwords), kCommitThreads, g, b.st, b.grid,
               b.aux, b.mark, b.list);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);

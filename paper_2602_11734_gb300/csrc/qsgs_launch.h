@@ -163,7 +163,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
 // also sets the graph conditional `cond` (while-loop body).
 cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, GrowShape shape, cudaStream_t s, Tracer& tr,
-                        cudaGraphConditionalHandle cond, int use_cond);
+                        cudaGraphConditionalHandle cond, int use_cond, int fullfield);
 // Exact-target trim (a no-op unless the last step overshot Nt) and the
 // front count of the current grid.
 cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_limit,

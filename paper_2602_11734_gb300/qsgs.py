@@ -24,6 +24,7 @@ QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING = 0, 1, 2, 3
 QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_CUDA = -1, -2, -3
 QSGS_ERR_TIMEOUT, QSGS_ERR_STATE, QSGS_ERR_NOMEM = -4, -5, -6
 QSGS_FMT_U8, QSGS_FMT_PACKED = 0, 1
+QSGS_MODE_LIETS, QSGS_MODE_FULLFIELD = 0, 1
 
 PARAM_KEYS = ("nx", "ny", "nz", "cd", "g_face", "g_edge", "g_corner", "spacing_s",
               "target_solid_fraction", "target_count", "seed", "max_steps")
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_destroy": ([H], None),
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
+                "qsgs_set_mode": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_time_grow": ([H, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
                 "qsgs_front_count_static": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
@@ -298,6 +300,10 @@ def qsgs_set_grow_tile(h, chunks: int) -> None:
     _check(load_library().qsgs_set_grow_tile(h, chunks), "qsgs_set_grow_tile")
 
 
+def qsgs_set_mode(h, mode: int) -> None:
+    _check(load_library().qsgs_set_mode(h, mode), "qsgs_set_mode")
+
+
 def qsgs_batch_set_grow_tile(b, chunks: int) -> None:
     _check(load_library().qsgs_batch_set_grow_tile(b, chunks), "qsgs_batch_set_grow_tile")
 
@@ -393,6 +399,10 @@ class Generator:
 
     def set_grow_tile(self, chunks: int) -> None:
         qsgs_set_grow_tile(self.handle, chunks)
+
+    def set_mode(self, mode: int) -> None:
+        """QSGS_MODE_LIETS (default) or QSGS_MODE_FULLFIELD (comparator)."""
+        qsgs_set_mode(self.handle, mode)
 
     def time_grow(self, grow_blocks: int = 0, reps: int = 5) -> float:
         return qsgs_time_grow(self.handle, grow_blocks, reps)

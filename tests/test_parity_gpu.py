@@ -303,3 +303,32 @@ def test_fig3_setting_small(oracle, Q, spacing):
     out, st = Q.generate(p)
     assert np.array_equal(out.cpu().numpy(), want.phase)
     assert (st.solid_count, st.steps, st.status) == (want.solid_count, want.steps, want.status)
+
+
+@pytest.mark.parametrize("case", [dict(nx=70, ny=66, nz=61, spacing_s=4, seed=3),
+                                  dict(nx=33, ny=90, nz=40, spacing_s=0, seed=8, cd=0.004)])
+def test_fullfield_comparator_is_the_same_realization(oracle, Q, case):
+    # Algorithm 2's full-field sweep on the same keyed draws == Algorithm 3.
+    p = dict(workloads.small_64(), **case)
+    want = oracle.run(p)
+    lists = Q.Generator(p)
+    full = Q.Generator(p)
+    try:
+        lists.seed()
+        a = lists.grow()
+        full.set_mode(Q.QSGS_MODE_FULLFIELD)
+        full.seed()
+        half = full.grow(max(1, want.steps // 2))  # switch modes mid-run as well
+        full.set_mode(Q.QSGS_MODE_LIETS)
+        full.grow(2)
+        full.set_mode(Q.QSGS_MODE_FULLFIELD)
+        b = full.grow()
+        assert half.status == Q.QSGS_RUNNING
+        assert np.array_equal(full.fetch().cpu().numpy(), want.phase)
+        assert torch.equal(full.fetch(), lists.fetch())
+        assert (b.solid_count, b.steps, b.status, b.sum_front, b.front_size) == \
+               (a.solid_count, a.steps, a.status, a.sum_front, a.front_size)
+        assert b.sum_draws > a.sum_draws  # every voxel drew every block
+    finally:
+        lists.close()
+        full.close()
