@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 500^3 sweep report")
     ap.add_argument("--no-fullfield", action="store_true",
                     help="skip the full-field (Algorithm 2) comparator")
+    ap.add_argument("--no-fontainebleau", action="store_true",
+                    help="skip the Fontainebleau benchmark sweep (Sec. 3.3 setting)")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the 200^3..1000^3 size sweep in the paper's Fig. 3 setting")
     ap.add_argument("--no-tune", action="store_true",
@@ -273,6 +275,43 @@ def bench_fullfield(Q, torch, dev, shape: dict) -> dict:
     out["paper_context"] = ("RTX 4060: LIETS 24 s vs vectorized GPU QSGS 6 min at 400^3 "
                             "(Sec. 3.2), i.e. ~15x")
     return out
+
+
+def bench_fontainebleau(Q, torch, dev) -> dict:
+    """The Fontainebleau benchmark of Sec. 3.3, generation only: 500^3,
+    porosity 0.15, S_d from a 225 um grain diameter and 4 um voxels,
+    G_ref 8e-4 for every class, s = 0..40 step 5, five realizations per s.
+    Device time of seeding through the exact target per realization."""
+    runs, per_s = [], {}
+    g0 = Q.Generator(workloads.fontainebleau(0, 0), device=dev)
+    g0.seed()
+    g0.grow()  # untimed warm-up
+    g0.close()
+    for sp in workloads.FONTAINEBLEAU_SPACINGS:
+        for k in range(5):
+            p = workloads.fontainebleau(sp, k)
+            g = Q.Generator(p, device=dev)
+            s = g.stream
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.seed()
+            st = g.grow()
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            assert st.status == Q.QSGS_OK, st
+            runs.append(ms)
+            per_s.setdefault(sp, []).append((ms, st.n_seeds, st.steps))
+            g.close()
+    n = 500**3
+    return {"workload": "fontainebleau_500", "realizations": len(runs),
+            "nodes_per_s": n * len(runs) / (sum(runs) / 1000.0),
+            "seed_probability": workloads.fontainebleau(0, 0)["cd"],
+            "per_spacing": [{"s": sp, "median_ms": round(statistics.median(x[0] for x in v), 3),
+                             "mean_seeds": statistics.mean(x[1] for x in v),
+                             "mean_steps": statistics.mean(x[2] for x in v)}
+                            for sp, v in sorted(per_s.items())]}
 
 
 def bench_sizes(Q, torch, dev) -> dict:
@@ -539,8 +578,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = served = sweep = sizes = fullfield = None
+    batched = served = sweep = sizes = fullfield = fontainebleau = None
     del g
+    if not a.no_fontainebleau and a.edge == 400:
+        fontainebleau = bench_fontainebleau(Q, torch, dev)
     if not a.no_fullfield and a.edge == 400:
         fullfield = bench_fullfield(Q, torch, dev, shape)
     if not a.no_sweep and a.edge == 400:
@@ -569,6 +610,7 @@ def main():
             "roofline": roofline, "rates": rates, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed, "clocks": clocks, "sweep_500": sweep,
             "size_sweep": sizes, "fullfield_comparator": fullfield,
+            "fontainebleau": fontainebleau,
             "batched": batched, "served": served,
         }), flush=True)
     if world > 1:

@@ -48,6 +48,32 @@ def fig3_size(n: int, spacing: bool, seed: int = 1) -> dict:
                 seed=seed, max_steps=0)
 
 
+# The Fontainebleau benchmark of Sec. 3.3: seed probability from the grain
+# diameter, S_d = 6 phi_s Delta^3 / (pi d^3), with voxel size Delta = 4 um;
+# a 500^3 domain, porosity 0.15, one reference probability 8e-4 for every
+# class, spacing s = 0 .. 40 in steps of 5, five realizations per s.  The
+# paper gives a grain diameter range of 200 .. 250 um, not one value; 225 um
+# is taken here.
+FONTAINEBLEAU_SPACINGS = tuple(range(0, 41, 5))
+FONTAINEBLEAU_VOXEL_UM = 4.0
+
+
+def fontainebleau_seed_probability(solid_fraction: float, grain_um: float,
+                                   voxel_um: float = FONTAINEBLEAU_VOXEL_UM) -> float:
+    """S_d = 6 phi_s Delta^3 / (pi d^3)."""
+    return 6.0 * solid_fraction * voxel_um**3 / (np.pi * grain_um**3)
+
+
+def fontainebleau(spacing: int, realization: int, n: int = 500, porosity: float = 0.15,
+                  grain_um: float = 225.0) -> dict:
+    """One realization of the Fontainebleau sweep (seed = 5 * (s / 5) + realization)."""
+    solid = round(1.0 - porosity, 12)
+    return dict(nx=n, ny=n, nz=n, cd=fontainebleau_seed_probability(solid, grain_um),
+                g_face=8e-4, g_edge=8e-4, g_corner=8e-4, spacing_s=spacing,
+                target_solid_fraction=solid, target_count=0,
+                seed=5 * (spacing // 5) + realization, max_steps=0)
+
+
 SWEEP_POROSITY = (0.08, 0.12, 0.16, 0.20, 0.25)
 SWEEP_SPACING = (10, 20, 30, 40, 50)
 

@@ -332,3 +332,15 @@ def test_fullfield_comparator_is_the_same_realization(oracle, Q, case):
     finally:
         lists.close()
         full.close()
+
+
+def test_fontainebleau_setting_small(oracle, Q):
+    # The Sec. 3.3 parameterisation (S_d from the grain diameter, one G_ref)
+    # on a small box with smaller grains, so that it holds several seeds.
+    p = workloads.fontainebleau(5, 1, n=64, grain_um=40.0)
+    assert p["cd"] == pytest.approx(6 * 0.85 * 64 / (np.pi * 40.0**3))
+    want = oracle.run(p)
+    out, st = Q.generate(p)
+    assert np.array_equal(out.cpu().numpy(), want.phase)
+    assert (st.solid_count, st.steps, st.status, st.n_seeds) == \
+           (want.solid_count, want.steps, want.status, want.n_accepted)
