@@ -344,3 +344,27 @@ def test_fontainebleau_setting_small(oracle, Q):
     assert np.array_equal(out.cpu().numpy(), want.phase)
     assert (st.solid_count, st.steps, st.status, st.n_seeds) == \
            (want.solid_count, want.steps, want.status, want.n_accepted)
+
+
+def test_largest_grid_properties(Q):
+    # Close to the 2^32-voxel limit of 32-bit voxel indices, with a ragged
+    # row (one pad bit per row) and a saturated face probability (the Eq. 1
+    # clamp): properties the oracle need not compute at this size.
+    p = dict(workloads.small_64(), nx=2047, ny=2048, nz=1024, cd=2e-6, spacing_s=0,
+             g_face=0.2, g_edge=0.05, g_corner=0.0125, target_solid_fraction=0.3, seed=99)
+    n = p["nx"] * p["ny"] * p["nz"]
+    assert n < 2**32
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        st = g.grow()
+        assert st.status == Q.QSGS_OK
+        assert st.solid_count == st.target_count == int(np.floor(0.3 * n + 0.5))
+        assert 0 < st.n_seeds <= st.n_candidates
+        words = g.fetch(fmt="packed").view(p["nz"] * p["ny"], -1)
+        assert words.shape[1] == 64
+        assert int((words[:, -1] < 0).sum()) == 0          # the pad bit (bit 31) stays 0
+        table = torch.tensor([bin(i).count("1") for i in range(256)], device=words.device)
+        assert int(table[words.contiguous().view(torch.uint8).long()].sum()) == st.solid_count
+    finally:
+        g.close()
