@@ -29,7 +29,7 @@ DONE, STALLED, MAX_STEPS = 0, 1, 2
 
 DEFAULTS = dict(nx=8, ny=8, nz=8, cd=0.0, g_face=0.0, g_edge=0.0, g_corner=0.0,
                 spacing_s=0, target_solid_fraction=0.0, target_count=0, seed=0,
-                max_steps=0)
+                max_steps=0, periodic=0)
 
 
 class OqParams(ctypes.Structure):
@@ -38,7 +38,7 @@ class OqParams(ctypes.Structure):
                 ("g_edge", ctypes.c_double), ("g_corner", ctypes.c_double),
                 ("spacing_s", ctypes.c_uint32), ("target_solid_fraction", ctypes.c_double),
                 ("target_count", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("max_steps", ctypes.c_uint32)]
+                ("max_steps", ctypes.c_uint32), ("periodic", ctypes.c_uint32)]
 
 
 class OqStepLog(ctypes.Structure):

@@ -28,6 +28,10 @@
  *       "appended"), not prune(New_t) alone (Algorithm 3 read literally).
  *   R6  Non-periodic domain: neighbours outside the grid are neither
  *       candidates (Algorithm 3, "inside domain") nor void.
+ *   R11 Periodic option (the roll of Sec. 2.2 and Algorithm 2): with
+ *       periodic = 1 the domain is a torus -- neighbours and the spacing
+ *       distance wrap around every axis -- and every dimension must be at
+ *       least 3, so that the 26 neighbours of a voxel are distinct.
  *   R7  Seed spacing: candidates are visited in ascending index; one is kept
  *       iff it lies outside the diamond (L1 ball of radius s-1, i.e. s-1
  *       dilations with the 6-connected kernel, Sec. 2.3 and Fig. 1 D) of
@@ -100,6 +104,8 @@ int oq_targets(const oq_params* p, uint64_t* nt, uint64_t* t_seed, uint64_t t_re
   const double two32 = 4294967296.0;
   uint64_t n = grid_size(p);
   if (p->nx == 0 || p->ny == 0 || p->nz == 0 || n >= 4294967296ull) return OQ_ERR_INVALID;
+  if (p->periodic > 1) return OQ_ERR_INVALID;
+  if (p->periodic && (p->nx < 3 || p->ny < 3 || p->nz < 3)) return OQ_ERR_INVALID;  /* R11 */
   if (!(p->cd >= 0.0 && p->cd <= 1.0)) return OQ_ERR_INVALID;
   if (!(p->g_face >= 0.0 && p->g_face <= 1.0)) return OQ_ERR_INVALID;
   if (!(p->g_edge >= 0.0 && p->g_edge <= 1.0)) return OQ_ERR_INVALID;
@@ -172,15 +178,18 @@ int oq_spacing(const oq_params* p, const uint32_t* cand, uint64_t n, uint8_t* ac
     int64_t x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
     for (int64_t dz = -r; dz <= r; ++dz) {
       int64_t zz = z + dz;
-      if (zz < 0 || zz >= nz) continue;
+      if (p->periodic) zz = ((zz % nz) + nz) % nz; /* R11: the diamond wraps */
+      else if (zz < 0 || zz >= nz) continue;
       int64_t rz = r - llabs(dz);
       for (int64_t dy = -rz; dy <= rz; ++dy) {
         int64_t yy = y + dy;
-        if (yy < 0 || yy >= ny) continue;
+        if (p->periodic) yy = ((yy % ny) + ny) % ny;
+        else if (yy < 0 || yy >= ny) continue;
         int64_t ry = rz - llabs(dy);
         for (int64_t dx = -ry; dx <= ry; ++dx) {
           int64_t xx = x + dx;
-          if (xx < 0 || xx >= nx) continue;
+          if (p->periodic) xx = ((xx % nx) + nx) % nx;
+          else if (xx < 0 || xx >= nx) continue;
           covered[xx + nx * (yy + ny * zz)] = 1;
         }
       }
@@ -190,13 +199,19 @@ int oq_spacing(const oq_params* p, const uint32_t* cand, uint64_t n, uint8_t* ac
   return 0;
 }
 
-/* Neighbour q of voxel v in direction (dx,dy,dz) if inside the domain (R6). */
+/* Neighbour q of voxel v in direction (dx,dy,dz) if inside the domain (R6);
+ * on the torus every neighbour exists (R11). */
 static int neighbour(const oq_params* p, uint64_t v, int dx, int dy, int dz, uint64_t* q) {
   int64_t nx = p->nx, ny = p->ny, nz = p->nz;
   int64_t x = (int64_t)(v % (uint64_t)nx);
   int64_t y = (int64_t)((v / (uint64_t)nx) % (uint64_t)ny);
   int64_t z = (int64_t)(v / ((uint64_t)nx * (uint64_t)ny));
   x += dx; y += dy; z += dz;
+  if (p->periodic) {
+    x = (x + nx) % nx;
+    y = (y + ny) % ny;
+    z = (z + nz) % nz;
+  }
   if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) return 0;
   *q = (uint64_t)(x + nx * (y + ny * z));
   return 1;
@@ -349,7 +364,7 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
 /* Algorithm 2 (Sec. 2.2), with the same draws as oq_run: each step every
  * solid cell of the start-of-step mask draws in every direction, and the
  * accepted neighbours are OR-ed into the phase array (non-periodic shift,
- * R6).  Stops like Algorithm 3: target reached, no solid cell with a void
+ * R6, or the periodic roll, R11).  Stops like Algorithm 3: target reached, no solid cell with a void
  * neighbour left, or the step limit. */
 int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
   uint64_t nt, t_seed, t_ref[3];

@@ -37,6 +37,7 @@ typedef struct {
   uint64_t target_count;        /* Nt; 0 = derive from phi_s                */
   uint64_t seed;                /* RNG key                                  */
   uint32_t max_steps;           /* 0 = unlimited                            */
+  uint32_t periodic;            /* 1: periodic domain (R11), each dim >= 3  */
 } oq_params;
 
 typedef struct {

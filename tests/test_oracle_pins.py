@@ -538,3 +538,120 @@ def test_growth_counter_layout(oracle, torch_philox):
         assert np.array_equal(r.phase.astype(bool), want)
         checked += 1
     assert checked > 20
+
+
+# --------------------------------------------------------------------------
+# Periodic option (R11): the torus of the roll in Sec. 2.2 / Algorithm 2
+# --------------------------------------------------------------------------
+_OFFSETS = [(dz, dy, dx) for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3)
+            if (dz, dy, dx) != (0, 0, 0)]
+
+
+def _torus_l1(a, b, dims):
+    nx, ny, nz = dims
+    (xa, ya, za), (xb, yb, zb) = ((v % nx, (v // nx) % ny, v // (nx * ny)) for v in (int(a), int(b)))
+    d = 0
+    for u, w, m in ((xa, xb, nx), (ya, yb, ny), (za, zb, nz)):
+        k = abs(u - w)
+        d += min(k, m - k)
+    return d
+
+
+def test_periodic_front_matches_roll_bruteforce(oracle):
+    rng = np.random.default_rng(31)
+    for _ in range(25):
+        nx, ny, nz = (int(v) for v in rng.integers(3, 12, size=3))
+        phase = rng.random((nz, ny, nx)) < rng.uniform(0.2, 0.99)
+        void_near = np.zeros_like(phase)
+        for dz, dy, dx in _OFFSETS:
+            void_near |= np.roll(~phase, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+        got = oracle.front(dict(nx=nx, ny=ny, nz=nz, target_solid_fraction=0.5, periodic=1),
+                           phase.astype(np.uint8))
+        assert np.array_equal(got, np.flatnonzero(phase & void_near))
+
+
+@pytest.mark.parametrize("classes", [(0, 1, 2), (0,), (2,)])
+def test_periodic_unit_probability_growth_is_a_rolled_dilation(oracle, classes):
+    # G = 1 on the torus: after k steps the solid set is the seeds dilated k
+    # times by the class offsets, with np.roll (periodic) shifts.
+    g = [1.0 if c in classes else 0.0 for c in range(3)]
+    rng = np.random.default_rng(8)
+    for trial in range(4):
+        nx, ny, nz = (int(v) for v in rng.integers(3, 13, size=3))
+        n = nx * ny * nz
+        k = int(rng.integers(1, 4))
+        p = dict(nx=nx, ny=ny, nz=nz, cd=0.01, g_face=g[0], g_edge=g[1], g_corner=g[2],
+                 spacing_s=int(rng.integers(0, 4)), target_count=n, seed=trial, max_steps=k,
+                 periodic=1)
+        seeds = _seeds_phase(oracle, p)
+        if not seeds.any():
+            continue
+        offs = [o for o in _OFFSETS if (abs(o[0]) + abs(o[1]) + abs(o[2]) - 1) in classes]
+        want = seeds.copy()
+        for _ in range(k):
+            nxt = want.copy()
+            for o in offs:
+                nxt |= np.roll(want, shift=o, axis=(0, 1, 2))
+            if np.array_equal(nxt, want):
+                break
+            want = nxt
+        r = oracle.run(p)
+        assert np.array_equal(r.phase.astype(bool), want)
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 8])
+def test_periodic_spacing_uses_the_torus_distance(oracle, s):
+    rng = np.random.default_rng(200 + s)
+    for trial in range(5):
+        dims = tuple(int(v) for v in rng.integers(3, 15, size=3))
+        p = dict(nx=dims[0], ny=dims[1], nz=dims[2], spacing_s=s, cd=0.06,
+                 target_solid_fraction=0.5, seed=int(rng.integers(0, 2**32)), periodic=1)
+        cand = oracle.seed_candidates(p)
+        acc = oracle.spacing(p, cand)
+        kept = cand[acc]
+        for i, j in itertools.combinations(range(kept.size), 2):
+            assert _torus_l1(kept[i], kept[j], dims) >= s
+        for i in np.nonzero(~acc)[0]:
+            assert any(_torus_l1(cand[i], k, dims) < s for k in kept if k < cand[i])
+
+
+def test_periodic_list_indexed_equals_full_field(oracle):
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        p = dict(nx=int(rng.integers(3, 14)), ny=int(rng.integers(3, 14)),
+                 nz=int(rng.integers(3, 14)), cd=float(rng.uniform(0.002, 0.05)),
+                 g_face=float(rng.uniform(0, 0.3)), g_edge=float(rng.uniform(0, 0.2)),
+                 g_corner=float(rng.uniform(0, 0.1)), spacing_s=int(rng.integers(0, 5)),
+                 target_solid_fraction=float(rng.uniform(0.2, 0.95)),
+                 seed=int(rng.integers(0, 2**63)), periodic=1)
+        a, b = oracle.run(p), oracle.run_fullfield(p)
+        assert np.array_equal(a.phase, b.phase)
+        assert (a.solid_count, a.steps, a.status, a.front_size) == \
+               (b.solid_count, b.steps, b.status, b.front_size)
+
+
+def test_periodic_needs_three_cells_per_axis(oracle):
+    for dims in ((2, 5, 5), (5, 1, 5), (5, 5, 2)):
+        p = dict(nx=dims[0], ny=dims[1], nz=dims[2], target_solid_fraction=0.5, periodic=1)
+        with pytest.raises(Exception):
+            oracle.run(p)
+    oracle.run(dict(nx=3, ny=3, nz=3, target_solid_fraction=0.5, periodic=1, cd=0.2))
+
+
+def test_periodic_equals_open_domain_away_from_the_faces(oracle):
+    # Draws depend on (seed, voxel, step, direction) only, so a run whose
+    # growth never reaches a face is the same on the torus.
+    rng = np.random.default_rng(40)
+    checked = 0
+    for trial in range(60):
+        p = dict(nx=17, ny=15, nz=16, cd=0.0008, g_face=0.3, g_edge=0.1, g_corner=0.05,
+                 target_count=3000, max_steps=2, seed=trial)
+        seeds = _seeds_phase(oracle, p)
+        zz, yy, xx = np.nonzero(seeds)
+        if len(xx) == 0 or min(xx.min(), yy.min(), zz.min()) < 3 or \
+                xx.max() > 13 or yy.max() > 11 or zz.max() > 12:
+            continue
+        a, b = oracle.run(p), oracle.run(dict(p, periodic=1))
+        assert np.array_equal(a.phase, b.phase)
+        checked += 1
+    assert checked >= 3
