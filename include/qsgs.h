@@ -85,6 +85,9 @@ typedef struct qsgs_params {
   uint64_t target_count;
   uint64_t seed;
   uint32_t max_steps;
+  uint32_t periodic;  /* 0: open domain; 1: periodic (a torus: neighbours and the
+                         spacing distance wrap, the roll of Sec. 2.2); each
+                         dimension must then be >= 3 */
 } qsgs_params;
 
 /* Run statistics.

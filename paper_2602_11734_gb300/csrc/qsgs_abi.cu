@@ -43,6 +43,8 @@ struct Ints {
 int check_params(const qsgs_params* p, Ints* out) {
   if (!p) return QSGS_ERR_INVALID;
   if (p->nx == 0 || p->ny == 0 || p->nz == 0) return QSGS_ERR_INVALID;
+  if (p->periodic > 1) return QSGS_ERR_INVALID;
+  if (p->periodic && (p->nx < 3 || p->ny < 3 || p->nz < 3)) return QSGS_ERR_INVALID;
   const uint64_t n = (uint64_t)p->nx * p->ny * p->nz;
   if (n >= (1ull << 32)) return QSGS_ERR_INVALID;
   const double vals[4] = {p->cd, p->g_face, p->g_edge, p->g_corner};
@@ -85,7 +87,12 @@ Layout make_layout(const qsgs_params* p) {
   uint64_t ncells = 0;
   if (p->spacing_s >= 2) {
     const uint32_t s = p->spacing_s;
-    L.cg = CellGeomHost{s, (p->nx + s - 1) / s, (p->ny + s - 1) / s, (p->nz + s - 1) / s};
+    if (p->periodic) {  // cells of width >= s tile the torus exactly
+      auto cells = [s](uint32_t n) { return n / s ? n / s : 1u; };
+      L.cg = CellGeomHost{s, cells(p->nx), cells(p->ny), cells(p->nz)};
+    } else {
+      L.cg = CellGeomHost{s, (p->nx + s - 1) / s, (p->ny + s - 1) / s, (p->nz + s - 1) / s};
+    }
     ncells = (uint64_t)L.cg.ncx * L.cg.ncy * L.cg.ncz;
   }
   uint64_t max_items = n > nwords ? n : nwords;
@@ -434,7 +441,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   if (!h) return QSGS_ERR_NOMEM;
   h->p = *params;
   h->ints = ints;
-  h->g = make_geom(params->nx, params->ny, params->nz);
+  h->g = make_geom(params->nx, params->ny, params->nz, params->periodic);
   h->L = L;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->ws = static_cast<uint8_t*>(dev_workspace);
@@ -930,7 +937,7 @@ int qsgs_front_count_static(const uint32_t* dev_grid, uint32_t nx, uint32_t ny, 
   const uint64_t words = (uint64_t)((nx + 31u) / 32u) * ny * nz;
   if ((uint64_t)nx * ny * nz > 0xFFFFFFFFull) return QSGS_ERR_INVALID;
   if (words > front_scratch_max_words()) return QSGS_ERR_WORKSPACE;
-  const Geom g = make_geom(nx, ny, nz);
+  const Geom g = make_geom(nx, ny, nz, 0);
   unsigned long long front = 0;
   uint32_t error = 0;
   const cudaError_t e =

@@ -55,6 +55,7 @@ struct Geom {
   uint32_t nwords;   // W * nrows
   uint32_t n;        // nx * ny * nz (< 2^32)
   uint32_t pad_mask; // bits of the last word of a row that lie at x >= nx
+  uint32_t periodic; // 1: neighbours wrap around every axis (a torus)
   FastDiv div_nx, div_ny, div_W;
 };
 

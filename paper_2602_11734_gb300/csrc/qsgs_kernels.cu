@@ -375,6 +375,10 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
 // statistics.  Warp-cooperative: the 32 lanes hold 32 consecutive words,
 // each neighbour row arrives in one coalesced load and the x-1 / x+1 bits
 // come from the neighbouring lanes.
+__device__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid, uint32_t w,
+                           uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7],
+                           uint32_t& front, uint32_t& r, uint32_t& xw);
+
 struct FrontCountPolicy {
   Geom g;
   RunState* st;
@@ -385,6 +389,11 @@ struct FrontCountPolicy {
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w, bool valid) const {
+    if (g.periodic) {  // the torus: the growth kernel's own neighbour masks
+      uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
+      if (valid) word_masks(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
+      return Item{w, front, 0u};
+    }
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t r = fast_div(w, g.div_W);
     const uint32_t xw = w - r * g.W;
@@ -540,7 +549,44 @@ struct CellOffsetPolicy {
 // ---------------------------------------------------------------------------
 struct CellGeom {
   uint32_t s, ncx, ncy, ncz;
+  uint32_t periodic;  // torus: cells of width >= s tile each axis exactly
 };
+
+// Cell of coordinate u on an axis of n voxels and nc cells.  Open domain:
+// width s (the last cell may be narrower).  Torus: nc = max(1, floor(n/s))
+// cells of width >= s, so a point within distance < s of u, across the
+// wrap too, lies in u's cell or one of its two neighbours.
+__device__ __forceinline__ uint32_t cell_coord(const CellGeom& cg, uint32_t u, uint32_t n,
+                                               uint32_t nc) {
+  return cg.periodic ? (uint32_t)(((unsigned long long)u * nc) / n) : u / cg.s;
+}
+
+// Cell cu + du on an axis of nc cells; false if it lies outside the open
+// domain, or repeats a cell already visited on a torus of fewer than 3 cells.
+__device__ __forceinline__ bool cell_step(const CellGeom& cg, int cu, int du, uint32_t nc,
+                                          uint32_t& out) {
+  int v = cu + du;
+  if (cg.periodic) {
+    if ((nc == 1 && du != 0) || (nc == 2 && du == -1)) return false;
+    v = v < 0 ? v + (int)nc : (v >= (int)nc ? v - (int)nc : v);
+  } else if (v < 0 || v >= (int)nc) {
+    return false;
+  }
+  out = (uint32_t)v;
+  return true;
+}
+
+// L1 distance between two voxels, around the torus when periodic.
+__device__ __forceinline__ int spacing_l1(const Geom& g, uint32_t x, uint32_t y, uint32_t z,
+                                          uint32_t xj, uint32_t yj, uint32_t zj) {
+  int dx = abs((int)xj - (int)x), dy = abs((int)yj - (int)y), dz = abs((int)zj - (int)z);
+  if (g.periodic) {
+    dx = min(dx, (int)g.nx - dx);
+    dy = min(dy, (int)g.ny - dy);
+    dz = min(dz, (int)g.nz - dz);
+  }
+  return dx + dy + dz;
+}
 
 __device__ __forceinline__ void decode_xyz(const Geom& g, uint32_t v, uint32_t& x, uint32_t& y,
                                            uint32_t& z) {
@@ -556,7 +602,9 @@ __global__ void k_cell_count(Geom g, CellGeom cg, const RunState* st, const uint
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t x, y, z;
     decode_xyz(g, cand[i], x, y, z);
-    const uint32_t cell = x / cg.s + cg.ncx * (y / cg.s + cg.ncy * (z / cg.s));
+    const uint32_t cell = cell_coord(cg, x, g.nx, cg.ncx) +
+                          cg.ncx * (cell_coord(cg, y, g.ny, cg.ncy) +
+                                    cg.ncy * cell_coord(cg, z, g.nz, cg.ncz));
     atomicAdd(count + cell, 1u);
   }
 }
@@ -567,7 +615,9 @@ __global__ void k_cell_fill(Geom g, CellGeom cg, const RunState* st, const uint3
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t x, y, z;
     decode_xyz(g, cand[i], x, y, z);
-    const uint32_t cell = x / cg.s + cg.ncx * (y / cg.s + cg.ncy * (z / cg.s));
+    const uint32_t cell = cell_coord(cg, x, g.nx, cg.ncx) +
+                          cg.ncx * (cell_coord(cg, y, g.ny, cg.ncy) +
+                                    cg.ncy * cell_coord(cg, z, g.nz, cg.ncz));
     items[atomicAdd(cursor + cell, 1u)] = i;
     decision[i] = 0;
   }
@@ -588,12 +638,12 @@ __device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const Cel
   decode_xyz(g, cand[i], x, y, z);
   uint32_t k0 = 0, k1 = 0;
   if (lane < 27) {
-    const int xx = (int)(x / cg.s) + (int)(lane % 3u) - 1;
-    const int yy = (int)(y / cg.s) + (int)((lane / 3u) % 3u) - 1;
-    const int zz = (int)(z / cg.s) + (int)(lane / 9u) - 1;
-    if (xx >= 0 && xx < (int)cg.ncx && yy >= 0 && yy < (int)cg.ncy && zz >= 0 &&
-        zz < (int)cg.ncz) {
-      const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
+    uint32_t xx, yy, zz;
+    if (cell_step(cg, (int)cell_coord(cg, x, g.nx, cg.ncx), (int)(lane % 3u) - 1, cg.ncx, xx) &&
+        cell_step(cg, (int)cell_coord(cg, y, g.ny, cg.ncy), (int)((lane / 3u) % 3u) - 1, cg.ncy,
+                  yy) &&
+        cell_step(cg, (int)cell_coord(cg, z, g.nz, cg.ncz), (int)(lane / 9u) - 1, cg.ncz, zz)) {
+      const uint32_t cell = xx + cg.ncx * (yy + cg.ncy * zz);
       k0 = start[cell];
       k1 = start[cell + 1];
     }
@@ -603,8 +653,7 @@ __device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const Cel
     if (j >= i) return false;
     uint32_t xj, yj, zj;
     decode_xyz(g, cand[j], xj, yj, zj);
-    const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
-    return l1 < (int)cg.s;
+    return spacing_l1(g, x, y, z, xj, yj, zj) < (int)cg.s;
   };
   uint32_t mine = 0;
   for (uint32_t k = k0; k < k1; ++k) {
@@ -738,25 +787,26 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
       if (((volatile uint8_t*)decision)[i] != 0) continue;
       uint32_t x, y, z;
       decode_xyz(g, cand[i], x, y, z);
-      const int cx = (int)(x / cg.s), cy = (int)(y / cg.s), cz = (int)(z / cg.s);
+      const int cx = (int)cell_coord(cg, x, g.nx, cg.ncx);
+      const int cy = (int)cell_coord(cg, y, g.ny, cg.ncy);
+      const int cz = (int)cell_coord(cg, z, g.nz, cg.ncz);
       bool pending = false, rejected = false;
       for (int dz = -1; dz <= 1 && !rejected; ++dz) {
-        const int zz = cz + dz;
-        if (zz < 0 || zz >= (int)cg.ncz) continue;
+        uint32_t zz;
+        if (!cell_step(cg, cz, dz, cg.ncz, zz)) continue;
         for (int dy = -1; dy <= 1 && !rejected; ++dy) {
-          const int yy = cy + dy;
-          if (yy < 0 || yy >= (int)cg.ncy) continue;
+          uint32_t yy;
+          if (!cell_step(cg, cy, dy, cg.ncy, yy)) continue;
           for (int dx = -1; dx <= 1 && !rejected; ++dx) {
-            const int xx = cx + dx;
-            if (xx < 0 || xx >= (int)cg.ncx) continue;
-            const uint32_t cell = (uint32_t)xx + cg.ncx * ((uint32_t)yy + cg.ncy * (uint32_t)zz);
+            uint32_t xx;
+            if (!cell_step(cg, cx, dx, cg.ncx, xx)) continue;
+            const uint32_t cell = xx + cg.ncx * (yy + cg.ncy * zz);
             for (uint32_t k = start[cell]; k < start[cell + 1]; ++k) {
               const uint32_t j = items[k];
               if (j >= i) continue;  // only earlier candidates matter
               uint32_t xj, yj, zj;
               decode_xyz(g, cand[j], xj, yj, zj);
-              const int l1 = abs((int)xj - (int)x) + abs((int)yj - (int)y) + abs((int)zj - (int)z);
-              if (l1 >= s) continue;
+              if (spacing_l1(g, x, y, z, xj, yj, zj) >= s) continue;
               const uint8_t dj = ((volatile uint8_t*)decision)[j];
               if (dj == 1) { rejected = true; break; }
               if (dj == 0) pending = true;
@@ -835,16 +885,31 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
                                           uint32_t self, const uint32_t (&live)[3],
                                           uint32_t (&V)[28], uint32_t (&Bm)[7], uint32_t& front) {
-  const int yy = (int)y + DY, zz = (int)z + DZ;
+  int yy = (int)y + DY, zz = (int)z + DZ;
+  if (g.periodic) {  // the torus: every row exists
+    yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
+    zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
+  }
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
-    const uint32_t* row = grid + (size_t)((int)r + DY + (int)g.ny * DZ) * g.W;
+    const uint32_t* row = grid + (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
     c = __ldg(row + xw);
     if (xw == g.W - 1) c |= g.pad_mask;
     if (xw > 0) l = __ldg(row + xw - 1);
     if (xw + 1 < g.W) {
       rr = __ldg(row + xw + 1);
       if (xw + 1 == g.W - 1) rr |= g.pad_mask;
+    }
+    if (g.periodic) {
+      // x wraps: voxel nx-1 (bit p of the last word) is the x-1 neighbour of
+      // voxel 0, and voxel 0 the x+1 neighbour of voxel nx-1.
+      const uint32_t p = (g.nx - 1) & 31u;
+      if (xw == 0) l = (__ldg(row + g.W - 1) >> p) << 31;
+      if (xw == g.W - 1) {
+        const uint32_t first = __ldg(row) & 1u;
+        if (p == 31) rr = first;
+        else c = (c & ~(2u << p)) | (first << (p + 1));
+      }
     }
   }
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
@@ -888,6 +953,28 @@ __device__ __forceinline__ uint32_t live_directions(const RunState* st) {
   return live_dirs;
 }
 
+// Word and bit of the d-neighbour of bit i of word w (in the domain, or on
+// the torus).
+__device__ __forceinline__ void claim_target(const Geom& g, uint32_t w, uint32_t i, int d,
+                                             uint32_t& wq, uint32_t& bit) {
+  if (!g.periodic) {
+    const int xi = (int)i + dir_dx(d);  // -1 .. 32: target bit, word carry
+    wq = (uint32_t)((int)w + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5));
+    bit = 1u << (xi & 31);
+    return;
+  }
+  const uint32_t r = fast_div(w, g.div_W);
+  const uint32_t z = fast_div(r, g.div_ny);
+  const int y = (int)(r - z * g.ny) + dir_dy(d);
+  const int zz = (int)z + dir_dz(d);
+  const int x = (int)((w - r * g.W) * 32u + i) + dir_dx(d);
+  const uint32_t xq = x < 0 ? g.nx - 1 : (x >= (int)g.nx ? 0u : (uint32_t)x);
+  const uint32_t yq = y < 0 ? g.ny - 1 : (y >= (int)g.ny ? 0u : (uint32_t)y);
+  const uint32_t zq = zz < 0 ? g.nz - 1 : (zz >= (int)g.nz ? 0u : (uint32_t)zz);
+  wq = (zq * g.ny + yq) * g.W + (xq >> 5);
+  bit = 1u << (xq & 31u);
+}
+
 // Claims of buffered draws: a draw's direction j wins when it passed its
 // threshold and its target is a void in-domain neighbour (bit i of V_{4b+j}).
 __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, const GrowWarpSmem& S,
@@ -898,15 +985,14 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
     const uint4 vm = S.V[owner][b];
     uint32_t win = (x >> 16) & (((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
                                 (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3));
-    const int wo = (int)S.w[owner];
+    const uint32_t wo = S.w[owner];
     while (win) {
       const uint32_t j = __ffs(win) - 1;
       win &= win - 1;
-      const int d = (int)(4u * b + j);
-      const int xi = (int)i + dir_dx(d);  // -1 .. 32: target bit, word carry
-      const int wq = wo + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5);
+      uint32_t wq, bit;
+      claim_target(g, wo, i, (int)(4u * b + j), wq, bit);
       // Fire-and-forget: the claim grid collects New_t; nobody waits.
-      atomicOr(claims + (uint32_t)wq, 1u << (xi & 31));
+      atomicOr(claims + wq, bit);
     }
   }
 }
@@ -917,7 +1003,7 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
 __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                            uint32_t w, uint32_t live_dirs, uint32_t (&V)[28],
                                            uint32_t (&Bm)[7], uint32_t& front, uint32_t& r,
-                                           uint32_t& xw) {
+                                           uint32_t& xw) {  // declared before FrontCountPolicy
   const uint32_t self = __ldg(grid + w);
   r = fast_div(w, g.div_W);
   xw = w - r * g.W;
@@ -1166,10 +1252,9 @@ __global__ void __launch_bounds__(256)
         while (win) {
           const uint32_t j = __ffs(win) - 1;
           win &= win - 1;
-          const int d = 4 * b + (int)j;
-          const int xi = (int)i + dir_dx(d);
-          const int wq = (int)w + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5);
-          atomicOr(claims + (uint32_t)wq, 1u << (xi & 31));
+          uint32_t wq, bit;
+          claim_target(g, w, i, 4 * b + (int)j, wq, bit);
+          atomicOr(claims + wq, bit);
         }
       }
     }
@@ -1298,8 +1383,9 @@ static uint32_t batch_commit_grid(uint64_t max_words) {
   return (uint32_t)(blocks ? blocks : 1);
 }
 
-Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz) {
+Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic) {
   Geom g{};
+  g.periodic = periodic ? 1u : 0u;
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -1371,7 +1457,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
               kScanThreads, sp, ctl);
   const uint8_t* decision = nullptr;
   if (b.cg.s >= 2) {
-    const CellGeom cg{b.cg.s, b.cg.ncx, b.cg.ncy, b.cg.ncz};
+    const CellGeom cg{b.cg.s, b.cg.ncx, b.cg.ncy, b.cg.ncz, g.periodic};
     const uint32_t ncells = cg.ncx * cg.ncy * cg.ncz;
     cudaError_t e = cudaMemsetAsync(b.cell_count, 0, (size_t)ncells * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;

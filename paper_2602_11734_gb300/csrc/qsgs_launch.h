@@ -134,7 +134,7 @@ struct StepBuffers {
   uint32_t* list;  // candidate word list (ascending)
 };
 
-Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz);
+Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic);
 // Launch shape of a growth kernel: thread blocks, and chunks of 32
 // candidate words a warp takes per dispenser grab (its "front tile").
 struct GrowShape {

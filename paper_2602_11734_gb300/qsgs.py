@@ -27,7 +27,7 @@ QSGS_FMT_U8, QSGS_FMT_PACKED = 0, 1
 QSGS_MODE_LIETS, QSGS_MODE_FULLFIELD = 0, 1
 
 PARAM_KEYS = ("nx", "ny", "nz", "cd", "g_face", "g_edge", "g_corner", "spacing_s",
-              "target_solid_fraction", "target_count", "seed", "max_steps")
+              "target_solid_fraction", "target_count", "seed", "max_steps", "periodic")
 
 
 class QsgsParams(ctypes.Structure):
@@ -36,7 +36,7 @@ class QsgsParams(ctypes.Structure):
                 ("g_edge", ctypes.c_double), ("g_corner", ctypes.c_double),
                 ("spacing_s", ctypes.c_uint32), ("target_solid_fraction", ctypes.c_double),
                 ("target_count", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("max_steps", ctypes.c_uint32)]
+                ("max_steps", ctypes.c_uint32), ("periodic", ctypes.c_uint32)]
 
 
 class QsgsStats(ctypes.Structure):
@@ -137,7 +137,7 @@ def make_params(p: dict) -> QsgsParams:
     if unknown:
         raise KeyError(f"unknown parameter(s) {sorted(unknown)}")
     q = dict(nx=1, ny=1, nz=1, cd=0.0, g_face=0.0, g_edge=0.0, g_corner=0.0, spacing_s=0,
-             target_solid_fraction=0.0, target_count=0, seed=0, max_steps=0)
+             target_solid_fraction=0.0, target_count=0, seed=0, max_steps=0, periodic=0)
     q.update(p)
     return QsgsParams(**q)
 

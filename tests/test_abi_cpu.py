@@ -110,3 +110,19 @@ def test_null_handles_are_rejected(lib):
     assert lib.qsgs_query(None, ctypes.byref(s)) == Q.QSGS_ERR_INVALID
     assert lib.qsgs_fetch(None, None, 0, 0, 0) == Q.QSGS_ERR_INVALID
     lib.qsgs_destroy(None)
+
+
+def test_periodic_params_checked_like_the_oracle(lib, oracle):
+    for dims, ok in (((3, 3, 3), True), ((2, 9, 9), False), ((9, 1, 9), False), ((40, 33, 3), True)):
+        p = dict(nx=dims[0], ny=dims[1], nz=dims[2], cd=0.01, target_solid_fraction=0.5, periodic=1)
+        if ok:
+            Q.qsgs_check_params(p)
+            assert Q.qsgs_workspace_bytes(p) > 0
+        else:
+            with pytest.raises(Q.QsgsError) as e:
+                Q.qsgs_check_params(p)
+            assert e.value.code == Q.QSGS_ERR_INVALID
+            with pytest.raises(Exception):
+                oracle.run(p)
+    with pytest.raises(Q.QsgsError):
+        Q.qsgs_check_params(dict(nx=8, ny=8, nz=8, target_solid_fraction=0.5, periodic=2))

@@ -368,3 +368,45 @@ def test_largest_grid_properties(Q):
         assert int(table[words.contiguous().view(torch.uint8).long()].sum()) == st.solid_count
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (5, 7, 4), (31, 9, 10), (32, 12, 9), (33, 10, 11),
+                                  (64, 7, 6), (70, 20, 17), (95, 13, 5)])
+def test_periodic_parity(oracle, Q, dims):
+    # The torus (R11): x wraps inside one word, across words and at ragged
+    # row ends; y and z wrap across rows and planes; spacing wraps too.
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    for s, cd in ((0, 0.02), (3, 0.05), (7, 0.08)):
+        p = dict(workloads.small_64(), nx=nx, ny=ny, nz=nz, spacing_s=s, cd=cd,
+                 g_face=0.05, g_edge=0.02, g_corner=0.01, target_solid_fraction=0.8,
+                 seed=n + s, periodic=1)
+        assert_same(oracle, Q, p)
+
+
+def test_periodic_batch_and_fullfield(oracle, Q):
+    rng = np.random.default_rng(77)
+    params = [dict(workloads.random_small(rng, max_edge=30), periodic=1) for _ in range(5)]
+    params = [dict(p, nx=max(3, p["nx"]), ny=max(3, p["ny"]), nz=max(3, p["nz"])) for p in params]
+    gens = [Q.Generator(p) for p in params]
+    b = Q.Batch(len(params), sum(Q.word_count(p) for p in params))
+    try:
+        b.set_members(gens)
+        for g, st, p in zip(gens, b.run(), params):
+            want = oracle.run(p)
+            assert np.array_equal(g.fetch().cpu().numpy(), want.phase), p
+            assert (st.solid_count, st.steps, st.front_size) == \
+                   (want.solid_count, want.steps, want.front_size), p
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
+    p = params[0]
+    g = Q.Generator(p)
+    try:
+        g.set_mode(Q.QSGS_MODE_FULLFIELD)
+        g.seed()
+        g.grow()
+        assert np.array_equal(g.fetch().cpu().numpy(), oracle.run(p).phase)
+    finally:
+        g.close()
