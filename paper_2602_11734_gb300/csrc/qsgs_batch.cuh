@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       const PhiloxKeys keys = md.keys;
       uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
       GrowCounters cnt{0, 0};
-      grow_chunk(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys, smem[warp],
+      grow_chunk<kRuntime>(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys,
+                           smem[warp],
                  cnt);
       flush_counters(st, cnt);
       __syncwarp();  // s_thr[warp] is rewritten by the next chunk

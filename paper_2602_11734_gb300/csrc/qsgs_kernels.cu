@@ -375,6 +375,16 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
 // statistics.  Warp-cooperative: the 32 lanes hold 32 consecutive words,
 // each neighbour row arrives in one coalesced load and the x-1 / x+1 bits
 // come from the neighbouring lanes.
+// Domain kind of a growth-path instantiation: the open domain (R6), the
+// torus (R11), or read from Geom at run time (batches mix both).
+enum DomainKind : int { kOpen = 0, kTorus = 1, kRuntime = 2 };
+
+template <int DK>
+__device__ __forceinline__ bool on_torus(const Geom& g) {
+  return DK == kRuntime ? g.periodic != 0u : DK == kTorus;
+}
+
+template <int DK>
 __device__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid, uint32_t w,
                            uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7],
                            uint32_t& front, uint32_t& r, uint32_t& xw);
@@ -391,7 +401,7 @@ struct FrontCountPolicy {
   __device__ Item load(uint32_t w, bool valid) const {
     if (g.periodic) {  // the torus: the growth kernel's own neighbour masks
       uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
-      if (valid) word_masks(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
+      if (valid) word_masks<kTorus>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
       return Item{w, front, 0u};
     }
     const uint32_t lane = threadIdx.x & 31u;
@@ -880,13 +890,13 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
 // V masks of the three directions that land in row (y+DY, z+DZ).
 // V masks of the three directions that land in row (y+DY, z+DZ); `front`
 // collects every void neighbour, live class or not.
-template <int DZ, int DY>
+template <int DZ, int DY, int DK>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
                                           uint32_t self, const uint32_t (&live)[3],
                                           uint32_t (&V)[28], uint32_t (&Bm)[7], uint32_t& front) {
   int yy = (int)y + DY, zz = (int)z + DZ;
-  if (g.periodic) {  // the torus: every row exists
+  if (on_torus<DK>(g)) {  // the torus: every row exists
     yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
     zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
   }
@@ -900,7 +910,7 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
       rr = __ldg(row + xw + 1);
       if (xw + 1 == g.W - 1) rr |= g.pad_mask;
     }
-    if (g.periodic) {
+    if (on_torus<DK>(g)) {
       // x wraps: voxel nx-1 (bit p of the last word) is the x-1 neighbour of
       // voxel 0, and voxel 0 the x+1 neighbour of voxel nx-1.
       const uint32_t p = (g.nx - 1) & 31u;
@@ -955,9 +965,10 @@ __device__ __forceinline__ uint32_t live_directions(const RunState* st) {
 
 // Word and bit of the d-neighbour of bit i of word w (in the domain, or on
 // the torus).
+template <int DK>
 __device__ __forceinline__ void claim_target(const Geom& g, uint32_t w, uint32_t i, int d,
                                              uint32_t& wq, uint32_t& bit) {
-  if (!g.periodic) {
+  if (!on_torus<DK>(g)) {
     const int xi = (int)i + dir_dx(d);  // -1 .. 32: target bit, word carry
     wq = (uint32_t)((int)w + (dir_dy(d) + (int)g.ny * dir_dz(d)) * (int)g.W + (xi >> 5));
     bit = 1u << (xi & 31);
@@ -977,6 +988,7 @@ __device__ __forceinline__ void claim_target(const Geom& g, uint32_t w, uint32_t
 
 // Claims of buffered draws: a draw's direction j wins when it passed its
 // threshold and its target is a void in-domain neighbour (bit i of V_{4b+j}).
+template <int DK>
 __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, const GrowWarpSmem& S,
                                            uint32_t nwin, uint32_t lane) {
   for (uint32_t k = lane; k < nwin; k += 32) {
@@ -990,7 +1002,7 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
       const uint32_t j = __ffs(win) - 1;
       win &= win - 1;
       uint32_t wq, bit;
-      claim_target(g, wo, i, (int)(4u * b + j), wq, bit);
+      claim_target<DK>(g, wo, i, (int)(4u * b + j), wq, bit);
       // Fire-and-forget: the claim grid collects New_t; nobody waits.
       atomicOr(claims + wq, bit);
     }
@@ -1000,6 +1012,7 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
 // Bit-parallel over the 32 voxels of word w: the 26 void-target masks V_d
 // (V[26], V[27] zero), the 7 Philox-block masks and the front bits; also the
 // word's row r and word-in-row xw.
+template <int DK>
 __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                            uint32_t w, uint32_t live_dirs, uint32_t (&V)[28],
                                            uint32_t (&Bm)[7], uint32_t& front, uint32_t& r,
@@ -1012,21 +1025,22 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   // Per class: all ones if its threshold is positive (live), else zero.
   const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
                             0u - ((live_dirs >> 18) & 1u)};
-  row_masks<-1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<-1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<-1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, -1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, 0>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, 1>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<-1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<-1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<-1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<0, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  row_masks<1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
   V[26] = 0;
   V[27] = 0;
 }
 
 // One warp, one chunk of up to 32 candidate words (w = 0xFFFFFFFF: no word
 // for this lane).  All 32 lanes must call it together.
+template <int DK>
 __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
                                            uint32_t* claims, uint32_t* mark, uint32_t w,
                                            uint32_t t, uint32_t live_dirs, const uint4* thr,
@@ -1037,7 +1051,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
   if (w != 0xFFFFFFFFu) {
     uint32_t V[28], front = 0, r, xw;
-    word_masks(g, grid, w, live_dirs, V, Bm, front, r, xw);
+    word_masks<DK>(g, grid, w, live_dirs, V, Bm, front, r, xw);
     cnt.front += __popc(front);
     // A word holding front voxels now may hold some after the step too.
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
@@ -1125,13 +1139,13 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
       nwin += __popc(balb);
       if (nwin > (uint32_t)kGrowWins - 64u) {
         __syncwarp();
-        claim_wins(g, claims, S, nwin, lane);
+        claim_wins<DK>(g, claims, S, nwin, lane);
         __syncwarp();
         nwin = 0;
       }
     }
     __syncwarp();
-    claim_wins(g, claims, S, nwin, lane);
+    claim_wins<DK>(g, claims, S, nwin, lane);
     __syncwarp();  // S.Q is refilled by the next round
     done = round_end;
   }
@@ -1174,6 +1188,7 @@ __device__ __forceinline__ void finish_dispenser(uint32_t* next, uint32_t* done)
   }
 }
 
+template <int DK>
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
            uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys, uint32_t tile) {
@@ -1198,7 +1213,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     for (uint32_t c = ti * tile; c < c_end; ++c) {
       const uint32_t idx = c * 32u + lane;
       const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
-      grow_chunk(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
+      grow_chunk<DK>(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
     }
   }
   flush_counters(st, cnt);
@@ -1233,7 +1248,7 @@ __global__ void __launch_bounds__(256)
     const uint32_t w = k * stride + blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= g.nwords) continue;
     uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
-    word_masks(g, grid, w, live_dirs, V, Bm, front, r, xw);
+    word_masks<kRuntime>(g, grid, w, live_dirs, V, Bm, front, r, xw);
     front_n += __popc(front);
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
     const uint32_t x0 = xw * 32u;
@@ -1253,7 +1268,7 @@ __global__ void __launch_bounds__(256)
           const uint32_t j = __ffs(win) - 1;
           win &= win - 1;
           uint32_t wq, bit;
-          claim_target(g, w, i, 4 * b + (int)j, wq, bit);
+          claim_target<kRuntime>(g, w, i, 4 * b + (int)j, wq, bit);
           atomicOr(claims + wq, bit);
         }
       }
@@ -1425,8 +1440,11 @@ cudaError_t prepare_kernels() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_grow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_grow<kOpen>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kTorus>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGrowSmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
@@ -1434,7 +1452,10 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_spacing_rounds_csr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSpacingSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_grow, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_grow<kOpen>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kTorus>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1503,9 +1524,14 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
     QSGS_LAUNCH(tr, kClsGrow, s, k_grow_fullfield, blocks, 256, g, b.grid, b.aux, b.mark, b.st,
                 make_philox_keys((uint64_t)k1 << 32 | k0));
   } else {
-    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g,
-                     b.list, b.grid, b.aux, b.mark, b.st,
-                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+    if (g.periodic)
+      QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kTorus>, shape.blocks, kGrowThreads,
+                       kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                       make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+    else
+      QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kOpen>, shape.blocks, kGrowThreads,
+                       kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                       make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
   }
   QSGS_LAUNCH(tr, kClsFront, s, k_commit, commit_grid(g.nwords), kCommitThreads, g, b.st, b.grid,
               b.aux, b.mark, b.list);
@@ -1561,7 +1587,7 @@ static uint32_t grow_wave(K kernel) {
 
 uint32_t default_grow_blocks() {
   static uint32_t blocks = 0;
-  if (!blocks) blocks = grow_wave(k_grow);
+  if (!blocks) blocks = grow_wave(k_grow<kOpen>);
   return blocks;
 }
 
@@ -1573,9 +1599,14 @@ uint32_t default_batch_grow_blocks() {
 
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              GrowShape shape, cudaStream_t s, Tracer& tr) {
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow, shape.blocks, kGrowThreads, kGrowSmemBytes, g, b.list,
-                   b.grid, b.aux, b.mark, b.st, make_philox_keys((uint64_t)k1 << 32 | k0),
-                   shape.tile);
+  if (g.periodic)
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kTorus>, shape.blocks, kGrowThreads, kGrowSmemBytes,
+                     g, b.list, b.grid, b.aux, b.mark, b.st,
+                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+  else
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kOpen>, shape.blocks, kGrowThreads, kGrowSmemBytes,
+                     g, b.list, b.grid, b.aux, b.mark, b.st,
+                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
   return cudaSuccess;
 }
 
