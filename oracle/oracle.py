@@ -38,7 +38,8 @@ class OqParams(ctypes.Structure):
                 ("g_edge", ctypes.c_double), ("g_corner", ctypes.c_double),
                 ("spacing_s", ctypes.c_uint32), ("target_solid_fraction", ctypes.c_double),
                 ("target_count", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("max_steps", ctypes.c_uint32), ("periodic", ctypes.c_uint32)]
+                ("max_steps", ctypes.c_uint32), ("periodic", ctypes.c_uint32),
+                ("blocked", ctypes.c_void_p)]
 
 
 class OqStepLog(ctypes.Structure):
@@ -104,13 +105,22 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def _params(p: dict) -> OqParams:
+def _params(p: dict, blocked=None) -> OqParams:
+    """Parameters; ``blocked`` (optional, N bytes, x fastest): cells of
+    earlier phases (R12).  The returned struct keeps the array alive."""
     q = dict(DEFAULTS)
     unknown = set(p) - set(DEFAULTS)
     if unknown:
         raise KeyError(f"unknown parameter(s) {sorted(unknown)}")
     q.update(p)
-    return OqParams(**q)
+    P = OqParams(**q)
+    if blocked is not None:
+        arr = np.ascontiguousarray(blocked, dtype=np.uint8).reshape(-1)
+        if arr.size != P.nx * P.ny * P.nz:
+            raise ValueError("blocked must hold one byte per voxel")
+        P.blocked = arr.ctypes.data
+        P._keep = arr
+    return P
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -149,8 +159,8 @@ def threshold(t_ref: int, nt: int, c: int) -> int:
     return int(lib().oq_threshold(t_ref, nt, c))
 
 
-def seed_candidates(p: dict) -> np.ndarray:
-    P = _params(p)
+def seed_candidates(p: dict, blocked=None) -> np.ndarray:
+    P = _params(p, blocked)
     n = lib().oq_seed_candidates(ctypes.byref(P), None, 0)
     out = np.zeros(max(n, 1), dtype=np.uint32)
     lib().oq_seed_candidates(ctypes.byref(P), _ptr(out, ctypes.c_uint32), n)
@@ -167,11 +177,11 @@ def spacing(p: dict, cand: np.ndarray) -> np.ndarray:
     return acc[:len(c)].astype(bool)
 
 
-def front(p: dict, phase: np.ndarray) -> np.ndarray:
+def front(p: dict, phase: np.ndarray, blocked=None) -> np.ndarray:
     ph = np.ascontiguousarray(phase, dtype=np.uint8).reshape(-1)
     out = np.zeros(max(ph.size, 1), dtype=np.uint32)
-    n = lib().oq_front(ctypes.byref(_params(p)), _ptr(ph, ctypes.c_uint8),
-                       _ptr(out, ctypes.c_uint32))
+    P = _params(p, blocked)
+    n = lib().oq_front(ctypes.byref(P), _ptr(ph, ctypes.c_uint8), _ptr(out, ctypes.c_uint32))
     return out[:n]
 
 
@@ -200,9 +210,10 @@ def _result(P: OqParams, phase: np.ndarray, s: OqSummary, log) -> Result:
                   status=s.status, log=log)
 
 
-def run(p: dict, log_cap: int = 100000) -> Result:
-    """One realization by Algorithm 3 (list-indexed growth)."""
-    P = _params(p)
+def run(p: dict, log_cap: int = 100000, blocked=None) -> Result:
+    """One realization by Algorithm 3 (list-indexed growth); ``blocked``:
+    cells of earlier phases (R12)."""
+    P = _params(p, blocked)
     n = P.nx * P.ny * P.nz
     phase = np.zeros(n, dtype=np.uint8)
     log = np.zeros(log_cap, dtype=_LOG_DTYPE)
@@ -214,9 +225,9 @@ def run(p: dict, log_cap: int = 100000) -> Result:
     return _result(P, phase, s, log[:min(s.steps, log_cap)])
 
 
-def run_fullfield(p: dict) -> Result:
+def run_fullfield(p: dict, blocked=None) -> Result:
     """The same realization by the full-field sweep of Algorithm 2."""
-    P = _params(p)
+    P = _params(p, blocked)
     n = P.nx * P.ny * P.nz
     phase = np.zeros(n, dtype=np.uint8)
     s = OqSummary()
@@ -224,3 +235,19 @@ def run_fullfield(p: dict) -> Result:
     if rc != 0:
         raise ValueError(f"oracle run failed (rc={rc})")
     return _result(P, phase, s, None)
+
+
+def run_phases(phases: list) -> tuple:
+    """Sec. 2.1 steps 4-5 with independent discrete phases (R12): phase k
+    (k = 1, 2, ...) is generated on the cells no earlier phase holds; the
+    label map has k on its cells and 0 on the matrix.  Returns (labels
+    (nz, ny, nx) uint8, [Result of every phase])."""
+    p0 = dict(DEFAULTS, **phases[0])
+    shape = (p0["nz"], p0["ny"], p0["nx"])
+    labels = np.zeros(shape, dtype=np.uint8)
+    results = []
+    for k, p in enumerate(phases, start=1):
+        r = run(p, blocked=labels != 0)
+        labels[r.phase.astype(bool)] = k
+        results.append(r)
+    return labels, results

@@ -28,6 +28,12 @@
  *       "appended"), not prune(New_t) alone (Algorithm 3 read literally).
  *   R6  Non-periodic domain: neighbours outside the grid are neither
  *       candidates (Algorithm 3, "inside domain") nor void.
+ *   R12 Later growing phases (Sec. 2.1 step 4, independent discrete
+ *       phases): a phase is generated "on the still unassigned cells" --
+ *       cells of earlier phases (blocked) are never seeds, never void
+ *       targets and never count as void neighbours; seeding, spacing, Eq. 1
+ *       (phi_a = c/N over the whole domain) and the trim are otherwise those
+ *       of the first phase.  Phase-interaction probabilities are not read.
  *   R11 Periodic option (the roll of Sec. 2.2 and Algorithm 2): with
  *       periodic = 1 the domain is a torus -- neighbours and the spacing
  *       distance wrap around every axis -- and every dimension must be at
@@ -99,6 +105,9 @@ static uint64_t grid_size(const oq_params* p) {
   return (uint64_t)p->nx * (uint64_t)p->ny * (uint64_t)p->nz;
 }
 
+/* A cell of an earlier phase (R12). */
+static int blocked(const oq_params* p, uint64_t v) { return p->blocked && p->blocked[v]; }
+
 /* R2 / R9: integer forms of the parameters. */
 int oq_targets(const oq_params* p, uint64_t* nt, uint64_t* t_seed, uint64_t t_ref[3]) {
   const double two32 = 4294967296.0;
@@ -150,7 +159,7 @@ uint64_t oq_seed_candidates(const oq_params* p, uint32_t* out, uint64_t cap) {
     uint32_t ctr[4] = {(uint32_t)group, (uint32_t)(group >> 32), 0xFFFFFFFFu, 0x100u};
     uint32_t r[4];
     oq_philox4x32_10(ctr, key, r);
-    if ((uint64_t)r[v & 3] < t_seed) {
+    if ((uint64_t)r[v & 3] < t_seed && !blocked(p, v)) {
       if (count < cap) out[count] = (uint32_t)v;
       ++count;
     }
@@ -223,7 +232,8 @@ static int has_void_neighbour(const oq_params* p, const uint8_t* phase, uint64_t
                               const int32_t dirs[78]) {
   for (int d = 0; d < 26; ++d) {
     uint64_t q;
-    if (neighbour(p, v, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) && phase[q] == 0)
+    if (neighbour(p, v, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) && phase[q] == 0 &&
+        !blocked(p, q))
       return 1;
   }
   return 0;
@@ -306,7 +316,7 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
         uint64_t a = A[i], q;
         /* neighbours inside the domain that are still void */
         if (!neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q)) continue;
-        if (phase[q] != 0) continue;
+        if (phase[q] != 0 || blocked(p, q)) continue;
         if (thr[cls[d]] == 0) continue; /* this attempt cannot succeed */
         ++live;
         /* an independent draw for this (source, step, direction) */
@@ -399,7 +409,7 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
         if (!solid_mask[a]) continue;
         uint64_t q;
         int void_q = neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) &&
-                     !solid_mask[q];
+                     !solid_mask[q] && !blocked(p, q);
         if (void_q && thr[cls[d]] > 0) ++live;
         uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
         uint32_t r[4];

@@ -38,6 +38,7 @@ typedef struct {
   uint64_t seed;                /* RNG key                                  */
   uint32_t max_steps;           /* 0 = unlimited                            */
   uint32_t periodic;            /* 1: periodic domain (R11), each dim >= 3  */
+  const uint8_t* blocked;       /* cells of earlier phases (R12); NULL: none */
 } oq_params;
 
 typedef struct {

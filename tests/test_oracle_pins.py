@@ -655,3 +655,103 @@ def test_periodic_equals_open_domain_away_from_the_faces(oracle):
         assert np.array_equal(a.phase, b.phase)
         checked += 1
     assert checked >= 3
+
+
+# --------------------------------------------------------------------------
+# Later growing phases (R12): cells of earlier phases are blocked
+# --------------------------------------------------------------------------
+def _random_case(rng, periodic=0):
+    lo = 3 if periodic else 2
+    return dict(nx=int(rng.integers(lo, 13)), ny=int(rng.integers(lo, 13)),
+                nz=int(rng.integers(lo, 13)), cd=float(rng.uniform(0.01, 0.08)),
+                g_face=float(rng.uniform(0.05, 0.4)), g_edge=float(rng.uniform(0.0, 0.2)),
+                g_corner=float(rng.uniform(0.0, 0.1)), spacing_s=int(rng.integers(0, 4)),
+                target_solid_fraction=float(rng.uniform(0.1, 0.5)),
+                seed=int(rng.integers(0, 2**63)), periodic=periodic)
+
+
+def test_blocked_nothing_changes_nothing(oracle):
+    rng = np.random.default_rng(51)
+    for _ in range(10):
+        p = _random_case(rng)
+        none = np.zeros((p["nz"], p["ny"], p["nx"]), np.uint8)
+        a, b = oracle.run(p), oracle.run(p, blocked=none)
+        assert np.array_equal(a.phase, b.phase) and a.steps == b.steps
+
+
+def test_blocked_seeding_is_the_filtered_draw(oracle):
+    rng = np.random.default_rng(52)
+    for _ in range(10):
+        p = _random_case(rng)
+        blocked = rng.random((p["nz"], p["ny"], p["nx"])) < 0.4
+        free = oracle.seed_candidates(p)
+        got = oracle.seed_candidates(p, blocked=blocked)
+        assert np.array_equal(got, free[~blocked.reshape(-1)[free]])
+
+
+def test_blocked_front_matches_bruteforce(oracle):
+    rng = np.random.default_rng(53)
+    for _ in range(20):
+        nx, ny, nz = (int(v) for v in rng.integers(2, 12, size=3))
+        blocked = rng.random((nz, ny, nx)) < 0.3
+        phase = (rng.random((nz, ny, nx)) < 0.5) & ~blocked
+        open_void = ~phase & ~blocked
+        near = ndimage.binary_dilation(open_void, structure=np.ones((3, 3, 3), bool))
+        got = oracle.front(dict(nx=nx, ny=ny, nz=nz, target_solid_fraction=0.5),
+                           phase.astype(np.uint8), blocked=blocked)
+        assert np.array_equal(got, np.flatnonzero(phase & near))
+
+
+def test_blocked_unit_growth_is_a_geodesic_dilation(oracle):
+    # G = 1: after k steps the phase is the seeds dilated k times inside the
+    # unblocked cells only.
+    rng = np.random.default_rng(54)
+    checked = 0
+    for trial in range(12):
+        nx, ny, nz = (int(v) for v in rng.integers(5, 14, size=3))
+        n = nx * ny * nz
+        k = int(rng.integers(1, 4))
+        blocked = rng.random((nz, ny, nx)) < 0.35
+        p = dict(nx=nx, ny=ny, nz=nz, cd=0.03, g_face=1.0, g_edge=1.0, g_corner=1.0,
+                 target_count=n, seed=trial, max_steps=k)
+        cand = oracle.seed_candidates(p, blocked=blocked)
+        if cand.size == 0:
+            continue
+        want = np.zeros(n, bool)
+        want[cand] = True
+        want = want.reshape(nz, ny, nx)
+        for _ in range(k):
+            want = ndimage.binary_dilation(want, structure=np.ones((3, 3, 3), bool)) & ~blocked
+        r = oracle.run(p, blocked=blocked)
+        assert np.array_equal(r.phase.astype(bool), want)
+        assert not (r.phase.astype(bool) & blocked).any()
+        checked += 1
+    assert checked >= 6
+
+
+def test_phases_are_disjoint_and_reach_their_targets(oracle):
+    rng = np.random.default_rng(55)
+    for periodic in (0, 1):
+        for _ in range(6):
+            p1 = _random_case(rng, periodic)
+            dims = {k: p1[k] for k in ("nx", "ny", "nz")}
+            p2 = dict(_random_case(rng, periodic), **dims, target_solid_fraction=0.2)
+            p3 = dict(_random_case(rng, periodic), **dims, target_solid_fraction=0.1)
+            labels, rs = oracle.run_phases([p1, p2, p3])
+            for k, r in enumerate(rs, start=1):
+                assert int((labels == k).sum()) == r.solid_count
+                if r.status == oracle.DONE:
+                    assert r.solid_count == r.target_count
+            assert np.array_equal(labels == 1, rs[0].phase.reshape(labels.shape).astype(bool))
+
+
+def test_blocked_list_indexed_equals_full_field(oracle):
+    rng = np.random.default_rng(56)
+    for periodic in (0, 1):
+        for _ in range(8):
+            p = _random_case(rng, periodic)
+            blocked = rng.random((p["nz"], p["ny"], p["nx"])) < 0.25
+            a, b = oracle.run(p, blocked=blocked), oracle.run_fullfield(p, blocked=blocked)
+            assert np.array_equal(a.phase, b.phase)
+            assert (a.solid_count, a.steps, a.status, a.front_size) == \
+                   (b.solid_count, b.steps, b.status, b.front_size)
