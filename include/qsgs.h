@@ -239,6 +239,31 @@ int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks);
  * qsgs_time_grow always times it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_mode(qsgs_handle* h, int mode);
 
+/* Later growing phases (Sec. 2.1 step 4 with independent discrete phases,
+ * reading R12): a phase is generated on the cells no earlier phase holds.
+ *   dev_blocked  device, read only, owned by the caller: the packed grid
+ *                (QSGS_FMT_PACKED layout of this handle's dims) of the cells
+ *                of all earlier phases; NULL = none (the first phase).  It
+ *                must stay valid and unchanged from qsgs_seed to the last
+ *                fetch; 4-byte aligned.
+ * Blocked cells are never seeds, never void targets and never count as void
+ * neighbours; targets stay fractions of the whole domain.  Set it before
+ * qsgs_seed.  Batches use each member's own setting.  Returns QSGS_OK or
+ * QSGS_ERR_INVALID. */
+int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked);
+
+/* Phase-map composition: writes `label` into dev_dst[v] (device uint8 map
+ * of N bytes, x fastest) for every solid voxel v of this realization and
+ * leaves the other bytes unchanged.  Blocks.  Returns QSGS_OK,
+ * QSGS_ERR_INVALID, QSGS_ERR_STATE (not seeded) or QSGS_ERR_CUDA. */
+int qsgs_fetch_label(qsgs_handle* h, void* dev_dst, size_t bytes, uint8_t label);
+
+/* ORs this realization's packed grid into dev_dst (device, >= 4 nz ny W
+ * bytes, 4-byte aligned): accumulates the blocked grid of the next phase.
+ * Blocks.  Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_STATE or
+ * QSGS_ERR_CUDA. */
+int qsgs_fetch_or(qsgs_handle* h, void* dev_dst, size_t bytes);
+
 /* Tuning probe (no counterpart in the paper): replays the growth kernel of
  * the handle's next step `reps` times with `grow_blocks` thread blocks (0 =
  * default) and writes the mean milliseconds per launch to *ms (host).  The

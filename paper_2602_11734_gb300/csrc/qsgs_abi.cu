@@ -850,6 +850,37 @@ int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
   return QSGS_OK;
 }
 
+int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked) {
+  if (!h) return QSGS_ERR_INVALID;
+  if (dev_blocked && (reinterpret_cast<uintptr_t>(dev_blocked) % 4)) return QSGS_ERR_INVALID;
+  h->g.blocked = static_cast<const uint32_t*>(dev_blocked);
+  destroy_graph(h);  // the geometry (with the pointer) is baked into the graph
+  h->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_fetch_label(qsgs_handle* h, void* dev_dst, size_t bytes, uint8_t label) {
+  if (!h || !dev_dst || bytes < (size_t)h->g.n) return QSGS_ERR_INVALID;
+  if (!h->seeded) return QSGS_ERR_STATE;
+  cudaError_t e = launch_label_u8(h->g, h->grid, static_cast<uint8_t*>(dev_dst), label, h->stream,
+                                  h->tracer);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = h->tracer.collect();
+  return e == cudaSuccess ? QSGS_OK : cuda_fail(h, e);
+}
+
+int qsgs_fetch_or(qsgs_handle* h, void* dev_dst, size_t bytes) {
+  if (!h || !dev_dst || bytes < (size_t)h->g.nwords * 4 ||
+      (reinterpret_cast<uintptr_t>(dev_dst) % 4))
+    return QSGS_ERR_INVALID;
+  if (!h->seeded) return QSGS_ERR_STATE;
+  cudaError_t e = launch_or_words(h->g.nwords, h->grid, static_cast<uint32_t*>(dev_dst),
+                                  h->stream, h->tracer);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = h->tracer.collect();
+  return e == cudaSuccess ? QSGS_OK : cuda_fail(h, e);
+}
+
 int qsgs_set_mode(qsgs_handle* h, int mode) {
   if (!h || (mode != QSGS_MODE_LIETS && mode != QSGS_MODE_FULLFIELD)) return QSGS_ERR_INVALID;
   if (mode != h->mode) {

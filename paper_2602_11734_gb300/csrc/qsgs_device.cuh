@@ -57,6 +57,7 @@ struct Geom {
   uint32_t pad_mask; // bits of the last word of a row that lie at x >= nx
   uint32_t periodic; // 1: neighbours wrap around every axis (a torus)
   FastDiv div_nx, div_ny, div_W;
+  const uint32_t* blocked;  // packed cells of earlier phases (R12), or nullptr
 };
 
 // ---------------------------------------------------------------------------

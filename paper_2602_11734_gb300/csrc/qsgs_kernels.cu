@@ -204,6 +204,7 @@ struct SeedCompactPolicy {
         }
       }
     }
+    if (g.blocked != nullptr && bits) bits &= ~g.blocked[w];  // R12: only unassigned cells
     return Item{w, bits, 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
@@ -384,6 +385,12 @@ __device__ __forceinline__ bool on_torus(const Geom& g) {
   return DK == kRuntime ? g.periodic != 0u : DK == kTorus;
 }
 
+// Cells of earlier phases (R12) are only looked at by the run-time kind.
+template <int DK>
+__device__ __forceinline__ bool has_blocked(const Geom& g) {
+  return DK == kRuntime && g.blocked != nullptr;
+}
+
 template <int DK>
 __device__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid, uint32_t w,
                            uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7],
@@ -399,9 +406,9 @@ struct FrontCountPolicy {
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w, bool valid) const {
-    if (g.periodic) {  // the torus: the growth kernel's own neighbour masks
+    if (g.periodic || g.blocked) {  // the growth kernel's own neighbour masks
       uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
-      if (valid) word_masks<kTorus>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
+      if (valid) word_masks<kRuntime>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
       return Item{w, front, 0u};
     }
     const uint32_t lane = threadIdx.x & 31u;
@@ -890,6 +897,32 @@ __host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
 // V masks of the three directions that land in row (y+DY, z+DZ).
 // V masks of the three directions that land in row (y+DY, z+DZ); `front`
 // collects every void neighbour, live class or not.
+// Word xw of a row (x-1 / x+1 neighbour words in l / rr) as occupancy: pad
+// bits solid; on the torus the x wrap is folded in -- voxel nx-1 (bit p of
+// the last word) is the x-1 neighbour of voxel 0, and voxel 0 the x+1
+// neighbour of voxel nx-1.
+template <int DK>
+__device__ __forceinline__ void row_words(const Geom& g, const uint32_t* __restrict__ row,
+                                          uint32_t xw, uint32_t& c, uint32_t& l, uint32_t& rr) {
+  c = __ldg(row + xw);
+  if (xw == g.W - 1) c |= g.pad_mask;
+  l = xw > 0 ? __ldg(row + xw - 1) : 0xFFFFFFFFu;
+  rr = 0xFFFFFFFFu;
+  if (xw + 1 < g.W) {
+    rr = __ldg(row + xw + 1);
+    if (xw + 1 == g.W - 1) rr |= g.pad_mask;
+  }
+  if (on_torus<DK>(g)) {
+    const uint32_t p = (g.nx - 1) & 31u;
+    if (xw == 0) l = (__ldg(row + g.W - 1) >> p) << 31;
+    if (xw == g.W - 1) {
+      const uint32_t first = __ldg(row) & 1u;
+      if (p == 31) rr = first;
+      else c = (c & ~(2u << p)) | (first << (p + 1));
+    }
+  }
+}
+
 template <int DZ, int DY, int DK>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
@@ -902,24 +935,14 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
   }
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
   if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
-    const uint32_t* row = grid + (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
-    c = __ldg(row + xw);
-    if (xw == g.W - 1) c |= g.pad_mask;
-    if (xw > 0) l = __ldg(row + xw - 1);
-    if (xw + 1 < g.W) {
-      rr = __ldg(row + xw + 1);
-      if (xw + 1 == g.W - 1) rr |= g.pad_mask;
-    }
-    if (on_torus<DK>(g)) {
-      // x wraps: voxel nx-1 (bit p of the last word) is the x-1 neighbour of
-      // voxel 0, and voxel 0 the x+1 neighbour of voxel nx-1.
-      const uint32_t p = (g.nx - 1) & 31u;
-      if (xw == 0) l = (__ldg(row + g.W - 1) >> p) << 31;
-      if (xw == g.W - 1) {
-        const uint32_t first = __ldg(row) & 1u;
-        if (p == 31) rr = first;
-        else c = (c & ~(2u << p)) | (first << (p + 1));
-      }
+    const size_t ro = (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
+    row_words<DK>(g, grid + ro, xw, c, l, rr);
+    if (has_blocked<DK>(g)) {  // cells of earlier phases are not void either
+      uint32_t bc, bl, br;
+      row_words<DK>(g, g.blocked + ro, xw, bc, bl, br);
+      c |= bc;
+      l |= bl;
+      rr |= br;
     }
   }
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
@@ -1360,6 +1383,30 @@ __global__ void k_unpack_u8(Geom g, const uint32_t* grid, uint8_t* out, unsigned
 }
 
 // ---------------------------------------------------------------------------
+// Phase maps (R12): the label of this phase into a uint8 map (other bytes
+// untouched), and this phase's cells ORed into a packed blocked grid.
+// ---------------------------------------------------------------------------
+__global__ void k_label_u8(Geom g, const uint32_t* grid, uint8_t* out, uint8_t label) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < g.nwords;
+       w += gridDim.x * blockDim.x) {
+    uint32_t bits = grid[w];
+    if (!bits) continue;
+    const uint32_t r = fast_div(w, g.div_W);
+    const uint32_t v0 = r * g.nx + (w - r * g.W) * 32u;
+    while (bits) {
+      const uint32_t i = __ffs(bits) - 1;
+      bits &= bits - 1;
+      out[v0 + i] = label;
+    }
+  }
+}
+
+__global__ void k_or_words(uint32_t n, const uint32_t* src, uint32_t* dst) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (src[i]) dst[i] |= src[i];
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
 static int g_num_sms = 0;
@@ -1401,6 +1448,7 @@ static uint32_t batch_commit_grid(uint64_t max_words) {
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic) {
   Geom g{};
   g.periodic = periodic ? 1u : 0u;
+  g.blocked = nullptr;
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -1446,6 +1494,9 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_grow<kTorus>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
@@ -1456,6 +1507,9 @@ cudaError_t prepare_kernels() {
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow<kTorus>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1524,7 +1578,11 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
     QSGS_LAUNCH(tr, kClsGrow, s, k_grow_fullfield, blocks, 256, g, b.grid, b.aux, b.mark, b.st,
                 make_philox_keys((uint64_t)k1 << 32 | k0));
   } else {
-    if (g.periodic)
+    if (g.blocked)
+      QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,
+                       kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                       make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+    else if (g.periodic)
       QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kTorus>, shape.blocks, kGrowThreads,
                        kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
                        make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
@@ -1597,9 +1655,32 @@ uint32_t default_batch_grow_blocks() {
   return blocks;
 }
 
+cudaError_t launch_label_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint8_t label,
+                            cudaStream_t s, Tracer& tr) {
+  uint64_t blocks = ((uint64_t)g.nwords + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  QSGS_LAUNCH(tr, kClsFetch, s, k_label_u8, (uint32_t)(blocks ? blocks : 1), 256, g, grid, out,
+              label);
+  return cudaSuccess;
+}
+
+cudaError_t launch_or_words(uint32_t n, const uint32_t* src, uint32_t* dst, cudaStream_t s,
+                            Tracer& tr) {
+  uint64_t blocks = ((uint64_t)n + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  QSGS_LAUNCH(tr, kClsFetch, s, k_or_words, (uint32_t)(blocks ? blocks : 1), 256, n, src, dst);
+  return cudaSuccess;
+}
+
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              GrowShape shape, cudaStream_t s, Tracer& tr) {
-  if (g.periodic)
+  if (g.blocked)
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,
+                     kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+  else if (g.periodic)
     QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kTorus>, shape.blocks, kGrowThreads, kGrowSmemBytes,
                      g, b.list, b.grid, b.aux, b.mark, b.st,
                      make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);

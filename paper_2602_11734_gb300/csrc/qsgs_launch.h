@@ -196,6 +196,12 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowSh
                               int use_cond);
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
                                unsigned long long* out, cudaStream_t s);
+// Phase maps: `label` into out[v] for every solid voxel v (other bytes
+// untouched); src words ORed into dst (n words).
+cudaError_t launch_label_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint8_t label,
+                            cudaStream_t s, Tracer& tr);
+cudaError_t launch_or_words(uint32_t n, const uint32_t* src, uint32_t* dst, cudaStream_t s,
+                            Tracer& tr);
 // Voxels [vb, ve) of the grid as one byte each into out[0 .. ve - vb).
 cudaError_t launch_unpack_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint64_t vb,
                              uint64_t ve, cudaStream_t s, Tracer& tr);

@@ -97,6 +97,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_mode": ([H, ctypes.c_int], ctypes.c_int),
+                "qsgs_set_blocked": ([H, ctypes.c_void_p], ctypes.c_int),
+                "qsgs_fetch_label": ([H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint8],
+                                     ctypes.c_int),
+                "qsgs_fetch_or": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
                 "qsgs_time_grow": ([H, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
                 "qsgs_front_count_static": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
@@ -304,6 +308,20 @@ def qsgs_set_mode(h, mode: int) -> None:
     _check(load_library().qsgs_set_mode(h, mode), "qsgs_set_mode")
 
 
+def qsgs_set_blocked(h, dev_ptr: int) -> None:
+    _check(load_library().qsgs_set_blocked(h, ctypes.c_void_p(dev_ptr or None)),
+           "qsgs_set_blocked")
+
+
+def qsgs_fetch_label(h, dev_ptr: int, nbytes: int, label: int) -> None:
+    _check(load_library().qsgs_fetch_label(h, ctypes.c_void_p(dev_ptr), nbytes, label),
+           "qsgs_fetch_label")
+
+
+def qsgs_fetch_or(h, dev_ptr: int, nbytes: int) -> None:
+    _check(load_library().qsgs_fetch_or(h, ctypes.c_void_p(dev_ptr), nbytes), "qsgs_fetch_or")
+
+
 def qsgs_batch_set_grow_tile(b, chunks: int) -> None:
     _check(load_library().qsgs_batch_set_grow_tile(b, chunks), "qsgs_batch_set_grow_tile")
 
@@ -404,6 +422,20 @@ class Generator:
         """QSGS_MODE_LIETS (default) or QSGS_MODE_FULLFIELD (comparator)."""
         qsgs_set_mode(self.handle, mode)
 
+    def set_blocked(self, blocked) -> None:
+        """Packed int32 device tensor of the cells of earlier phases (kept
+        referenced here while the handle uses it), or None."""
+        self._blocked = blocked
+        qsgs_set_blocked(self.handle, 0 if blocked is None else blocked.data_ptr())
+
+    def fetch_label(self, labels, label: int) -> None:
+        """Writes `label` into the uint8 device map `labels` at this phase's cells."""
+        qsgs_fetch_label(self.handle, labels.data_ptr(), labels.numel(), label)
+
+    def fetch_or(self, blocked) -> None:
+        """ORs this phase's cells into the packed int32 device tensor `blocked`."""
+        qsgs_fetch_or(self.handle, blocked.data_ptr(), blocked.numel() * 4)
+
     def time_grow(self, grow_blocks: int = 0, reps: int = 5) -> float:
         return qsgs_time_grow(self.handle, grow_blocks, reps)
 
@@ -499,3 +531,36 @@ def generate(params: dict, device=None, fmt: str = "u8"):
         return out, st
     finally:
         g.close()
+
+
+def generate_phases(phases: list, device=None):
+    """Sec. 2.1 steps 4-5 with independent discrete phases: phase k (k = 1,
+    2, ...) grows on the cells no earlier phase holds; returns the uint8
+    label map (nz, ny, nx) on the device (0 = matrix) and every phase's
+    Stats.  All phases must have the same grid dims and domain kind."""
+    import torch
+    if not phases or len(phases) > 255:
+        raise ValueError("1 .. 255 phases")
+    first = make_params(phases[0])
+    dims = (first.nx, first.ny, first.nz, first.periodic)
+    dev = torch.device(device) if device is not None else torch.device(
+        "cuda", torch.cuda.current_device())
+    words = word_count(phases[0])
+    blocked = torch.zeros(words, dtype=torch.int32, device=dev)
+    labels = torch.zeros((first.nz, first.ny, first.nx), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)  # the zero fills ran on torch's stream
+    stats = []
+    for k, p in enumerate(phases, start=1):
+        q = make_params(p)
+        if (q.nx, q.ny, q.nz, q.periodic) != dims:
+            raise ValueError("all phases need the same grid")
+        g = Generator(p, device=dev)
+        try:
+            g.set_blocked(blocked if k > 1 else None)
+            g.seed()
+            stats.append(g.grow())
+            g.fetch_label(labels, k)
+            g.fetch_or(blocked)
+        finally:
+            g.close()
+    return labels, stats

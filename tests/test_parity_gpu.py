@@ -410,3 +410,61 @@ def test_periodic_batch_and_fullfield(oracle, Q):
         assert np.array_equal(g.fetch().cpu().numpy(), oracle.run(p).phase)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_phases_match_the_oracle(oracle, Q, periodic):
+    # Independent discrete phases (R12): each grows on the cells no earlier
+    # phase holds; the label maps and every phase's statistics agree.
+    rng = np.random.default_rng(300 + periodic)
+    for trial in range(3):
+        dims = dict(nx=int(rng.integers(20, 70)), ny=int(rng.integers(12, 40)),
+                    nz=int(rng.integers(10, 30)), periodic=periodic)
+        phases = []
+        for frac, cd, s in ((0.35, 0.004, 3), (0.2, 0.01, 0), (0.15, 0.02, 5)):
+            phases.append(dict(workloads.small_64(), **dims, cd=cd, spacing_s=s,
+                               g_face=0.05, g_edge=0.02, g_corner=0.01,
+                               target_solid_fraction=frac, seed=int(rng.integers(0, 2**62))))
+        want, results = oracle.run_phases(phases)
+        labels, stats = Q.generate_phases(phases)
+        assert np.array_equal(labels.cpu().numpy(), want), (trial, dims)
+        for st, r in zip(stats, results):
+            assert (st.solid_count, st.steps, st.status, st.n_seeds, st.front_size) == \
+                   (r.solid_count, r.steps, r.status, r.n_accepted, r.front_size)
+
+
+def test_blocked_single_phase_and_batch(oracle, Q):
+    rng = np.random.default_rng(310)
+    params = [dict(workloads.random_small(rng, max_edge=26), cd=0.03, max_steps=0)
+              for _ in range(4)]
+    blocks, gens = [], []
+    for p in params:
+        shape = (p["nz"], p["ny"], p["nx"])
+        blk = rng.random(shape) < 0.3
+        words = ((p["nx"] + 31) // 32)
+        packed = np.zeros((p["nz"], p["ny"], words * 32), dtype=bool)
+        packed[:, :, :p["nx"]] = blk
+        w32 = np.packbits(packed, axis=-1, bitorder="little").view(np.uint32).reshape(-1)
+        t = torch.from_numpy(w32.view(np.int32).copy()).cuda()
+        g = Q.Generator(p)
+        g.set_blocked(t)
+        blocks.append((blk, t))
+        gens.append(g)
+    b = Q.Batch(len(params), sum(Q.word_count(p) for p in params))
+    try:
+        b.set_members(gens[:2])
+        stats = b.run()
+        for g, st, p, (blk, _) in zip(gens[:2], stats, params, blocks):
+            want = oracle.run(p, blocked=blk)
+            assert np.array_equal(g.fetch().cpu().numpy(), want.phase)
+            assert st.solid_count == want.solid_count and st.steps == want.steps
+        for g, p, (blk, _) in zip(gens[2:], params[2:], blocks[2:]):
+            g.seed()
+            st = g.grow()
+            want = oracle.run(p, blocked=blk)
+            assert np.array_equal(g.fetch().cpu().numpy(), want.phase)
+            assert (st.solid_count, st.front_size) == (want.solid_count, want.front_size)
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
