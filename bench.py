@@ -61,6 +61,8 @@ def parse():
                     help="skip the full-field (Algorithm 2) comparator")
     ap.add_argument("--no-fontainebleau", action="store_true",
                     help="skip the Fontainebleau benchmark sweep (Sec. 3.3 setting)")
+    ap.add_argument("--no-phases", action="store_true",
+                    help="skip the three-phase label-map report")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the 200^3..1000^3 size sweep in the paper's Fig. 3 setting")
     ap.add_argument("--no-tune", action="store_true",
@@ -312,6 +314,28 @@ def bench_fontainebleau(Q, torch, dev) -> dict:
                              "mean_seeds": statistics.mean(x[1] for x in v),
                              "mean_steps": statistics.mean(x[2] for x in v)}
                             for sp, v in sorted(per_s.items())]}
+
+
+def bench_phases(Q, torch, dev) -> dict:
+    """Three independent growing phases on the 400^3 box (Sec. 2.1 steps 4-5,
+    reading R12): volume fractions 0.45 / 0.20 / 0.10 of the domain, the
+    rest matrix; each phase with the single-phase parameters otherwise.
+    Wall time of the whole label map (seeding, growth, label and blocked
+    fetches of all three phases), after an untimed run."""
+    base = workloads.single_400()
+    phases = [dict(base, target_solid_fraction=f, seed=10 + k, spacing_s=s)
+              for k, (f, s) in enumerate(((0.45, 30), (0.20, 15), (0.10, 0)))]
+    Q.generate_phases(phases, device=dev)  # untimed warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    labels, stats = Q.generate_phases(phases, device=dev)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    counts = torch.bincount(labels.view(-1), minlength=4).cpu().tolist()
+    return {"workload": "phases_400", "phases": len(phases), "ms": round(dt * 1e3, 3),
+            "nodes_per_s": 400**3 / dt,
+            "label_counts": counts,
+            "exact_targets": all(st.solid_count == st.target_count for st in stats)}
 
 
 def bench_sizes(Q, torch, dev) -> dict:
@@ -578,8 +602,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(CPU_SAMPLE_EDGE)
-    batched = served = sweep = sizes = fullfield = fontainebleau = None
+    batched = served = sweep = sizes = fullfield = fontainebleau = phases = None
     del g
+    if not a.no_phases and a.edge == 400:
+        phases = bench_phases(Q, torch, dev)
     if not a.no_fontainebleau and a.edge == 400:
         fontainebleau = bench_fontainebleau(Q, torch, dev)
     if not a.no_fullfield and a.edge == 400:
@@ -610,7 +636,7 @@ def main():
             "roofline": roofline, "rates": rates, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed, "clocks": clocks, "sweep_500": sweep,
             "size_sweep": sizes, "fullfield_comparator": fullfield,
-            "fontainebleau": fontainebleau,
+            "fontainebleau": fontainebleau, "phases": phases,
             "batched": batched, "served": served,
         }), flush=True)
     if world > 1:
