@@ -239,6 +239,15 @@ int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks);
  * qsgs_time_grow always times it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
 int qsgs_set_mode(qsgs_handle* h, int mode);
 
+/* Failure-detection knob (no counterpart in the paper): how many polls a
+ * device-side wait of this handle's order-preserving passes (seeding,
+ * first candidate list, trim, front count) makes before it gives up,
+ * records the timeout and lets the kernel finish; the next query or grow
+ * call then returns QSGS_ERR_TIMEOUT (the realization is invalid; reseed).
+ * 0 = the default 2^20 polls (about a second).  Returns QSGS_OK or
+ * QSGS_ERR_INVALID. */
+int qsgs_set_spin_limit(qsgs_handle* h, uint32_t polls);
+
 /* Later growing phases (Sec. 2.1 step 4 with independent discrete phases,
  * reading R12): a phase is generated on the cells no earlier phase holds.
  *   dev_blocked  device, read only, owned by the caller: the packed grid

@@ -144,6 +144,7 @@ struct qsgs_handle {
   uint32_t grow_blocks;
   uint32_t grow_tile;
   int mode;  // QSGS_MODE_LIETS or QSGS_MODE_FULLFIELD
+  uint32_t spin_limit;  // polls before a device-side wait gives up
   bool seeded;
   cudaError_t last_cuda;
   Tracer tracer;
@@ -219,7 +220,7 @@ int seed_on_stream(qsgs_handle* h, cudaStream_t stream) {
                 h->list,       h->mark,        h->cell_count,  h->cell_start, h->cell_items,
                 h->decision,   h->conf_off,    h->adj,        h->L.adj_cap,
                 h->L.cand_cap, h->L.cg};
-  e = launch_seed(h->g, b, h->k0, h->k1, kSpinLimit, stream, h->tracer);
+  e = launch_seed(h->g, b, h->k0, h->k1, h->spin_limit, stream, h->tracer);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->seeded = true;
   h->list_stale = false;
@@ -269,7 +270,7 @@ cudaError_t build_graph(qsgs_handle* h) {
   e = cudaStreamBeginCaptureToGraph(h->stream, h->graph, &loop, nullptr, 1,
                                     cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  le = launch_epilogue(h->g, b, kSpinLimit, h->stream, capture_tracer);
+  le = launch_epilogue(h->g, b, h->spin_limit, h->stream, capture_tracer);
   e = cudaStreamEndCapture(h->stream, &captured);
   if (le != cudaSuccess) return le;
   if (e != cudaSuccess) return e;
@@ -463,6 +464,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->grow_blocks = default_grow_blocks();
   h->grow_tile = 1;
   h->mode = QSGS_MODE_LIETS;
+  h->spin_limit = kSpinLimit;
   h->seeded = false;
   h->last_cuda = cudaSuccess;
   h->graph = nullptr;
@@ -493,7 +495,7 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
   const StepBuffers b = step_buffers(h);
   cudaError_t e = cudaSuccess;
   if (h->list_stale) {
-    e = launch_front_list(h->g, b, kSpinLimit, h->stream, h->tracer);
+    e = launch_front_list(h->g, b, h->spin_limit, h->stream, h->tracer);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->list_stale = false;
   }
@@ -528,7 +530,7 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
       if (rc != QSGS_OK) return rc;
       if (s.status != kRunning || !s.active) break;
     }
-    e = launch_epilogue(h->g, b, kSpinLimit, h->stream, h->tracer);
+    e = launch_epilogue(h->g, b, h->spin_limit, h->stream, h->tracer);
     if (e != cudaSuccess) return cuda_fail(h, e);
     const int rc = read_state(h, &s);
     if (rc != QSGS_OK) return rc;
@@ -816,7 +818,7 @@ int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n) {
   for (size_t m = 0; m < nm; ++m) {
     qsgs_handle* h = b->members[m];
     if (b->host_states[m].status != kRunning && !h->finalized) {
-      e = launch_epilogue(h->g, step_buffers(h), kSpinLimit, b->stream, h->tracer);
+      e = launch_epilogue(h->g, step_buffers(h), h->spin_limit, b->stream, h->tracer);
       if (e != cudaSuccess) return batch_fail(b, e);
       h->finalized = true;
       any_final = true;
@@ -847,6 +849,14 @@ int qsgs_batch_set_grow_blocks(qsgs_batch* b, uint32_t blocks) {
   b->grow_blocks = blocks ? blocks : default_batch_grow_blocks();
   destroy_batch_graph(b);  // the grid size is baked into the graph
   b->graph_tried = false;
+  return QSGS_OK;
+}
+
+int qsgs_set_spin_limit(qsgs_handle* h, uint32_t polls) {
+  if (!h) return QSGS_ERR_INVALID;
+  h->spin_limit = polls ? polls : kSpinLimit;
+  destroy_graph(h);  // the limit is a launch argument inside the graph
+  h->graph_tried = false;
   return QSGS_OK;
 }
 

@@ -515,7 +515,7 @@ struct AcceptPolicy {
   }
   __device__ uint32_t count(const Item& it) const { return it.ok; }
   __device__ void emit(const Item& it, unsigned long long off) const {
-    if (off < st->nt) {
+    if (off < st->nt && it.v < g.n) {  // v >= N only after a timed-out scan
       const uint32_t r = fast_div(it.v, g.div_nx);
       const uint32_t x = it.v - r * g.nx;
       atomicOr(grid + (size_t)r * g.W + (x >> 5), 1u << (x & 31));
@@ -617,6 +617,7 @@ __global__ void k_cell_count(Geom g, CellGeom cg, const RunState* st, const uint
                              uint32_t* count) {
   const uint32_t n = st->cand_n;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (cand[i] >= g.n) continue;  // only after a timed-out scan (reported)
     uint32_t x, y, z;
     decode_xyz(g, cand[i], x, y, z);
     const uint32_t cell = cell_coord(cg, x, g.nx, cg.ncx) +
@@ -630,13 +631,14 @@ __global__ void k_cell_fill(Geom g, CellGeom cg, const RunState* st, const uint3
                             uint32_t* cursor, uint32_t* items, uint8_t* decision) {
   const uint32_t n = st->cand_n;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    decision[i] = 0;
+    if (cand[i] >= g.n) continue;  // only after a timed-out scan (reported)
     uint32_t x, y, z;
     decode_xyz(g, cand[i], x, y, z);
     const uint32_t cell = cell_coord(cg, x, g.nx, cg.ncx) +
                           cg.ncx * (cell_coord(cg, y, g.ny, cg.ncy) +
                                     cg.ncy * cell_coord(cg, z, g.nz, cg.ncz));
     items[atomicAdd(cursor + cell, 1u)] = i;
-    decision[i] = 0;
   }
 }
 
@@ -649,8 +651,10 @@ __device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const Cel
                                                         const uint32_t* cand,
                                                         const uint32_t* start,
                                                         const uint32_t* items, uint32_t i,
-                                                        uint32_t* out) {
+                                                        uint32_t* out,
+                                                        unsigned long long out_cap = 0) {
   const uint32_t lane = threadIdx.x & 31u;
+  if (cand[i] >= g.n) return 0;  // only after a timed-out scan (reported)
   uint32_t x, y, z;
   decode_xyz(g, cand[i], x, y, z);
   uint32_t k0 = 0, k1 = 0;
@@ -667,7 +671,7 @@ __device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const Cel
   }
   auto conflicts = [&](uint32_t k, uint32_t& j) {
     j = items[k];
-    if (j >= i) return false;
+    if (j >= i || cand[j] >= g.n) return false;
     uint32_t xj, yj, zj;
     decode_xyz(g, cand[j], xj, yj, zj);
     return spacing_l1(g, x, y, z, xj, yj, zj) < (int)cg.s;
@@ -687,7 +691,10 @@ __device__ __forceinline__ uint32_t scan_conflicts_warp(const Geom& g, const Cel
     uint32_t pos = incl - mine;
     for (uint32_t k = k0; k < k1; ++k) {
       uint32_t j;
-      if (conflicts(k, j)) out[pos++] = j;
+      if (conflicts(k, j)) {
+        if (pos < out_cap) out[pos] = j;  // out_cap < count only after a timed-out scan
+        ++pos;
+      }
     }
   }
   return __shfl_sync(0xffffffffu, incl, 31);
@@ -734,8 +741,11 @@ __global__ void k_conflict_fill(Geom g, CellGeom cg, const RunState* st, const u
   if (st->adj_n > cap) return;
   const uint32_t n = st->cand_n;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps)
-    scan_conflicts_warp(g, cg, cand, start, items, i, adj + off[i]);
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+    const unsigned long long o = off[i];
+    scan_conflicts_warp(g, cg, cand, start, items, i, adj + (o < cap ? o : cap),
+                        o < cap ? cap - o : 0ull);
+  }
 }
 
 // Rounds over the conflict lists (one block).  Each round settles at least
@@ -764,8 +774,11 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       if (((volatile uint8_t*)dec)[i] != 0) continue;
       bool pending = false, rejected = false;
-      for (uint32_t k = off[i]; k < off[i + 1]; ++k) {
-        const uint8_t dj = ((volatile uint8_t*)dec)[adj[k]];
+      const unsigned long long k_end = off[i + 1] < cap ? off[i + 1] : cap;
+      for (unsigned long long k = off[i]; k < k_end; ++k) {
+        const uint32_t j = adj[k];
+        if (j >= n) continue;  // only after a timed-out scan (reported)
+        const uint8_t dj = ((volatile uint8_t*)dec)[j];
         if (dj == 1) { rejected = true; break; }
         if (dj == 0) pending = true;
       }
@@ -802,6 +815,10 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
     uint32_t mine = 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       if (((volatile uint8_t*)decision)[i] != 0) continue;
+      if (cand[i] >= g.n) {  // only after a timed-out scan (reported)
+        decision[i] = 2;
+        continue;
+      }
       uint32_t x, y, z;
       decode_xyz(g, cand[i], x, y, z);
       const int cx = (int)cell_coord(cg, x, g.nx, cg.ncx);
@@ -820,7 +837,7 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
             const uint32_t cell = xx + cg.ncx * (yy + cg.ncy * zz);
             for (uint32_t k = start[cell]; k < start[cell + 1]; ++k) {
               const uint32_t j = items[k];
-              if (j >= i) continue;  // only earlier candidates matter
+              if (j >= i || cand[j] >= g.n) continue;  // only earlier candidates matter
               uint32_t xj, yj, zj;
               decode_xyz(g, cand[j], xj, yj, zj);
               if (spacing_l1(g, x, y, z, xj, yj, zj) >= s) continue;
@@ -1235,7 +1252,8 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
     const uint32_t c_end = min(ti * tile + tile, nchunks);
     for (uint32_t c = ti * tile; c < c_end; ++c) {
       const uint32_t idx = c * 32u + lane;
-      const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
+      uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
+      if (w >= g.nwords) w = 0xFFFFFFFFu;  // only after a timed-out scan (reported)
       grow_chunk<DK>(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
     }
   }

@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_mode": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_set_blocked": ([H, ctypes.c_void_p], ctypes.c_int),
+                "qsgs_set_spin_limit": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_fetch_label": ([H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint8],
                                      ctypes.c_int),
                 "qsgs_fetch_or": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
@@ -306,6 +307,10 @@ def qsgs_set_grow_tile(h, chunks: int) -> None:
 
 def qsgs_set_mode(h, mode: int) -> None:
     _check(load_library().qsgs_set_mode(h, mode), "qsgs_set_mode")
+
+
+def qsgs_set_spin_limit(h, polls: int) -> None:
+    _check(load_library().qsgs_set_spin_limit(h, polls), "qsgs_set_spin_limit")
 
 
 def qsgs_set_blocked(h, dev_ptr: int) -> None:

@@ -468,3 +468,34 @@ def test_blocked_single_phase_and_batch(oracle, Q):
         b.close()
         for g in gens:
             g.close()
+
+
+def test_bounded_wait_gives_up_and_the_handle_recovers(Q):
+    # Failure detection without a fault: with a two-poll limit the look-back
+    # waits of the order-preserving passes give up (their predecessors have
+    # not published yet), the kernels finish, and the host reads
+    # QSGS_ERR_TIMEOUT; the same handle with the default limit then gives
+    # the golden realization.
+    row = _golden("single_400")[0]
+    g = Q.Generator(row["params"])
+    try:
+        Q.qsgs_set_spin_limit(g.handle, 2)
+        codes = []
+        for _ in range(8):
+            g.seed()
+            try:
+                g.grow()
+                codes.append(Q.QSGS_OK)
+            except Q.QsgsError as e:
+                codes.append(e.code)
+                break
+        assert codes[-1] == Q.QSGS_ERR_TIMEOUT, codes
+        Q.qsgs_set_spin_limit(g.handle, 0)
+        g.seed()
+        st = g.grow()
+        phase = g.fetch().cpu().numpy()
+        assert hashlib.sha256(phase.tobytes()).hexdigest() == row["sha256_u8"]
+        assert (st.solid_count, st.steps, st.status) == (row["solid_count"], row["steps"],
+                                                         row["status"])
+    finally:
+        g.close()
