@@ -392,9 +392,10 @@ __device__ __forceinline__ bool has_blocked(const Geom& g) {
 }
 
 template <int DK>
-__device__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid, uint32_t w,
-                           uint32_t live_dirs, uint32_t (&V)[28], uint32_t (&Bm)[7],
-                           uint32_t& front, uint32_t& r, uint32_t& xw);
+__device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __restrict__ grid,
+                                           uint32_t w, uint32_t live_dirs, uint32_t (&V)[28],
+                                           uint32_t (&Bm)[7], uint32_t& front, uint32_t& r,
+                                           uint32_t& xw);
 
 struct FrontCountPolicy {
   Geom g;
