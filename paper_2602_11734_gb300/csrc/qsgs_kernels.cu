@@ -878,28 +878,30 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // solid, its d-neighbour is void and inside the domain, and d's class has a
 // positive threshold) and the 7 Philox-block masks B_b = OR of V_d over the
 // directions of block b; words that still hold front voxels are marked for
-// the next candidate list.  Phase 2: the lanes queue their (word, block,
-// voxel) pairs in shared memory, then the warp drains the queue two pairs
-// per lane at a time -- one Philox call per pair -- so no lane idles while
-// another draws; passing draws are buffered and claimed by full warps.
+// the next candidate list.  Phase 2: the non-empty (word, block) masks are
+// listed in shared memory as entries and the chunk's (voxel, block) pairs --
+// one Philox call each -- are numbered through them; lane L takes the L-th
+// 32nd of that range and walks it with a cursor (a binary search for its
+// first entry, then bit by bit, two pairs per iteration), so every lane draws
+// the same number of blocks whatever the density of its own word; passing
+// draws are buffered and claimed by full warps.
 // ---------------------------------------------------------------------------
 constexpr int kGrowThreads = 256;
 constexpr int kGrowWarps = kGrowThreads / 32;
 #ifndef QSGS_GROW_MIN_BLOCKS
 #define QSGS_GROW_MIN_BLOCKS 3  // resident blocks per SM the register budget aims for
 #endif
-constexpr int kGrowQueue = 2048;  // pairs per drain round; a word has at most 7 * 32
-constexpr int kGrowWins = 256;    // deferred claims buffered per warp
+constexpr int kGrowEntries = 7 * 32 + 1;  // non-empty masks of a chunk, plus one spare
+constexpr int kGrowWins = 256;            // deferred claims buffered per warp
 
 struct GrowWarpSmem {
-  uint4 V[32][7];  // per lane word, per block b: V_{4b..4b+3}
-  union {
-    uint32_t B[32 * 7];      // per lane word, per block: voxels that draw it (read
-                             // into registers before the queue is filled)
-    uint16_t Q[kGrowQueue];  // queued pairs: lane << 8 | block << 5 | bit
-  };
-  uint32_t w[32], v0[32];    // per lane: word index, voxel index of its bit 0
-  uint32_t win[kGrowWins];   // draws that passed a threshold: pair | pass bits << 16
+  uint4 V[32][7];                // per lane word, per block b: V_{4b..4b+3}
+  uint4 E[kGrowEntries];         // non-empty (word, block) masks: {voxels that draw
+                                 // the block, voxel index of bit 0, counter word
+                                 // kGrowTag | b, claim tag lane << 8 | b << 5}
+  uint16_t P[kGrowEntries + 1];  // number of the first pair of each entry
+  uint32_t w[32];                // per lane: word index
+  uint32_t win[kGrowWins];       // draws that passed a threshold: tag | bit | pass bits << 16
 };
 // Dynamic shared memory of a growth block (one GrowWarpSmem per warp).
 constexpr size_t kGrowSmemBytes = sizeof(GrowWarpSmem) * kGrowWarps;
@@ -1079,6 +1081,21 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   V[27] = 0;
 }
 
+// Index of the highest set bit of m (0xFFFFFFFF for m = 0) and 1 << i
+// (0 for i > 31): the PTX bfind and shl semantics, so that an exhausted mask
+// needs no test.
+__device__ __forceinline__ uint32_t top_bit(uint32_t m) {
+  uint32_t i;
+  asm("bfind.u32 %0, %1;" : "=r"(i) : "r"(m));
+  return i;
+}
+
+__device__ __forceinline__ uint32_t bit_at(uint32_t i) {
+  uint32_t b;
+  asm("shl.b32 %0, %1, %2;" : "=r"(b) : "r"(1u), "r"(i));
+  return b;
+}
+
 // One warp, one chunk of up to 32 candidate words (w = 0xFFFFFFFF: no word
 // for this lane).  All 32 lanes must call it together.
 template <int DK>
@@ -1090,6 +1107,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   const uint32_t lane = threadIdx.x & 31;
   // Phase 1: masks of this lane's word.
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
+  uint32_t v0 = 0;
   if (w != 0xFFFFFFFFu) {
     uint32_t V[28], front = 0, r, xw;
     word_masks<DK>(g, grid, w, live_dirs, V, Bm, front, r, xw);
@@ -1099,97 +1117,103 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
 #pragma unroll
     for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
     S.w[lane] = w;
-    S.v0[lane] = r * g.nx + xw * 32u;
+    v0 = r * g.nx + xw * 32u;
   }
-  // The 224 (word, block) masks are dealt round-robin to the lanes (lane j
-  // takes masks j, j+32, ...), which evens out the queueing work between
-  // dense and sparse words.
+  // Phase 2.  Pairs and non-empty masks of the lanes, counted by one warp
+  // scan (pairs in the low half-word: at most 7 * 32 * 32 = 7168).
+  uint32_t items = 0, ents = 0;
 #pragma unroll
-  for (int b = 0; b < 7; ++b) S.B[lane * 7 + b] = Bm[b];
-  __syncwarp();
-  uint32_t mine[7], items = 0;
-#pragma unroll
-  for (int gi = 0; gi < 7; ++gi) {
-    mine[gi] = S.B[lane + 32 * gi];
-    items += __popc(mine[gi]);
+  for (int b = 0; b < 7; ++b) {
+    items += __popc(Bm[b]);
+    ents += Bm[b] ? 1u : 0u;
   }
-  __syncwarp();  // S.B is overwritten by the queue below
-  uint32_t incl = items;
+  const uint32_t mine = items | (ents << 16);
+  uint32_t incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= (uint32_t)o) incl += y;
   }
-  const uint32_t excl = incl - items;
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t total = tot & 0xFFFFu, n_ent = tot >> 16;
   cnt.draws += total;  // one Philox block per pair; every pair has a live void target
-
-  // Phase 2: drain in rounds of at most kGrowQueue pairs.
-  uint32_t done = 0;  // pairs of the lanes already queued and drained
-  while (done < total) {
-    // Lanes whose pairs all fit into this round.
-    const bool fits = excl >= done && incl - done <= (uint32_t)kGrowQueue;
-    const uint32_t fit_mask = __ballot_sync(0xffffffffu, fits && items > 0);
-    uint32_t round_end = done;
-    if (fit_mask) round_end = __shfl_sync(0xffffffffu, incl, 31 - __clz(fit_mask));
-    if (fits && items > 0) {
-      uint32_t pos = excl - done;
+  if (total == 0) return;  // warp-uniform
+  {
+    const uint32_t excl = incl - mine;
+    uint32_t e = excl >> 16, p = excl & 0xFFFFu;
 #pragma unroll
-      for (int gi = 0; gi < 7; ++gi) {
-        uint32_t m = mine[gi];
-        const uint32_t q = lane + 32u * gi;        // mask index = word * 7 + block
-        const uint32_t tag = ((q / 7u) << 8) | ((q % 7u) << 5);
-        while (m) {  // two pairs per pass: half the passes of the densest mask
-          const uint32_t l1 = m & (0u - m);
-          m ^= l1;
-          const uint32_t l2 = m & (0u - m);
-          m ^= l2;
-          S.Q[pos] = (uint16_t)(tag | __popc(l1 - 1u));
-          if (l2) S.Q[pos + 1] = (uint16_t)(tag | __popc(l2 - 1u));
-          pos += l2 ? 2u : 1u;
-        }
+    for (int b = 0; b < 7; ++b) {
+      if (Bm[b]) {
+        S.E[e] = make_uint4(Bm[b], v0, kGrowTag | (uint32_t)b, (lane << 8) | ((uint32_t)b << 5));
+        S.P[e] = (uint16_t)p;
+        ++e;
+        p += __popc(Bm[b]);
       }
     }
-    __syncwarp();
-    const uint32_t round_n = round_end - done;
-    // Each lane draws two pairs per iteration (two independent Philox chains
-    // in flight hide the multiply latency).  Draws that pass a threshold (a
-    // few per cent) are buffered and claimed together, so the claim work
-    // runs on full warps instead of one or two lanes of every iteration.
-    uint32_t nwin = 0;
-    for (uint32_t k0 = 0; k0 < round_n; k0 += 64) {
-      const uint32_t ka = k0 + lane, kb = ka + 32;
-      const bool va = ka < round_n, vb = kb < round_n;
-      const uint32_t ea = va ? S.Q[ka] : 0u, eb = vb ? S.Q[kb] : 0u;
-      const uint32_t ba = (ea >> 5) & 7u, bb = (eb >> 5) & 7u;
-      const U4 ra = philox4x32_10(U4{S.v0[ea >> 8] + (ea & 31u), 0u, t, kGrowTag | ba}, keys);
-      const U4 rb = philox4x32_10(U4{S.v0[eb >> 8] + (eb & 31u), 0u, t, kGrowTag | bb}, keys);
-      const uint4 tha = thr[ba], thb = thr[bb];
-      uint32_t pa = (ra.x <= tha.x ? 1u : 0u) | (ra.y <= tha.y ? 2u : 0u) | (ra.z <= tha.z ? 4u : 0u) |
-                    (ra.w <= tha.w ? 8u : 0u);
-      uint32_t pb = (rb.x <= thb.x ? 1u : 0u) | (rb.y <= thb.y ? 2u : 0u) | (rb.z <= thb.z ? 4u : 0u) |
-                    (rb.w <= thb.w ? 8u : 0u);
-      pa = va ? pa : 0u;
-      pb = vb ? pb : 0u;
-      const uint32_t lt = (1u << lane) - 1u;
-      const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
-      const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
-      if (pa) S.win[nwin + __popc(bala & lt)] = ea | (pa << 16);
-      nwin += __popc(bala);
-      if (pb) S.win[nwin + __popc(balb & lt)] = eb | (pb << 16);
-      nwin += __popc(balb);
-      if (nwin > (uint32_t)kGrowWins - 64u) {
-        __syncwarp();
-        claim_wins<DK>(g, claims, S, nwin, lane);
-        __syncwarp();
-        nwin = 0;
-      }
-    }
-    __syncwarp();
-    claim_wins<DK>(g, claims, S, nwin, lane);
-    __syncwarp();  // S.Q is refilled by the next round
-    done = round_end;
   }
+  __syncwarp();
+  // Lane L draws pairs [s, s + n): an even split of the chunk's total.  Pairs
+  // are numbered entry by entry, highest voxel bit first within an entry.
+  const uint32_t per = total >> 5, extra = total & 31u;
+  const uint32_t n = per + (lane < extra ? 1u : 0u);
+  const uint32_t s = lane * per + min(lane, extra);
+  uint32_t k = 0;  // the last entry whose first pair is at or before s
+#pragma unroll
+  for (uint32_t step = 128; step; step >>= 1)
+    if (k + step < n_ent && S.P[k + step] <= s) k += step;
+  uint4 E = S.E[k];
+  uint32_t m = E.x;
+  for (uint32_t j = S.P[k]; j < s; ++j) m ^= bit_at(top_bit(m));  // pairs before s
+  // Each lane draws two pairs per iteration (two independent Philox chains
+  // in flight hide the multiply latency).  After a lane's pair empties the
+  // cursor's mask the cursor moves to the next entry (index at most n_ent:
+  // the spare entry is read, never used).  Draws that pass a threshold (a
+  // few per cent) are buffered and claimed together, so the claim work runs
+  // on full warps instead of one or two lanes of every iteration.
+  const uint32_t iters = (per + (extra ? 1u : 0u) + 1u) >> 1;
+  uint32_t nwin = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const bool va = 2u * it < n, vb = 2u * it + 1u < n;
+    const uint32_t ia = top_bit(m);
+    m ^= bit_at(ia);
+    const uint32_t xa = E.y + ia, cwa = E.z, ta = E.w | ia;
+    if (va && m == 0) {
+      E = S.E[++k];
+      m = E.x;
+    }
+    const uint32_t ib = top_bit(m);
+    m ^= bit_at(ib);
+    const uint32_t xb = E.y + ib, cwb = E.z, tb = E.w | ib;
+    if (vb && m == 0) {
+      E = S.E[++k];
+      m = E.x;
+    }
+    const U4 ra = philox4x32_10(U4{xa, 0u, t, cwa}, keys);
+    const U4 rb = philox4x32_10(U4{xb, 0u, t, cwb}, keys);
+    const uint4 tha = thr[cwa & 7u], thb = thr[cwb & 7u];
+    uint32_t pa = (ra.x <= tha.x ? 1u : 0u) | (ra.y <= tha.y ? 2u : 0u) | (ra.z <= tha.z ? 4u : 0u) |
+                  (ra.w <= tha.w ? 8u : 0u);
+    uint32_t pb = (rb.x <= thb.x ? 1u : 0u) | (rb.y <= thb.y ? 2u : 0u) | (rb.z <= thb.z ? 4u : 0u) |
+                  (rb.w <= thb.w ? 8u : 0u);
+    pa = va ? pa : 0u;
+    pb = vb ? pb : 0u;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
+    const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
+    if (pa) S.win[nwin + __popc(bala & lt)] = ta | (pa << 16);
+    nwin += __popc(bala);
+    if (pb) S.win[nwin + __popc(balb & lt)] = tb | (pb << 16);
+    nwin += __popc(balb);
+    if (nwin > (uint32_t)kGrowWins - 64u) {
+      __syncwarp();
+      claim_wins<DK>(g, claims, S, nwin, lane);
+      __syncwarp();
+      nwin = 0;
+    }
+  }
+  __syncwarp();
+  claim_wins<DK>(g, claims, S, nwin, lane);
+  __syncwarp();  // S.E, S.P, S.V and S.win are rewritten by the next chunk
 }
 
 // `draws` is warp-uniform (a chunk total); `front` is per lane.  live is
