@@ -1169,11 +1169,11 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   // cursor's mask the cursor moves to the next entry (index at most n_ent:
   // the spare entry is read, never used).  Draws that pass a threshold (a
   // few per cent) are buffered and claimed together, so the claim work runs
-  // on full warps instead of one or two lanes of every iteration.
-  const uint32_t iters = (per + (extra ? 1u : 0u) + 1u) >> 1;
+  // on full warps instead of one or two lanes of every iteration.  va / vb:
+  // the lane has a pair left (always, but in the last iteration).
+  const uint32_t full = per >> 1;  // iterations in which every lane has both pairs
   uint32_t nwin = 0;
-  for (uint32_t it = 0; it < iters; ++it) {
-    const bool va = 2u * it < n, vb = 2u * it + 1u < n;
+  auto draw2 = [&](const bool va, const bool vb) {
     const uint32_t ia = top_bit(m);
     m ^= bit_at(ia);
     const uint32_t xa = E.y + ia, cwa = E.z, ta = E.w | ia;
@@ -1210,7 +1210,9 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
       __syncwarp();
       nwin = 0;
     }
-  }
+  };
+  for (uint32_t it = 0; it < full; ++it) draw2(true, true);
+  if ((per & 1u) | extra) draw2(2u * full < n, 2u * full + 1u < n);
   __syncwarp();
   claim_wins<DK>(g, claims, S, nwin, lane);
   __syncwarp();  // S.E, S.P, S.V and S.win are rewritten by the next chunk
