@@ -53,9 +53,7 @@ __device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_
     if (lane == 0 && valid) mk = md.mark[(gs - md.word_base) >> 5];
     if (in) {
       c = md.aux[(size_t)par * md.g.nwords + w];
-      const uint32_t o = md.aux[(size_t)(par ^ 1u) * md.g.nwords + w];
       const uint32_t old = md.grid[w];
-      if (o) md.aux[(size_t)(par ^ 1u) * md.g.nwords + w] = 0;
       if (c) md.grid[w] = old | c;
     }
     if (mk) md.mark[(gs - md.word_base) >> 5] = 0;
@@ -120,16 +118,14 @@ __global__ void __launch_bounds__(256, 2)
     } else {
       if (!st->active) continue;
       const uint32_t par = st->t & 1u;
-      uint32_t* cur = md.aux + (size_t)par * md.g.nwords;
-      uint32_t* nxt = md.aux + (size_t)(par ^ 1u) * md.g.nwords;
-      uint32_t c[G], o[G], old[G], mk = 0;
+      const uint32_t* cur = md.aux + (size_t)par * md.g.nwords;
+      uint32_t c[G], old[G], mk = 0;
       if (lane < (uint32_t)G && g0 + lane <= glast) mk = md.mark[(lw0 >> 5) + lane];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t w = lw0 + j * 32u + lane;
         const bool in = g0 + j <= glast && w < nloc;
         c[j] = in ? cur[w] : 0u;
-        o[j] = in ? nxt[w] : 0u;
         old[j] = in ? grid[w] : 0u;
       }
       if (mk) md.mark[(lw0 >> 5) + lane] = 0;
@@ -137,7 +133,6 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t w = lw0 + j * 32u + lane;
-        if (o[j]) nxt[w] = 0;
         if (c[j]) md.grid[w] = old[j] | c[j];
         claims += (uint32_t)__popc(c[j]);
         const uint32_t mkw = __shfl_sync(0xffffffffu, mk, j);
@@ -258,10 +253,10 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
       const PhiloxKeys keys = md.keys;
       uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
+      uint32_t* other = md.aux + (size_t)((t & 1u) ^ 1u) * md.g.nwords;
       GrowCounters cnt{0, 0};
-      grow_chunk<kRuntime>(md.g, md.grid, claims, md.mark, w, t, live_dirs, s_thr[warp], keys,
-                           smem[warp],
-                 cnt);
+      grow_chunk<kRuntime>(md.g, md.grid, claims, other, md.mark, w, t, live_dirs, s_thr[warp],
+                           keys, smem[warp], cnt);
       flush_counters(st, cnt);
       __syncwarp();  // s_thr[warp] is rewritten by the next chunk
     }

@@ -229,73 +229,40 @@ struct SeedCompactPolicy {
 // U New_t) lies in those words, and the growth kernel itself computes the
 // exact front bits of every candidate word from the grid.
 //
-// kCommitInitial (after seeding): every word holding a solid voxel.
-// kCommitStep (after a growth step): ORs the step's claims into the grid,
-// counts them, emits marked or claimed words, clears the marks and the
-// claim grid of the next step.  The list stays in ascending word order.
-// (The step loop of a single realization uses k_commit below instead: the
-// growth step does not depend on the order of the list.)
-enum : int { kCommitInitial = 0, kCommitStep = 1 };
-
-struct CommitPolicy {
+// The first list of a run (after seeding, or after the blocked cells or
+// the state changed) is every word holding a solid voxel, in ascending word
+// order: InitialListPolicy, an ordered look-back scan over the words.  The
+// lists of later steps come from k_commit below.
+struct InitialListPolicy {
   Geom g;
   RunState* st;
-  uint32_t* grid;
-  uint32_t* aux;   // two claim grids of nwords words each
-  uint32_t* mark;  // one bit per word, set by the growth kernel
+  const uint32_t* grid;
   uint32_t* list;
-  int mode;
   struct Item {
-    uint32_t w;      // word index
-    uint32_t bits;   // 1: listed
-    uint32_t extra;  // claims of this step in the word
-    uint32_t old;    // the word before the claims
-    uint32_t flags;  // 1: lane 0 clears the warp's mark word; 2: clear the other claim word
+    uint32_t w;     // word index
+    uint32_t bits;  // 1: listed
   };
-  __device__ bool active() const { return mode == kCommitInitial || st->active != 0; }
+  __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
-  // Called by the 32 lanes of a warp together; lane l holds word 32j + l, so
-  // lane 0 reads the warp's mark word and shares it.
   __device__ Item load(uint32_t w, bool valid) const {
-    const uint32_t lane = threadIdx.x & 31u;
-    if (mode == kCommitInitial) {
-      const uint32_t solid = valid ? grid[w] : 0u;
-      return Item{w, solid ? 1u : 0u, 0u, 0u, 0u};
-    }
-    uint32_t m = 0;
-    if (lane == 0 && valid) m = mark[w >> 5];
-    m = __shfl_sync(0xffffffffu, m, 0);
-    if (!valid) return Item{w, 0u, 0u, 0u, 0u};
-    const uint32_t par = st->t & 1u;
-    const uint32_t c = aux[(size_t)par * g.nwords + w];
-    const uint32_t other = aux[(size_t)(par ^ 1u) * g.nwords + w];
-    const uint32_t old = grid[w];
-    const uint32_t keep = ((m >> lane) & 1u) | (c ? 1u : 0u);
-    return Item{w, keep, c, old, (lane == 0 && m ? 1u : 0u) | (other ? 2u : 0u)};
+    const uint32_t solid = valid ? grid[w] : 0u;
+    return Item{w, solid ? 1u : 0u};
   }
-  // Claims into the grid; the marks and the claim grid of the previous step
-  // are cleared for the next step.
-  __device__ void apply(const Item& it, bool valid) const {
-    if (mode == kCommitInitial || !valid) return;
-    if (it.flags & 1u) mark[it.w >> 5] = 0;
-    if (it.flags & 2u) aux[(size_t)((st->t & 1u) ^ 1u) * g.nwords + it.w] = 0;
-    if (it.extra) grid[it.w] = it.old | it.extra;
-  }
+  __device__ void apply(const Item&, bool) const {}
   __device__ uint32_t count(const Item& it) const { return it.bits; }
-  __device__ uint32_t side(const Item& it, int k) const { return k == 1 ? __popc(it.extra) : 0u; }
-  __device__ unsigned long long* side_sum(int k) const {
-    return (k == 1 && mode == kCommitStep) ? &st->claimed : nullptr;
-  }
+  __device__ uint32_t side(const Item&, int) const { return 0u; }
+  __device__ unsigned long long* side_sum(int) const { return nullptr; }
   __device__ void emit(const Item& it, unsigned long long off) const { list[off] = it.w; }
   __device__ void total(unsigned long long n) const { st->front_words = (uint32_t)n; }
 };
 
-// Commit of a growth step without an ordered scan: the same work as
-// CommitPolicy in kCommitStep mode, but the next candidate list is appended
-// in any order (one atomic per block and tile), so no tile waits on
-// another.  The growth step gives the same result for any order of its
-// list: every draw is keyed by (voxel, step, block) and claims are ORed.
+// Commit of a growth step: ORs the step's claims into the grid, counts them,
+// appends marked or claimed words to the next candidate list and clears the
+// marks (the growth kernel has already cleared the other claim grid).  The
+// list is appended in any order (one atomic per block and tile), so no tile
+// waits on another: the growth step gives the same result for any order of
+// its list, every draw being keyed by (voxel, step, block) and claims ORed.
 // Thread t of a block takes words base + k * 256 + t (k < 8) of a 2048-word
 // tile; all loads of a tile are issued before its stores.
 constexpr int kCommitThreads = 256;
@@ -312,20 +279,18 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t par = st->t & 1u;
   const uint32_t nw = g.nwords;
-  uint32_t* claims = aux + (size_t)par * nw;
-  uint32_t* prev = aux + (size_t)(par ^ 1u) * nw;  // claim grid of the next step
+  const uint32_t* claims = aux + (size_t)par * nw;
   if (threadIdx.x == 0) s_claimed = 0;
   uint32_t claimed = 0;
   constexpr uint32_t kTile = kCommitThreads * kCommitItems;
   for (uint32_t base = blockIdx.x * kTile; base < nw; base += gridDim.x * kTile) {
-    uint32_t m[kCommitItems], c[kCommitItems], o[kCommitItems], old[kCommitItems];
+    uint32_t m[kCommitItems], c[kCommitItems], old[kCommitItems];
 #pragma unroll
     for (int k = 0; k < kCommitItems; ++k) {
       const uint32_t w = base + k * kCommitThreads + threadIdx.x;
       const bool valid = w < nw;
       m[k] = (lane == 0 && valid) ? mark[w >> 5] : 0u;
       c[k] = valid ? claims[w] : 0u;
-      o[k] = valid ? prev[w] : 0u;
       old[k] = valid ? grid[w] : 0u;
     }
     uint32_t keep = 0;  // bit k: word k is listed
@@ -333,7 +298,6 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
     for (int k = 0; k < kCommitItems; ++k) {
       const uint32_t w = base + k * kCommitThreads + threadIdx.x;
       if (m[k]) mark[w >> 5] = 0;
-      if (o[k]) prev[w] = 0;
       if (c[k]) grid[w] = old[k] | c[k];
       claimed += __popc(c[k]);
       const uint32_t mk = __shfl_sync(0xffffffffu, m[k], 0);
@@ -1100,7 +1064,8 @@ __device__ __forceinline__ uint32_t bit_at(uint32_t i) {
 // for this lane).  All 32 lanes must call it together.
 template <int DK>
 __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
-                                           uint32_t* claims, uint32_t* mark, uint32_t w,
+                                           uint32_t* claims, uint32_t* other, uint32_t* mark,
+                                           uint32_t w,
                                            uint32_t t, uint32_t live_dirs, const uint4* thr,
                                            const PhiloxKeys& keys, GrowWarpSmem& S,
                                            GrowCounters& cnt) {
@@ -1114,6 +1079,11 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     cnt.front += __popc(front);
     // A word holding front voxels now may hold some after the step too.
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
+    // The other claim grid takes the next step's claims.  Its only non-zero
+    // words hold the previous step's claims (already in the grid), and
+    // every word claimed then is on this step's list: clearing listed words
+    // leaves it all zero for the next step.
+    other[w] = 0;
 #pragma unroll
     for (int b = 0; b < 7; ++b) S.V[lane][b] = make_uint4(V[4 * b], V[4 * b + 1], V[4 * b + 2], V[4 * b + 3]);
     S.w[lane] = w;
@@ -1269,6 +1239,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   load_thresholds(st, threadIdx.x, s_thr);
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
+  uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
   const uint32_t nchunks = (n + 31) / 32;
@@ -1281,7 +1252,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
       const uint32_t idx = c * 32u + lane;
       uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
       if (w >= g.nwords) w = 0xFFFFFFFFu;  // only after a timed-out scan (reported)
-      grow_chunk<DK>(g, grid, claims, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
+      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
     }
   }
   flush_counters(st, cnt);
@@ -1308,6 +1279,7 @@ __global__ void __launch_bounds__(256)
   load_thresholds(st, threadIdx.x, s_thr);
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;
+  uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;  // cleared as in k_grow
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t rounds = (g.nwords + stride - 1) / stride;  // uniform: every lane loops alike
   uint32_t front_n = 0, live_n = 0;
@@ -1319,6 +1291,7 @@ __global__ void __launch_bounds__(256)
     word_masks<kRuntime>(g, grid, w, live_dirs, V, Bm, front, r, xw);
     front_n += __popc(front);
     if (front) atomicOr(mark + (w >> 5), 1u << (w & 31));
+    other[w] = 0;
     const uint32_t x0 = xw * 32u;
     const uint32_t len = min(32u, g.nx - x0);
     const uint32_t v0 = r * g.nx + x0;
@@ -1605,8 +1578,8 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<AcceptPolicy>, scan_grid(g.n), kScanThreads, ap,
               ctl);
   // Initial candidate words (Sec. 2.3 step 2) replace the candidate list.
-  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitInitial};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
+  InitialListPolicy cp{g, b.st, b.grid, b.list};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<InitialListPolicy>, scan_grid(g.nwords), kScanThreads,
               cp, ctl);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, (cudaGraphConditionalHandle)0, 0);
   return cudaSuccess;
@@ -1739,8 +1712,8 @@ cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, u
 cudaError_t launch_front_list(const Geom& g, const StepBuffers& b, uint32_t spin_limit,
                               cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
-  CommitPolicy cp{g, b.st, b.grid, b.aux, b.mark, b.list, kCommitInitial};
-  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<CommitPolicy>, scan_grid(g.nwords), kScanThreads,
+  InitialListPolicy cp{g, b.st, b.grid, b.list};
+  QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<InitialListPolicy>, scan_grid(g.nwords), kScanThreads,
               cp, ctl);
   return cudaSuccess;
 }
