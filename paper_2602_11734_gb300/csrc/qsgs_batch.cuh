@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       RunState* st = md.st;
       const uint32_t t = st->t;
       const uint32_t live_dirs = live_directions(st);
-      load_thresholds(st, lane, s_thr[warp]);
+      load_thresholds<true>(st, lane, s_thr[warp]);  // complemented, for fail_bits
       __syncwarp();
       const uint32_t j = (c - md.chunk_base) * 32u + lane;
       const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;

@@ -954,11 +954,15 @@ struct GrowCounters {
 // Per-direction thresholds of one instance as T - 1 (a draw succeeds iff
 // r <= T - 1), grouped by Philox block, and the mask of live directions
 // (classes with T > 0).  Written by lanes 0..27 of a warp or block.
+// kComplement stores ~(T - 1) instead: r + ~(T - 1) carries out of 32 bits
+// exactly when r > T - 1, which fail_bits below reads off the carry flag.
+template <bool kComplement = false>
 __device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr) {
   if (lane < 28) {
     const int d = (int)lane;
     const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
-    reinterpret_cast<uint32_t*>(thr)[d] = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+    const uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+    reinterpret_cast<uint32_t*>(thr)[d] = kComplement ? ~t1 : t1;
   }
 }
 
@@ -1045,6 +1049,26 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   V[27] = 0;
 }
 
+// Bit j set: word j of r fails its threshold (r_j > T_j - 1), for the four
+// words of a Philox block against the complemented thresholds nthr_j =
+// ~(T_j - 1): the carry out of r_j + nthr_j, shifted in word by word (w
+// first, so that x lands in bit 0).  Eight integer adds, no compare/select.
+__device__ __forceinline__ uint32_t fail_bits(const U4& r, const uint4& nthr) {
+  uint32_t acc, t;
+  asm("add.cc.u32 %1, %2, %3;\n\t"
+      "addc.u32 %0, %10, %10;\n\t"
+      "add.cc.u32 %1, %4, %5;\n\t"
+      "addc.u32 %0, %0, %0;\n\t"
+      "add.cc.u32 %1, %6, %7;\n\t"
+      "addc.u32 %0, %0, %0;\n\t"
+      "add.cc.u32 %1, %8, %9;\n\t"
+      "addc.u32 %0, %0, %0;"
+      : "=&r"(acc), "=&r"(t)
+      : "r"(r.w), "r"(nthr.w), "r"(r.z), "r"(nthr.z), "r"(r.y), "r"(nthr.y), "r"(r.x),
+        "r"(nthr.x), "r"(0u));
+  return acc;
+}
+
 // Index of the highest set bit of m (0xFFFFFFFF for m = 0) and 1 << i
 // (0 for i > 31): the PTX bfind and shl semantics, so that an exhausted mask
 // needs no test.
@@ -1065,8 +1089,8 @@ __device__ __forceinline__ uint32_t bit_at(uint32_t i) {
 template <int DK>
 __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __restrict__ grid,
                                            uint32_t* claims, uint32_t* other, uint32_t* mark,
-                                           uint32_t w,
-                                           uint32_t t, uint32_t live_dirs, const uint4* thr,
+                                           uint32_t w, uint32_t t, uint32_t live_dirs,
+                                           const uint4* nthr,
                                            const PhiloxKeys& keys, GrowWarpSmem& S,
                                            GrowCounters& cnt) {
   const uint32_t lane = threadIdx.x & 31;
@@ -1160,13 +1184,8 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     }
     const U4 ra = philox4x32_10(U4{xa, 0u, t, cwa}, keys);
     const U4 rb = philox4x32_10(U4{xb, 0u, t, cwb}, keys);
-    const uint4 tha = thr[cwa & 7u], thb = thr[cwb & 7u];
-    uint32_t pa = (ra.x <= tha.x ? 1u : 0u) | (ra.y <= tha.y ? 2u : 0u) | (ra.z <= tha.z ? 4u : 0u) |
-                  (ra.w <= tha.w ? 8u : 0u);
-    uint32_t pb = (rb.x <= thb.x ? 1u : 0u) | (rb.y <= thb.y ? 2u : 0u) | (rb.z <= thb.z ? 4u : 0u) |
-                  (rb.w <= thb.w ? 8u : 0u);
-    pa = va ? pa : 0u;
-    pb = vb ? pb : 0u;
+    const uint32_t pa = va ? fail_bits(ra, nthr[cwa & 7u]) ^ 0xFu : 0u;  // passing words
+    const uint32_t pb = vb ? fail_bits(rb, nthr[cwb & 7u]) ^ 0xFu : 0u;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
     const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
@@ -1236,7 +1255,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
   const uint32_t live_dirs = live_directions(st);
-  load_thresholds(st, threadIdx.x, s_thr);
+  load_thresholds<true>(st, threadIdx.x, s_thr);  // complemented, for fail_bits
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;
