@@ -237,9 +237,11 @@ void destroy_graph(qsgs_handle* h) {
 }
 
 // Captures the whole growth loop of this handle into one graph: a while
-// node whose body is one step (its last kernel sets the loop condition),
-// followed by the exact-target epilogue.  Kernel arguments are fixed per
+// node whose body is kGraphStepsPerIteration steps (each one's last kernel
+// sets the loop condition), followed by the exact-target epilogue.  Kernel arguments are fixed per
 // handle, so the graph is built once and relaunched by every call.
+constexpr int kGraphStepsPerIteration = 4;
+
 cudaError_t build_graph(qsgs_handle* h) {
   cudaError_t e = cudaGraphCreate(&h->graph, 0);
   if (e != cudaSuccess) return e;
@@ -260,9 +262,14 @@ cudaError_t build_graph(qsgs_handle* h) {
   e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit,
-                               GrowShape{h->grow_blocks, h->grow_tile}, h->stream, capture_tracer,
-                               cond, 1, h->mode == QSGS_MODE_FULLFIELD);
+  // kGraphStepsPerIteration steps per evaluation of the loop condition: each
+  // step's kernels return at once when the step is not active, so the copies
+  // after the last step of a run cost a few microseconds of empty launches,
+  // against one conditional evaluation saved per step otherwise.
+  cudaError_t le = cudaSuccess;
+  for (int u = 0; u < kGraphStepsPerIteration && le == cudaSuccess; ++u)
+    le = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, GrowShape{h->grow_blocks, h->grow_tile},
+                     h->stream, capture_tracer, cond, 1, h->mode == QSGS_MODE_FULLFIELD);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(h->stream, &captured);
   if (le != cudaSuccess) return le;

@@ -115,10 +115,23 @@ __device__ void close_step(RunState* st) {
 
 // Closes the step that just ran and opens the next.  With a graph
 // conditional handle, also tells the enclosing while loop whether to go on.
-__global__ void k_step_control(RunState* st, cudaGraphConditionalHandle cond, int use_cond) {
-  close_step(st);
-  begin_step(st);
-  if (use_cond) cudaGraphSetConditional(cond, st->active ? 1u : 0u);
+// One warp: the 256-byte state comes in and goes back in one coalesced
+// access each, and lane 0 works on the shared-memory copy, so the chain of
+// dependent field reads costs shared-memory latency, not L2 latency.
+__global__ void __launch_bounds__(32)
+    k_step_control(RunState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  static_assert(sizeof(RunState) == 32 * sizeof(unsigned long long), "one word per lane");
+  __shared__ RunState s;
+  const uint32_t lane = threadIdx.x;
+  reinterpret_cast<unsigned long long*>(&s)[lane] = reinterpret_cast<const unsigned long long*>(st)[lane];
+  __syncwarp();
+  if (lane == 0) {
+    close_step(&s);
+    begin_step(&s);
+    if (use_cond) cudaGraphSetConditional(cond, s.active ? 1u : 0u);
+  }
+  __syncwarp();
+  reinterpret_cast<unsigned long long*>(st)[lane] = reinterpret_cast<unsigned long long*>(&s)[lane];
 }
 
 __device__ void set_step_limit(RunState* st, uint32_t extra) {
@@ -1054,16 +1067,17 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
 // ~(T_j - 1): the carry out of r_j + nthr_j, shifted in word by word (w
 // first, so that x lands in bit 0).  Eight integer adds, no compare/select.
 __device__ __forceinline__ uint32_t fail_bits(const U4& r, const uint4& nthr) {
-  uint32_t acc, t;
-  asm("add.cc.u32 %1, %2, %3;\n\t"
-      "addc.u32 %0, %10, %10;\n\t"
-      "add.cc.u32 %1, %4, %5;\n\t"
+  uint32_t acc;
+  asm("{\n\t.reg .u32 s;\n\t"
+      "add.cc.u32 s, %1, %2;\n\t"
+      "addc.u32 %0, %9, %9;\n\t"
+      "add.cc.u32 s, %3, %4;\n\t"
       "addc.u32 %0, %0, %0;\n\t"
-      "add.cc.u32 %1, %6, %7;\n\t"
+      "add.cc.u32 s, %5, %6;\n\t"
       "addc.u32 %0, %0, %0;\n\t"
-      "add.cc.u32 %1, %8, %9;\n\t"
-      "addc.u32 %0, %0, %0;"
-      : "=&r"(acc), "=&r"(t)
+      "add.cc.u32 s, %7, %8;\n\t"
+      "addc.u32 %0, %0, %0;\n\t}"
+      : "=&r"(acc)
       : "r"(r.w), "r"(nthr.w), "r"(r.z), "r"(nthr.z), "r"(r.y), "r"(nthr.y), "r"(r.x),
         "r"(nthr.x), "r"(0u));
   return acc;
@@ -1600,7 +1614,7 @@ cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32
   InitialListPolicy cp{g, b.st, b.grid, b.list};
   QSGS_LAUNCH(tr, kClsFront, s, k_lookback_scan<InitialListPolicy>, scan_grid(g.nwords), kScanThreads,
               cp, ctl);
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, (cudaGraphConditionalHandle)0, 0);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 32, b.st, (cudaGraphConditionalHandle)0, 0);
   return cudaSuccess;
 }
 
@@ -1630,7 +1644,7 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
   }
   QSGS_LAUNCH(tr, kClsFront, s, k_commit, commit_grid(g.nwords), kCommitThreads, g, b.st, b.grid,
               b.aux, b.mark, b.list);
-  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 1, b.st, cond, use_cond);
+  QSGS_LAUNCH(tr, kClsStepCtl, s, k_step_control, 1, 32, b.st, cond, use_cond);
   return cudaSuccess;
 }
 
