@@ -920,7 +920,7 @@ __device__ __forceinline__ void row_words(const Geom& g, const uint32_t* __restr
   }
 }
 
-template <int DZ, int DY, int DK>
+template <int DZ, int DY, int DK, bool kInterior = false>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
                                           uint32_t self, const uint32_t (&live)[3],
@@ -931,7 +931,7 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
     zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
   }
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
-  if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
+  if (kInterior || (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz)) {
     const size_t ro = (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
     row_words<DK>(g, grid + ro, xw, c, l, rr);
     if (has_blocked<DK>(g)) {  // cells of earlier phases are not void either
@@ -1049,15 +1049,32 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   // Per class: all ones if its threshold is positive (live), else zero.
   const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
                             0u - ((live_dirs >> 18) & 1u)};
-  row_masks<-1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<-1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<-1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<0, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-  row_masks<1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  // On the open domain, words whose nine neighbour rows all lie inside the
+  // grid (almost all of them) take a copy without the per-row bounds tests
+  // and branches (4 % of the 400^3 growth time).  The torus and run-time
+  // kinds keep one copy: there the second one costs more in register
+  // spills than it saves.
+  if (DK == kOpen && y >= 1 && y + 1 < g.ny && z >= 1 && z + 1 < g.nz) {
+    row_masks<-1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  } else {
+    row_masks<-1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<0, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+  }
   V[26] = 0;
   V[27] = 0;
 }
