@@ -37,13 +37,13 @@ CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
 PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
 # DRAM bytes (read + write) per k_grow launch of the 400^3 realization, from
-# an ncu capture of a 160^3 run scaled by Philox blocks to the 1.569e9 blocks
-# of the 400^3 run; None until the current kernel has been captured (reset
-# to None whenever the kernel changes).
-K_GROW_TRAFFIC_BYTES = None
+# an ncu capture of a 160^3 run (65.1 MB over its 56 launches and 1.024e8
+# Philox blocks) scaled by Philox blocks to the 1.569e9 blocks of the 400^3
+# run; to be reset to None whenever the kernel changes.
+K_GROW_TRAFFIC_BYTES = 17.8e6
 # L2 load of the same kernel: lts__throughput of its mid-run launches (ncu
 # --set full, launches 31-32 of the 400^3 run); reset to None with the above.
-K_GROW_L2_PCT = None
+K_GROW_L2_PCT = 10.7
 
 
 def parse():
