@@ -707,9 +707,11 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   if (!b || (n && !members) || n > b->max_members) return QSGS_ERR_INVALID;
   std::vector<MemberDesc> descs(n);
   uint64_t words = 0;
+  uint32_t open_only = 1;
   for (uint32_t m = 0; m < n; ++m) {
     qsgs_handle* h = members[m];
     if (!h) return QSGS_ERR_INVALID;
+    if (h->g.periodic || h->g.blocked) open_only = 0;
     MemberDesc& d = descs[m];
     std::memset(&d, 0, sizeof(d));
     d.g = h->g;
@@ -741,6 +743,13 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   if (e != cudaSuccess) return batch_fail(b, e);
   b->members.assign(members, members + n);
   b->host_descs = descs;
+  // The growth kernel's domain kind is fixed in the graph: a change of kind
+  // rebuilds it at the next advance.
+  if (open_only != b->buf.open_only) {
+    destroy_batch_graph(b);
+    b->graph_tried = false;
+    b->buf.open_only = open_only;
+  }
   for (qsgs_handle* h : b->members) h->list_stale = true;
   return QSGS_OK;
 }

@@ -227,7 +227,10 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
 // Growth over the batch candidate list: warp chunk c belongs to the member
 // whose chunk range holds c, so every warp serves one member at a time.
 // Three blocks per SM like k_grow (the register cap costs a few spilled
-// bytes; measured faster than two blocks per SM).
+// bytes; measured faster than two blocks per SM).  DK = kOpen when no
+// member is periodic or has blocked cells (the open-domain code path of
+// k_grow), else kRuntime, which decides per member.
+template <int DK>
 __global__ void __launch_bounds__(kGrowThreads, 3)
     k_grow_batch(const MemberDesc* __restrict__ d, BatchState* bs,
                  const uint32_t* __restrict__ list, uint32_t tile) {
@@ -255,8 +258,8 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
       uint32_t* other = md.aux + (size_t)((t & 1u) ^ 1u) * md.g.nwords;
       GrowCounters cnt{0, 0};
-      grow_chunk<kRuntime>(md.g, md.grid, claims, other, md.mark, w, t, live_dirs, s_thr[warp],
-                           keys, smem[warp], cnt);
+      grow_chunk<DK>(md.g, md.grid, claims, other, md.mark, w, t, live_dirs, s_thr[warp], keys,
+                     smem[warp], cnt);
       flush_counters(st, cnt);
       __syncwarp();  // s_thr[warp] is rewritten by the next chunk
     }

@@ -1565,7 +1565,10 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_grow_batch<kOpen>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow_batch<kRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_spacing_rounds_csr, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1580,7 +1583,10 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_grow_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_grow_batch<kOpen>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow_batch<kRuntime>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
@@ -1719,7 +1725,7 @@ uint32_t default_grow_blocks() {
 
 uint32_t default_batch_grow_blocks() {
   static uint32_t blocks = 0;
-  if (!blocks) blocks = grow_wave(k_grow_batch);
+  if (!blocks) blocks = grow_wave(k_grow_batch<kRuntime>);
   return blocks;
 }
 
@@ -1841,8 +1847,12 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowSh
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond) {
   (void)spin_limit;
-  QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch, shape.blocks, kGrowThreads, kGrowSmemBytes,
-                   b.d, b.bs, b.list, shape.tile);
+  if (b.open_only)
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch<kOpen>, shape.blocks, kGrowThreads,
+                     kGrowSmemBytes, b.d, b.bs, b.list, shape.tile);
+  else
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch<kRuntime>, shape.blocks, kGrowThreads,
+                     kGrowSmemBytes, b.d, b.bs, b.list, shape.tile);
   QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
               b.list, 0);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,

@@ -183,6 +183,7 @@ struct BatchBuffers {
   uint32_t* list;
   uint32_t max_members;
   uint64_t max_words;
+  uint32_t open_only;  // no member is periodic or has blocked cells
 };
 
 // Batch step limits, prologue commit (lists every running member's solid
