@@ -112,6 +112,42 @@ def test_membership_changes_mid_run(oracle, Q):
             g.close()
 
 
+def test_domain_kind_switches_between_advances(oracle, Q):
+    # Open-only memberships run the open-domain growth kernel, memberships
+    # with a periodic member the run-time one; the batch graph is rebuilt
+    # whenever the kind changes, mid-run included.
+    rng = np.random.default_rng(11)
+    opens = [dict(workloads.small_64(), nx=int(rng.integers(20, 45)), ny=int(rng.integers(20, 45)),
+                  nz=int(rng.integers(20, 45)), spacing_s=int(rng.integers(0, 5)), seed=30 + i)
+             for i in range(3)]
+    torus = dict(workloads.small_64(), nx=33, ny=29, nz=31, spacing_s=3, seed=41, periodic=1)
+    params = opens + [torus]
+    gens = [Q.Generator(p) for p in params]
+    b = Q.Batch(4, sum(Q.word_count(p) for p in params))
+    try:
+        for g in gens:
+            g.seed()
+        o1, o2, o3, per = gens
+        b.set_members([o1, o2])           # open only
+        b.advance(3)
+        b.query()
+        b.set_members([o1, per, o3])      # a periodic member joins: run-time kind
+        b.advance(3)
+        b.query()
+        b.set_members([o2, o3])           # open only again
+        b.advance(0)
+        stats = {id(x): s for x, s in zip(b.members, b.query())}
+        b.set_members([o1, per])          # mixed, to the end
+        b.advance(0)
+        stats.update({id(x): s for x, s in zip(b.members, b.query())})
+        for g, p in zip(gens, params):
+            check_member(oracle, g, stats[id(g)], p)
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
+
+
 def test_batch_rerun_and_direct_launches(oracle, Q):
     rng = np.random.default_rng(5)
     params = [workloads.random_small(rng, max_edge=30) for _ in range(6)]
