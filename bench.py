@@ -35,7 +35,16 @@ WORKLOAD = "single_400"
 L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2: written between timed steps
 CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
-PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the ALU-ceiling probe
+PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the Philox-only probe
+# Issue-bound ALU peak of the growth kernel's work unit: each SM has four
+# warp schedulers issuing one warp-instruction (32 lanes) per clock, and a
+# Philox4x32-10 block is at least 40 lane-instructions (ten rounds of two
+# 32x32->64 multiplies and two three-input XORs), so the ceiling is
+# SMs x 4 x clock x 32 / 40 blocks per second (152 SMs at 2070 MHz:
+# 1.007e12 blocks/s).
+SCHEDULERS_PER_SM = 4
+PHILOX_BLOCK_INSTRUCTIONS = 40
+DEFAULT_SM_MHZ = 2070.0           # maximum SM clock of a GB300
 # DRAM bytes (read + write) per k_grow launch of the 400^3 realization, from
 # an ncu capture of a 160^3 run (65.1 MB over its 56 launches and 1.024e8
 # Philox blocks) scaled by Philox blocks to the 1.569e9 blocks of the 400^3
@@ -549,8 +558,9 @@ def main():
 
     # Kernel-level pass with the library's event profiler (not timed above).
     # k_grow is bound by integer ALU work: one Philox4x32-10 block per
-    # (front voxel, direction block) pair.  Its ceiling is the rate of the
-    # library's Philox probe on this GPU (same generator, no memory traffic).
+    # (front voxel, direction block) pair.  Its ceiling is the issue-bound
+    # Philox rate derived from the SM count and clock; the rate the library's
+    # Philox-only probe reaches on this GPU is reported beside it.
     g.set_profiling(True)
     g.seed()
     st_prof = g.grow()
@@ -560,14 +570,21 @@ def main():
     probe_out = torch.zeros(1, dtype=torch.int64, device=dev)
     probe_ms = min(Q.qsgs_bench_philox(PEAK_PROBE_BLOCKS, probe_out.data_ptr(), s.cuda_stream)
                    for _ in range(3))
-    peak = PEAK_PROBE_BLOCKS / (probe_ms / 1000.0) / 1e9
+    probe = PEAK_PROBE_BLOCKS / (probe_ms / 1000.0) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or DEFAULT_SM_MHZ
+    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 * 32 / PHILOX_BLOCK_INSTRUCTIONS / 1e9
     achieved = st_prof.sum_draws / (grow_ms / 1000.0) / 1e9
     pk, pk_kind = peaks()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gblock/s",
                 "frac": achieved / peak,
                 "traffic": K_GROW_TRAFFIC_BYTES if a.edge == 400 else None, "kernel": "k_grow",
                 "work": "Philox4x32-10 blocks drawn per second",
-                "peak_kind": "measured (qsgs_bench_philox probe on this GPU)",
+                "peak_kind": (f"derived: {sms} SMs x {SCHEDULERS_PER_SM} warp schedulers x "
+                              f"{sm_mhz:.0f} MHz x 32 lanes / {PHILOX_BLOCK_INSTRUCTIONS} "
+                              f"instructions per Philox4x32-10 block (issue bound)"),
+                "probe": {"value": probe, "unit": "Gblock/s", "frac": achieved / probe,
+                          "what": "qsgs_bench_philox: Philox4x32-10 alone on this GPU"},
                 "draws": st_prof.sum_draws, "launches": grow_launches,
                 "mean_launch_ms": grow_ms / max(1, grow_launches),
                 "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
