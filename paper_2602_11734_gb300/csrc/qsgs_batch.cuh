@@ -241,18 +241,25 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
   const uint32_t total = bs->total_chunks, n = bs->n_members;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
   const uint32_t ntiles = (total + tile - 1) / tile;
+  // The member of the warp's last chunk, its chunk range and thresholds (in
+  // s_thr[warp]) stay while the next chunk is the same member's.
+  uint32_t cur = 0xFFFFFFFFu, lo = 0, hi = 0, live_dirs = 0;
   for (uint32_t ti = blockIdx.x * kGrowWarps + warp; ti < ntiles;
        ti = next_chunk(&bs->scan.grow_next, nwarps)) {
     const uint32_t c_end = min(ti * tile + tile, total);
     for (uint32_t c = ti * tile; c < c_end; ++c) {
-      const uint32_t m = find_member(d, n, c, [](const MemberDesc& x) { return x.chunk_base; });
-      const MemberDesc& md = d[m];
-      RunState* st = md.st;
-      const uint32_t t = st->t;
-      const uint32_t live_dirs = live_directions(st);
-      load_thresholds<true>(st, lane, s_thr[warp]);  // complemented, for fail_bits
-      __syncwarp();
-      const uint32_t j = (c - md.chunk_base) * 32u + lane;
+      if (c < lo || c >= hi) {  // warp-uniform
+        cur = find_member(d, n, c, [](const MemberDesc& x) { return x.chunk_base; });
+        lo = d[cur].chunk_base;
+        hi = cur + 1 < n ? d[cur + 1].chunk_base : total;
+        live_dirs = live_directions(d[cur].st);
+        __syncwarp();  // the previous member's thresholds are no longer read
+        load_thresholds<true>(d[cur].st, lane, s_thr[warp]);  // complemented, for fail_bits
+        __syncwarp();
+      }
+      const MemberDesc& md = d[cur];
+      const uint32_t t = md.st->t;
+      const uint32_t j = (c - lo) * 32u + lane;
       const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
       const PhiloxKeys keys = md.keys;
       uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
@@ -260,8 +267,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       GrowCounters cnt{0, 0};
       grow_chunk<DK>(md.g, md.grid, claims, other, md.mark, w, t, live_dirs, s_thr[warp], keys,
                      smem[warp], cnt);
-      flush_counters(st, cnt);
-      __syncwarp();  // s_thr[warp] is rewritten by the next chunk
+      flush_counters(md.st, cnt);
     }
   }
   finish_dispenser(&bs->scan.grow_next, &bs->scan.grow_done);
