@@ -728,39 +728,21 @@ __global__ void k_conflict_fill(Geom g, CellGeom cg, const RunState* st, const u
 
 // Rounds over the conflict lists (one block).  Each round settles at least
 // the lowest undecided candidate, so cand_n + 1 rounds always suffice.  The
-// decisions live in shared memory while they fit (kSpacingSmem bytes), else
-// in the global array; they are copied out at the end.  When the conflict
-// lists fit beside them (offsets and entries: 4 bytes each), they are staged
-// into shared memory too, so that the rounds -- each a chain of dependent
-// reads -- pay shared-memory latency instead of L2 latency (6400
-// candidates of the 400^3 workload: ~75 KB).
-constexpr uint32_t kSpacingSmem = 200 * 1024;
+// decisions live in shared memory while they fit (kSpacingSmem candidates),
+// else in the global array; they are copied out at the end.
+constexpr uint32_t kSpacingSmem = 64 * 1024;
 
 __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
                                                             const uint32_t* off,
                                                             const uint32_t* adj,
                                                             uint8_t* decision,
                                                             unsigned long long cap) {
-  extern __shared__ uint4 s_spacing_[];  // 16-byte aligned
-  uint8_t* s_mem = reinterpret_cast<uint8_t*>(s_spacing_);
+  extern __shared__ uint8_t s_decision[];
   __shared__ uint32_t s_undecided;
-  const unsigned long long adj_n = st->adj_n;
-  if (adj_n > cap) return;
+  if (st->adj_n > cap) return;
   const uint32_t n = st->cand_n;
-  const unsigned long long nd = ((unsigned long long)n + 15ull) & ~15ull;
   const bool in_smem = n <= kSpacingSmem;
-  const bool lists_in_smem = nd + 4ull * ((unsigned long long)n + 1ull) + 4ull * adj_n <= kSpacingSmem;
-  uint8_t* dec = in_smem ? s_mem : decision;
-  const uint32_t* o = off;
-  const uint32_t* a = adj;
-  if (lists_in_smem) {
-    uint32_t* so = reinterpret_cast<uint32_t*>(s_mem + nd);
-    uint32_t* sa = so + n + 1;
-    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) so[i] = off[i];
-    for (uint32_t k = threadIdx.x; k < (uint32_t)adj_n; k += blockDim.x) sa[k] = adj[k];
-    o = so;
-    a = sa;
-  }
+  uint8_t* dec = in_smem ? s_decision : decision;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dec[i] = 0;
   __syncthreads();
   for (uint32_t round = 0; round <= n; ++round) {
@@ -770,9 +752,9 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       if (((volatile uint8_t*)dec)[i] != 0) continue;
       bool pending = false, rejected = false;
-      const unsigned long long k_end = o[i + 1] < cap ? o[i + 1] : cap;
-      for (unsigned long long k = o[i]; k < k_end; ++k) {
-        const uint32_t j = a[k];
+      const unsigned long long k_end = off[i + 1] < cap ? off[i + 1] : cap;
+      for (unsigned long long k = off[i]; k < k_end; ++k) {
+        const uint32_t j = adj[k];
         if (j >= n) continue;  // only after a timed-out scan (reported)
         const uint8_t dj = ((volatile uint8_t*)dec)[j];
         if (dj == 1) { rejected = true; break; }
@@ -789,7 +771,7 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
     if (left == 0) break;
   }
   if (in_smem)
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = s_mem[i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = s_decision[i];
 }
 
 // Fallback when the conflict lists exceed their buffer: one block runs all
