@@ -105,6 +105,11 @@ def test_ragged_multiword_parity(oracle, Q, dims):
     dict(spacing_s=1),
     dict(spacing_s=64, cd=0.05),
     dict(seed=2**64 - 1),
+    # dense fronts: thousands of (voxel, block) pairs per 32-word chunk and
+    # half of the draws passing (the claim buffer flushes every iteration)
+    dict(cd=0.35, g_face=0.5, g_edge=0.5, g_corner=0.5, target_solid_fraction=0.97),
+    dict(cd=0.3, g_face=0.004, g_edge=0.004, g_corner=0.004, target_solid_fraction=0.97),  # 16 steps
+    dict(cd=0.12, g_face=1.0, g_edge=1.0, g_corner=1.0, target_solid_fraction=0.99, periodic=1),
 ])
 def test_edge_case_parity(oracle, Q, extra):
     p = dict(workloads.small_64(), nx=37, ny=29, nz=23)
