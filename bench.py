@@ -608,7 +608,7 @@ def main():
         Q.qsgs_set_grow_tile(h, shape["tile"])
         Q.qsgs_seed(h)
         rc, _ = Q.qsgs_grow_until(h, 0)
-        Q.qsgs_fetch(h, host.data_ptr(), n_vox, Q.QSGS_FMT_U8, False)
+        Q.qsgs_fetch(h, host.data_ptr(), n_vox, Q.QSGS_FMT_U8, Q.QSGS_DST_HOST_MAPPED)
         Q.qsgs_destroy(h)
         t1 = time.perf_counter()
         if k:

@@ -64,6 +64,14 @@ extern "C" {
                              of word (y + ny z) W + (x >> 5); bits at
                              x >= nx are 0                                   */
 
+/* ---- fetch destinations (the dst_is_device argument of qsgs_fetch) ----- */
+#define QSGS_DST_HOST 0        /* host memory of any kind                     */
+#define QSGS_DST_DEVICE 1      /* device memory                               */
+#define QSGS_DST_HOST_MAPPED 2 /* page-locked host memory mapped into the
+                                  device's address space over the whole
+                                  [dst, dst + bytes) (cudaHostAlloc, or
+                                  cudaHostRegister of the whole range)        */
+
 /* Generation parameters (the problem statement of Sec. 2.1 and Sec. 3.2).
  *   nx, ny, nz   grid dimensions, each >= 1, product < 2^32
  *   cd           seed (core) probability c_d in [0, 1]
@@ -180,11 +188,16 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out);
  *   bytes          its size: >= N for QSGS_FMT_U8, >= 4 nz ny W for
  *                  QSGS_FMT_PACKED
  *   fmt            QSGS_FMT_U8 or QSGS_FMT_PACKED
+ *   dst_is_device  QSGS_DST_HOST, QSGS_DST_DEVICE or QSGS_DST_HOST_MAPPED
  * Blocks until the copy is complete.  Returns QSGS_OK, QSGS_ERR_INVALID
- * (fmt or size), QSGS_ERR_STATE or QSGS_ERR_CUDA.  A U8 fetch to the host
- * stages through the candidate-list area of the workspace in slabs of its
- * size, so it is only allowed when the realization has finished (status !=
- * QSGS_RUNNING). */
+ * (fmt, size or destination kind), QSGS_ERR_STATE or QSGS_ERR_CUDA.  A U8
+ * fetch to QSGS_DST_HOST memory stages through the candidate-list area of
+ * the workspace in slabs of its size, so it is only allowed when the
+ * realization has finished (status != QSGS_RUNNING).  To
+ * QSGS_DST_HOST_MAPPED memory the device writes the uint8 map directly (no
+ * staging, allowed at any time); a dst that the CUDA runtime does not know
+ * as mapped host memory is served like QSGS_DST_HOST.  The caller
+ * guarantees that the mapping covers all of [dst, dst + bytes). */
 int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_device);
 
 /* Synchronises the handle's stream and fills *out.  Returns QSGS_OK,

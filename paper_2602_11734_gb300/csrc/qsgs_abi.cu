@@ -559,17 +559,30 @@ int qsgs_query(qsgs_handle* h, qsgs_stats* out) {
 int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_device) {
   if (!h || !dst) return QSGS_ERR_INVALID;
   if (!h->seeded) return QSGS_ERR_STATE;
+  if (dst_is_device != QSGS_DST_HOST && dst_is_device != QSGS_DST_DEVICE &&
+      dst_is_device != QSGS_DST_HOST_MAPPED)
+    return QSGS_ERR_INVALID;
   const size_t n = h->g.n, packed = (size_t)h->g.nwords * 4;
-  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const cudaMemcpyKind kind =
+      dst_is_device == QSGS_DST_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   cudaError_t e = cudaSuccess;
   if (fmt == QSGS_FMT_PACKED) {
     if (bytes < packed) return QSGS_ERR_INVALID;
     e = cudaMemcpyAsync(dst, h->grid, packed, kind, h->stream);
   } else if (fmt == QSGS_FMT_U8) {
     if (bytes < n) return QSGS_ERR_INVALID;
-    if (dst_is_device) {
-      e = launch_unpack_u8(h->g, h->grid, static_cast<uint8_t*>(dst), 0, n, h->stream,
-                           h->tracer);
+    // Mapped host memory: its device address, if the runtime knows it.
+    void* mapped = nullptr;
+    if (dst_is_device == QSGS_DST_HOST_MAPPED &&
+        cudaHostGetDevicePointer(&mapped, dst, 0) != cudaSuccess) {
+      mapped = nullptr;
+      (void)cudaGetLastError();  // not mapped host memory: staged below
+    }
+    if (dst_is_device == QSGS_DST_DEVICE || mapped) {
+      // Straight into device memory, or over the host link into mapped host
+      // memory (16-byte stores: no staging and no separate copy).
+      uint8_t* out = static_cast<uint8_t*>(dst_is_device == QSGS_DST_DEVICE ? dst : mapped);
+      e = launch_unpack_u8(h->g, h->grid, out, 0, n, h->stream, h->tracer);
     } else {
       RunState s{};
       const int rc = read_state(h, &s);

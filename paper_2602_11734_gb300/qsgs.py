@@ -24,6 +24,7 @@ QSGS_OK, QSGS_STALLED, QSGS_MAX_STEPS, QSGS_RUNNING = 0, 1, 2, 3
 QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_CUDA = -1, -2, -3
 QSGS_ERR_TIMEOUT, QSGS_ERR_STATE, QSGS_ERR_NOMEM = -4, -5, -6
 QSGS_FMT_U8, QSGS_FMT_PACKED = 0, 1
+QSGS_DST_HOST, QSGS_DST_DEVICE, QSGS_DST_HOST_MAPPED = 0, 1, 2
 QSGS_MODE_LIETS, QSGS_MODE_FULLFIELD = 0, 1
 
 PARAM_KEYS = ("nx", "ny", "nz", "cd", "g_face", "g_edge", "g_corner", "spacing_s",
@@ -186,7 +187,9 @@ def qsgs_grow_until(h, max_steps: int = 0) -> tuple[int, dict]:
     return rc, s.as_dict()
 
 
-def qsgs_fetch(h, dst_ptr: int, nbytes: int, fmt: int, dst_is_device: bool) -> None:
+def qsgs_fetch(h, dst_ptr: int, nbytes: int, fmt: int, dst_is_device: int) -> None:
+    """dst_is_device: QSGS_DST_HOST (or False), QSGS_DST_DEVICE (or True) or
+    QSGS_DST_HOST_MAPPED."""
     rc = load_library().qsgs_fetch(h, ctypes.c_void_p(dst_ptr), nbytes, fmt, int(dst_is_device))
     if rc != QSGS_OK:
         raise QsgsError(rc, "qsgs_fetch")
@@ -400,7 +403,8 @@ class Generator:
 
     def fetch(self, out=None, fmt: str = "u8"):
         """Phase map as a uint8 (nz, ny, nx) tensor, or the packed uint32
-        words (fmt='packed').  ``out`` may be a CUDA or CPU tensor."""
+        words (fmt='packed').  ``out`` may be a CUDA or CPU tensor; a pinned
+        CPU tensor is written by the device directly."""
         import torch
         f = QSGS_FMT_U8 if fmt == "u8" else QSGS_FMT_PACKED
         if out is None:
@@ -408,7 +412,9 @@ class Generator:
                 out = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
             else:
                 out = torch.empty(self.words, dtype=torch.int32, device=self.device)
-        qsgs_fetch(self.handle, out.data_ptr(), out.numel() * out.element_size(), f, out.is_cuda)
+        dst = (QSGS_DST_DEVICE if out.is_cuda else
+               QSGS_DST_HOST_MAPPED if out.is_pinned() else QSGS_DST_HOST)
+        qsgs_fetch(self.handle, out.data_ptr(), out.numel() * out.element_size(), f, dst)
         return out
 
     def set_profiling(self, enable: bool = True) -> None:

@@ -282,8 +282,8 @@ def test_autotuned_shape_keeps_results(oracle, Q, tmp_path, monkeypatch):
 
 
 def test_host_u8_fetch_in_slabs(oracle, Q):
-    # The host u8 fetch is staged through the candidate-list area, which is
-    # smaller than the grid in bytes: several slabs, ragged last one.
+    # A pageable host buffer is staged through the candidate-list area, which
+    # is smaller than the grid in bytes: several slabs, ragged last one.
     p = dict(workloads.small_64(), nx=77, ny=45, nz=61, cd=0.001, spacing_s=4, seed=23)
     assert Q.word_count(p) * 4 < p["nx"] * p["ny"] * p["nz"]
     want = oracle.run(p)
@@ -291,11 +291,37 @@ def test_host_u8_fetch_in_slabs(oracle, Q):
     try:
         g.seed()
         g.grow()
-        host = torch.empty(g.shape, dtype=torch.uint8, pin_memory=True)
+        host = torch.empty(g.shape, dtype=torch.uint8)
+        assert not host.is_pinned()
         g.fetch(out=host)
         dev = g.fetch()
         assert np.array_equal(host.numpy(), want.phase)
         assert torch.equal(dev.cpu(), host)
+    finally:
+        g.close()
+
+
+def test_host_u8_fetch_into_mapped_memory(oracle, Q):
+    # Pinned host memory is written by the device directly, mid-run too; the
+    # same flag on pageable memory falls back to the staged copy.
+    p = dict(workloads.small_64(), nx=77, ny=45, nz=61, cd=0.001, spacing_s=4, seed=29)
+    n = p["nx"] * p["ny"] * p["nz"]
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        g.grow(3)
+        mid = torch.full(g.shape, 7, dtype=torch.uint8, pin_memory=True)
+        g.fetch(out=mid)                                   # running: direct writes
+        assert torch.equal(mid, g.fetch().cpu())
+        g.grow()
+        host = torch.full(g.shape, 7, dtype=torch.uint8, pin_memory=True)
+        Q.qsgs_fetch(g.handle, host.data_ptr(), n, Q.QSGS_FMT_U8, Q.QSGS_DST_HOST_MAPPED)
+        assert np.array_equal(host.numpy(), oracle.run(p).phase)
+        pageable = torch.full(g.shape, 7, dtype=torch.uint8)
+        Q.qsgs_fetch(g.handle, pageable.data_ptr(), n, Q.QSGS_FMT_U8, Q.QSGS_DST_HOST_MAPPED)
+        assert torch.equal(pageable, host)
+        with pytest.raises(Q.QsgsError):
+            Q.qsgs_fetch(g.handle, host.data_ptr(), n, Q.QSGS_FMT_U8, 3)  # no such kind
     finally:
         g.close()
 
