@@ -39,7 +39,8 @@ class OqParams(ctypes.Structure):
                 ("spacing_s", ctypes.c_uint32), ("target_solid_fraction", ctypes.c_double),
                 ("target_count", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("max_steps", ctypes.c_uint32), ("periodic", ctypes.c_uint32),
-                ("blocked", ctypes.c_void_p)]
+                ("blocked", ctypes.c_void_p), ("inter", ctypes.c_void_p),
+                ("n_labels", ctypes.c_uint32)]
 
 
 class OqStepLog(ctypes.Structure):
@@ -105,9 +106,11 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def _params(p: dict, blocked=None) -> OqParams:
-    """Parameters; ``blocked`` (optional, N bytes, x fastest): cells of
-    earlier phases (R12).  The returned struct keeps the array alive."""
+def _params(p: dict, blocked=None, inter=None) -> OqParams:
+    """Parameters; ``blocked`` (optional, N bytes, x fastest): labels of
+    earlier phases, 0 = unassigned (R12); ``inter`` (optional, (n_labels, 3)):
+    interaction probabilities I^{n,m} per label m = 1.. and class (R13).
+    The returned struct keeps the arrays alive."""
     q = dict(DEFAULTS)
     unknown = set(p) - set(DEFAULTS)
     if unknown:
@@ -120,6 +123,11 @@ def _params(p: dict, blocked=None) -> OqParams:
             raise ValueError("blocked must hold one byte per voxel")
         P.blocked = arr.ctypes.data
         P._keep = arr
+    if inter is not None:
+        tab = np.ascontiguousarray(inter, dtype=np.float64).reshape(-1, 3)
+        P.inter = tab.ctypes.data
+        P.n_labels = tab.shape[0]
+        P._keep_inter = tab
     return P
 
 
@@ -159,8 +167,8 @@ def threshold(t_ref: int, nt: int, c: int) -> int:
     return int(lib().oq_threshold(t_ref, nt, c))
 
 
-def seed_candidates(p: dict, blocked=None) -> np.ndarray:
-    P = _params(p, blocked)
+def seed_candidates(p: dict, blocked=None, inter=None) -> np.ndarray:
+    P = _params(p, blocked, inter)
     n = lib().oq_seed_candidates(ctypes.byref(P), None, 0)
     out = np.zeros(max(n, 1), dtype=np.uint32)
     lib().oq_seed_candidates(ctypes.byref(P), _ptr(out, ctypes.c_uint32), n)
@@ -177,10 +185,10 @@ def spacing(p: dict, cand: np.ndarray) -> np.ndarray:
     return acc[:len(c)].astype(bool)
 
 
-def front(p: dict, phase: np.ndarray, blocked=None) -> np.ndarray:
+def front(p: dict, phase: np.ndarray, blocked=None, inter=None) -> np.ndarray:
     ph = np.ascontiguousarray(phase, dtype=np.uint8).reshape(-1)
     out = np.zeros(max(ph.size, 1), dtype=np.uint32)
-    P = _params(p, blocked)
+    P = _params(p, blocked, inter)
     n = lib().oq_front(ctypes.byref(P), _ptr(ph, ctypes.c_uint8), _ptr(out, ctypes.c_uint32))
     return out[:n]
 
@@ -210,10 +218,11 @@ def _result(P: OqParams, phase: np.ndarray, s: OqSummary, log) -> Result:
                   status=s.status, log=log)
 
 
-def run(p: dict, log_cap: int = 100000, blocked=None) -> Result:
+def run(p: dict, log_cap: int = 100000, blocked=None, inter=None) -> Result:
     """One realization by Algorithm 3 (list-indexed growth); ``blocked``:
-    cells of earlier phases (R12)."""
-    P = _params(p, blocked)
+    labels of earlier phases (R12); ``inter``: their interaction
+    probabilities (R13)."""
+    P = _params(p, blocked, inter)
     n = P.nx * P.ny * P.nz
     phase = np.zeros(n, dtype=np.uint8)
     log = np.zeros(log_cap, dtype=_LOG_DTYPE)
@@ -225,9 +234,9 @@ def run(p: dict, log_cap: int = 100000, blocked=None) -> Result:
     return _result(P, phase, s, log[:min(s.steps, log_cap)])
 
 
-def run_fullfield(p: dict, blocked=None) -> Result:
+def run_fullfield(p: dict, blocked=None, inter=None) -> Result:
     """The same realization by the full-field sweep of Algorithm 2."""
-    P = _params(p, blocked)
+    P = _params(p, blocked, inter)
     n = P.nx * P.ny * P.nz
     phase = np.zeros(n, dtype=np.uint8)
     s = OqSummary()
@@ -237,17 +246,27 @@ def run_fullfield(p: dict, blocked=None) -> Result:
     return _result(P, phase, s, None)
 
 
-def run_phases(phases: list) -> tuple:
-    """Sec. 2.1 steps 4-5 with independent discrete phases (R12): phase k
-    (k = 1, 2, ...) is generated on the cells no earlier phase holds; the
-    label map has k on its cells and 0 on the matrix.  Returns (labels
-    (nz, ny, nx) uint8, [Result of every phase])."""
+def run_phases(phases: list, interactions=None) -> tuple:
+    """Sec. 2.1 steps 4-5: phase k (k = 1, 2, ...) is generated on the cells
+    no earlier phase holds (R12) -- or, when interactions[k - 1] is a dict
+    {m: (I_face, I_edge, I_corner)}, also enters cells of the earlier phases
+    m listed there (R13), which become phase k's.  The label map has k on
+    phase k's cells and 0 on the matrix.  Returns (labels (nz, ny, nx)
+    uint8, [Result of every phase])."""
     p0 = dict(DEFAULTS, **phases[0])
     shape = (p0["nz"], p0["ny"], p0["nx"])
     labels = np.zeros(shape, dtype=np.uint8)
     results = []
     for k, p in enumerate(phases, start=1):
-        r = run(p, blocked=labels != 0)
+        spec = interactions[k - 1] if interactions else None
+        inter = None
+        if spec:
+            inter = np.zeros((k - 1, 3))
+            for m, probs in spec.items():
+                if not 1 <= m < k:
+                    raise ValueError(f"phase {k} can only enter earlier phases, not {m}")
+                inter[m - 1] = probs
+        r = run(p, blocked=labels, inter=inter)
         labels[r.phase.astype(bool)] = k
         results.append(r)
     return labels, results

@@ -33,7 +33,18 @@
  *       cells of earlier phases (blocked) are never seeds, never void
  *       targets and never count as void neighbours; seeding, spacing, Eq. 1
  *       (phi_a = c/N over the whole domain) and the trim are otherwise those
- *       of the first phase.  Phase-interaction probabilities are not read.
+ *       of the first phase.
+ *   R13 Interacting phases (Sec. 2.1 step 4, second case): the phase being
+ *       generated (n) grows into a neighbour that belongs to an earlier
+ *       phase m with the interaction probability I^{n,m} of the direction's
+ *       class, a constant (Eq. 1 scales the growth probabilities G only);
+ *       a cell so entered becomes phase n's and counts towards its target,
+ *       and the draw of such an attempt is the same keyed word as for a
+ *       void target.  Unassigned cells are grown into with the Eq. 1
+ *       probabilities as before.  A voxel of phase n is active (front) if
+ *       it has a void neighbour or a neighbour of a phase m with a positive
+ *       I^{n,m} for that direction's class.  Seeds are only placed on
+ *       unassigned cells.  With every I = 0 this is R12.
  *   R11 Periodic option (the roll of Sec. 2.2 and Algorithm 2): with
  *       periodic = 1 the domain is a torus -- neighbours and the spacing
  *       distance wrap around every axis -- and every dimension must be at
@@ -48,9 +59,10 @@
  *   R9  Nt = target_count if given, else floor(phi_s N + 0.5) in IEEE double.
  *   R10 Exits, tested in this order before every step: c >= Nt (done);
  *       t >= max_steps (step limit); no (source, direction) pair with a void
- *       in-domain target and a positive threshold (stalled -- the grid can
- *       never change again; an empty front is the special case).  A stalled
- *       step is not counted.
+ *       in-domain target (or, R13, an enterable cell of an earlier phase)
+ *       and a positive threshold (stalled -- the grid can never change
+ *       again; an empty front is the special case).  A stalled step is not
+ *       counted.
  */
 #include "qsgs_oracle.h"
 
@@ -107,6 +119,16 @@ static uint64_t grid_size(const oq_params* p) {
 
 /* A cell of an earlier phase (R12). */
 static int blocked(const oq_params* p, uint64_t v) { return p->blocked && p->blocked[v]; }
+
+/* R13: threshold floor(I^{n,m} 2^32) of entering the cell v of an earlier
+ * phase m along a direction of class k; 0 when phase m is not entered. */
+static uint64_t inter_threshold(const oq_params* p, uint64_t v, int k) {
+  const uint32_t m = p->blocked ? p->blocked[v] : 0u;
+  if (m == 0 || !p->inter || m > p->n_labels) return 0;
+  const double prob = p->inter[3 * (m - 1) + (uint32_t)k];
+  if (!(prob > 0.0)) return 0;
+  return (uint64_t)floor((prob < 1.0 ? prob : 1.0) * 4294967296.0);
+}
 
 /* R2 / R9: integer forms of the parameters. */
 int oq_targets(const oq_params* p, uint64_t* nt, uint64_t* t_seed, uint64_t t_ref[3]) {
@@ -227,14 +249,16 @@ static int neighbour(const oq_params* p, uint64_t v, int dx, int dy, int dz, uin
 }
 
 /* "Solid cells which have at least one neighboring void cell" (Sec. 2.3
- * step 2), over the same 26 directions as growth. */
+ * step 2), over the same 26 directions as growth; with interacting phases
+ * (R13) a neighbour of a phase that may be entered along that direction
+ * counts as well. */
 static int has_void_neighbour(const oq_params* p, const uint8_t* phase, uint64_t v,
-                              const int32_t dirs[78]) {
+                              const int32_t dirs[78], const int32_t cls[26]) {
   for (int d = 0; d < 26; ++d) {
     uint64_t q;
-    if (neighbour(p, v, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) && phase[q] == 0 &&
-        !blocked(p, q))
-      return 1;
+    if (!neighbour(p, v, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) || phase[q] != 0)
+      continue;
+    if (!blocked(p, q) || inter_threshold(p, q, cls[d]) > 0) return 1;
   }
   return 0;
 }
@@ -244,7 +268,7 @@ uint64_t oq_front(const oq_params* p, const uint8_t* phase, uint32_t* out) {
   oq_directions(dirs, cls);
   uint64_t n = grid_size(p), k = 0;
   for (uint64_t v = 0; v < n; ++v)
-    if (phase[v] && has_void_neighbour(p, phase, v, dirs)) out[k++] = (uint32_t)v;
+    if (phase[v] && has_void_neighbour(p, phase, v, dirs, cls)) out[k++] = (uint32_t)v;
   return k;
 }
 
@@ -314,17 +338,19 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
     for (int d = 0; d < 26; ++d) {   /* every direction of every front voxel */
       for (uint64_t i = 0; i < a_n; ++i) {
         uint64_t a = A[i], q;
-        /* neighbours inside the domain that are still void */
+        /* neighbours inside the domain that are still void -- or, with
+         * interacting phases (R13), cells of an earlier phase */
         if (!neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q)) continue;
-        if (phase[q] != 0 || blocked(p, q)) continue;
-        if (thr[cls[d]] == 0) continue; /* this attempt cannot succeed */
+        if (phase[q] != 0) continue;
+        const uint64_t th = blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]];
+        if (th == 0) continue; /* this attempt cannot succeed */
         ++live;
         /* an independent draw for this (source, step, direction) */
         uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
         uint32_t r[4];
         oq_philox4x32_10(ctr, key, r);
-        if ((uint64_t)r[d & 3] < thr[cls[d]]) {
-          phase[q] = 1;  /* the void becomes solid ... */
+        if ((uint64_t)r[d & 3] < th) {
+          phase[q] = 1;  /* the void (or entered cell) becomes solid ... */
           A_new[new_n++] = (uint32_t)q;  /* ... and joins A_new */
         }
       }
@@ -354,7 +380,7 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
       uint32_t v;
       if (j >= new_n || (i < a_n && A[i] < A_new[j])) v = A[i++];
       else v = A_new[j++];
-      if (has_void_neighbour(p, phase, v, dirs)) merged[m++] = v;
+      if (has_void_neighbour(p, phase, v, dirs, cls)) merged[m++] = v;
     }
     uint32_t* tmp = A; A = merged; merged = tmp;
     a_n = m;
@@ -408,14 +434,17 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
       for (uint64_t a = 0; a < n; ++a) {
         if (!solid_mask[a]) continue;
         uint64_t q;
-        int void_q = neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) &&
-                     !solid_mask[q] && !blocked(p, q);
-        if (void_q && thr[cls[d]] > 0) ++live;
+        /* a target: void, or (R13) a cell of an earlier phase */
+        int target = neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) &&
+                     !solid_mask[q];
+        const uint64_t th =
+            !target ? 0 : (blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]]);
+        if (th > 0) ++live;
         uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
         uint32_t r[4];
         oq_philox4x32_10(ctr, key, r);
-        if ((uint64_t)r[d & 3] >= thr[cls[d]]) continue;
-        if (void_q) grown[q] = 1;
+        if ((uint64_t)r[d & 3] >= th) continue;
+        grown[q] = 1;
       }
     }
     if (live == 0) { status = OQ_STALLED; break; }
@@ -431,7 +460,7 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
   }
   uint64_t front = 0;
   for (uint64_t v = 0; v < n; ++v)
-    if (phase[v] && has_void_neighbour(p, phase, v, dirs)) ++front;
+    if (phase[v] && has_void_neighbour(p, phase, v, dirs, cls)) ++front;
   out->solid_count = c;
   out->target_count = nt;
   out->front_size = front;

@@ -38,7 +38,14 @@ typedef struct {
   uint64_t seed;                /* RNG key                                  */
   uint32_t max_steps;           /* 0 = unlimited                            */
   uint32_t periodic;            /* 1: periodic domain (R11), each dim >= 3  */
-  const uint8_t* blocked;       /* cells of earlier phases (R12); NULL: none */
+  const uint8_t* blocked;       /* labels of earlier phases (R12): 0 = still
+                                   unassigned, m >= 1 = cell of phase m;
+                                   NULL: none                                */
+  const double* inter;          /* R13: inter[3 (m - 1) + k] = interaction
+                                   probability I^{n,m} of class k (face,
+                                   edge, corner) for m = 1 .. n_labels; NULL
+                                   or 0: phase m's cells are never entered  */
+  uint32_t n_labels;            /* entries (labels) of inter                */
 } oq_params;
 
 typedef struct {

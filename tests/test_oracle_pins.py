@@ -755,3 +755,149 @@ def test_blocked_list_indexed_equals_full_field(oracle):
             assert np.array_equal(a.phase, b.phase)
             assert (a.solid_count, a.steps, a.status, a.front_size) == \
                    (b.solid_count, b.steps, b.status, b.front_size)
+
+
+# --------------------------------------------------------------------------
+# Interacting phases (R13): the phase grows into cells of earlier phases
+# with the interaction probability of the direction's class
+# --------------------------------------------------------------------------
+def _labels(rng, shape, n_labels, frac):
+    """Random labels 1..n_labels on about `frac` of the cells, 0 elsewhere."""
+    lab = rng.integers(1, n_labels + 1, size=shape).astype(np.uint8)
+    lab[rng.random(shape) >= frac] = 0
+    return lab
+
+
+def test_interaction_zero_is_the_independent_phase(oracle):
+    rng = np.random.default_rng(61)
+    for periodic in (0, 1):
+        for _ in range(8):
+            p = _random_case(rng, periodic)
+            lab = _labels(rng, (p["nz"], p["ny"], p["nx"]), 2, 0.3)
+            a = oracle.run(p, blocked=lab)
+            b = oracle.run(p, blocked=lab, inter=np.zeros((2, 3)))
+            assert np.array_equal(a.phase, b.phase)
+            assert (a.solid_count, a.steps, a.status, a.front_size) == \
+                   (b.solid_count, b.steps, b.status, b.front_size)
+
+
+def test_interaction_list_indexed_equals_full_field(oracle):
+    rng = np.random.default_rng(62)
+    for periodic in (0, 1):
+        for _ in range(10):
+            p = _random_case(rng, periodic)
+            lab = _labels(rng, (p["nz"], p["ny"], p["nx"]), 3, 0.4)
+            inter = rng.uniform(0.0, 0.6, size=(3, 3)) * (rng.random((3, 3)) < 0.7)
+            a = oracle.run(p, blocked=lab, inter=inter)
+            b = oracle.run_fullfield(p, blocked=lab, inter=inter)
+            assert np.array_equal(a.phase, b.phase)
+            assert (a.solid_count, a.steps, a.status, a.front_size) == \
+                   (b.solid_count, b.steps, b.status, b.front_size)
+
+
+def test_interaction_unit_probability_is_a_geodesic_dilation(oracle):
+    # G = 0 and I = 1 towards label 1 only: the phase never grows into void
+    # cells, and after k steps it is its seeds dilated k times (26-neighbour
+    # steps) through the cells of label 1; label-2 cells stay blocked.
+    rng = np.random.default_rng(63)
+    checked = 0
+    for trial in range(14):
+        nx, ny, nz = (int(v) for v in rng.integers(5, 13, size=3))
+        n = nx * ny * nz
+        k = int(rng.integers(1, 4))
+        lab = _labels(rng, (nz, ny, nx), 2, 0.7)
+        p = dict(nx=nx, ny=ny, nz=nz, cd=0.04, target_count=n, seed=trial, max_steps=k)
+        cand = oracle.seed_candidates(p, blocked=lab)
+        if cand.size == 0:
+            continue
+        want = np.zeros(n, bool)
+        want[cand] = True
+        want = want.reshape(nz, ny, nx)
+        for _ in range(k):
+            want |= ndimage.binary_dilation(want, structure=np.ones((3, 3, 3), bool)) & (lab == 1)
+        r = oracle.run(p, blocked=lab, inter=np.array([[1.0, 1.0, 1.0], [0.0, 0.0, 0.0]]))
+        assert np.array_equal(r.phase.astype(bool), want), trial
+        assert not (r.phase.astype(bool) & (lab == 2)).any()
+        checked += 1
+    assert checked >= 6
+
+
+def test_interaction_front_matches_bruteforce(oracle):
+    # Active: a neighbour that is void, or of a label whose I is positive for
+    # that direction's class.
+    rng = np.random.default_rng(64)
+    dirs, dcls = oracle.directions()
+    for _ in range(20):
+        nx, ny, nz = (int(v) for v in rng.integers(3, 11, size=3))
+        lab = _labels(rng, (nz, ny, nx), 2, 0.4)
+        inter = np.array([[0.5, 0.0, 0.0], [0.0, 0.0, 0.3]])   # label 1: faces, label 2: corners
+        phase = (rng.random((nz, ny, nx)) < 0.5) & (lab == 0)
+        ok = np.zeros((nz, ny, nx), bool)
+        for (dx, dy, dz), c in zip(dirs, dcls):
+            growable = (~phase & (lab == 0)) | (~phase & (lab >= 1) & (inter[np.maximum(lab, 1) - 1, c] > 0))
+            pad = np.pad(growable, 1, constant_values=False)
+            ok |= pad[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        got = oracle.front(dict(nx=nx, ny=ny, nz=nz, target_solid_fraction=0.5),
+                           phase.astype(np.uint8), blocked=lab, inter=inter)
+        assert np.array_equal(got, np.flatnonzero(phase & ok))
+
+
+@pytest.mark.parametrize("cls", [0, 2])
+def test_interaction_first_step_rate(oracle, cls):
+    # Seeds on a slab of void cells facing a label-1 slab, G = 0: the step-0
+    # entries into the label-1 slab are Bernoulli trials with p = floor(I 2^32) / 2^32
+    # for the directions of one class (no Eq. 1 factor).
+    prob = 0.15
+    inter = np.zeros((1, 3))
+    inter[0, cls] = prob
+    dirs, dcls = oracle.directions()
+    hits = trials = 0
+    for seed in range(60):
+        nx = ny = 16
+        nz = 4
+        lab = np.zeros((nz, ny, nx), np.uint8)
+        lab[2:] = 1                                    # z >= 2: phase 1
+        p = dict(nx=nx, ny=ny, nz=nz, cd=0.03, spacing_s=4, target_count=nx * ny * nz,
+                 seed=seed, max_steps=1)
+        seeds = np.zeros(nx * ny * nz, bool)
+        seeds[oracle.seed_candidates(p, blocked=lab)] = True
+        seeds = seeds.reshape(nz, ny, nx)
+        r = oracle.run(p, blocked=lab, inter=inter)
+        grown = r.phase.astype(bool) & (lab == 1)
+        # attempts: (seed, direction of the class) pairs that land in the slab
+        # with distinct targets -- spacing 4 keeps the targets of different
+        # seeds apart for faces and corners
+        s_idx = np.argwhere(seeds)
+        placed = r.phase.astype(bool) & (lab == 0)
+        s_idx = [t for t in s_idx if placed[tuple(t)]]
+        for z, y, x in s_idx:
+            for (dx, dy, dz), c in zip(dirs, dcls):
+                zz, yy, xx = z + dz, y + dy, x + dx
+                if c == cls and 0 <= xx < nx and 0 <= yy < ny and 0 <= zz < nz and lab[zz, yy, xx] == 1:
+                    trials += 1
+        hits += int(grown.sum())
+    p_exact = np.floor(prob * 2**32) / 2**32
+    z = (hits - trials * p_exact) / np.sqrt(trials * p_exact * (1 - p_exact))
+    assert trials > 100 and abs(z) < 5, (hits, trials)
+
+
+def test_interacting_phases_partition_and_reach_their_targets(oracle):
+    rng = np.random.default_rng(65)
+    for periodic in (0, 1):
+        for _ in range(5):
+            p1 = _random_case(rng, periodic)
+            dims = {k: p1[k] for k in ("nx", "ny", "nz")}
+            p2 = dict(_random_case(rng, periodic), **dims, target_solid_fraction=0.3)
+            p3 = dict(_random_case(rng, periodic), **dims, target_solid_fraction=0.15)
+            spec = [None, {1: (0.4, 0.2, 0.1)}, {1: (0.2, 0.0, 0.0), 2: (0.0, 0.3, 0.3)}]
+            labels, rs = oracle.run_phases([p1, p2, p3], spec)
+            indep, _ = oracle.run_phases([p1, p2, p3])
+            # the last phase's cells are exactly its own realization
+            assert np.array_equal(labels == 3, rs[2].phase.reshape(labels.shape).astype(bool))
+            for k, r in enumerate(rs, start=1):
+                if r.status == oracle.DONE:
+                    assert r.solid_count == r.target_count
+            # entering earlier phases only takes cells from them
+            assert int((labels == 1).sum()) <= rs[0].solid_count
+            assert np.array_equal(indep == 1, rs[0].phase.reshape(labels.shape).astype(bool))
+            assert not ((labels == 1) & (indep != 1)).any()
