@@ -274,6 +274,34 @@ int qsgs_set_spin_limit(qsgs_handle* h, uint32_t polls);
  * QSGS_ERR_INVALID. */
 int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked);
 
+/* Interacting growing phases (Sec. 2.1 step 4, second case; reading R13):
+ * the phase grows into cells of earlier phases as well.
+ *   dev_labels  device, read only, owned by the caller: one byte per voxel
+ *               (x fastest), 0 = unassigned, m = a cell of earlier phase m;
+ *               NULL clears the interaction (and the blocked cells).  It must
+ *               stay valid and unchanged from qsgs_seed to the last fetch.
+ *   probs       host: probs[3 (m - 1) + k] = the interaction probability
+ *               I^{n,m} in [0, 1] of class k (face, edge, corner) for the
+ *               labels m = 1 .. n_labels; read during the call only
+ *   n_labels    0 .. 255
+ *   dev_scratch device, owned by the caller, qsgs_interaction_bytes(params)
+ *               bytes, 16-byte aligned: packed grids and thresholds the
+ *               handle derives from the labels; valid as long as dev_labels
+ * A move along class k from a voxel of this phase into a cell of phase m
+ * succeeds with probability floor(I^{n,m}_k 2^32) / 2^32 (a constant: Eq. 1
+ * scales the growth probabilities only); the cell becomes this phase's and
+ * counts towards its target.  Voids are entered as in an independent phase;
+ * seeds only fall on unassigned cells; a voxel with a void or an enterable
+ * neighbour is active.  With all I = 0 this is qsgs_set_blocked of the
+ * labelled cells.  Set it before qsgs_seed.  Single realizations in
+ * QSGS_MODE_LIETS only: batches reject such members and qsgs_set_mode
+ * rejects QSGS_MODE_FULLFIELD while it is set.  Returns QSGS_OK,
+ * QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE (scratch too small), QSGS_ERR_STATE
+ * (full-field mode) or QSGS_ERR_CUDA. */
+size_t qsgs_interaction_bytes(const qsgs_params* params);
+int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double* probs,
+                         uint32_t n_labels, void* dev_scratch, size_t scratch_bytes);
+
 /* Phase-map composition: writes `label` into dev_dst[v] (device uint8 map
  * of N bytes, x fastest) for every solid voxel v of this realization and
  * leaves the other bytes unchanged.  Blocks.  Returns QSGS_OK,

@@ -161,6 +161,8 @@ struct qsgs_handle {
   bool list_stale;
   // The exact-target epilogue has run since the run ended (batch members).
   bool finalized;
+  // Interacting phase (R13): the label thresholds copied to the scratch.
+  std::vector<uint32_t> enter_thr;
 };
 
 namespace {
@@ -723,7 +725,7 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   uint32_t open_only = 1;
   for (uint32_t m = 0; m < n; ++m) {
     qsgs_handle* h = members[m];
-    if (!h) return QSGS_ERR_INVALID;
+    if (!h || h->g.enter) return QSGS_ERR_INVALID;  // interacting phases: single path only
     if (h->g.periodic || h->g.blocked) open_only = 0;
     MemberDesc& d = descs[m];
     std::memset(&d, 0, sizeof(d));
@@ -893,6 +895,9 @@ int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked) {
   if (!h) return QSGS_ERR_INVALID;
   if (dev_blocked && (reinterpret_cast<uintptr_t>(dev_blocked) % 4)) return QSGS_ERR_INVALID;
   h->g.blocked = static_cast<const uint32_t*>(dev_blocked);
+  h->g.enter = nullptr;  // an independent phase: no interaction
+  h->g.labels = nullptr;
+  h->g.enter_thr = nullptr;
   destroy_graph(h);  // the geometry (with the pointer) is baked into the graph
   h->graph_tried = false;
   return QSGS_OK;
@@ -920,8 +925,71 @@ int qsgs_fetch_or(qsgs_handle* h, void* dev_dst, size_t bytes) {
   return e == cudaSuccess ? QSGS_OK : cuda_fail(h, e);
 }
 
+size_t qsgs_interaction_bytes(const qsgs_params* p) {
+  Ints ints;
+  if (check_params(p, &ints) != QSGS_OK) return 0;
+  const uint64_t W = (p->nx + 31) / 32;
+  const uint64_t nwords = W * p->ny * p->nz;
+  return (size_t)(4 * nwords * 4 + 256 * 3 * 4);
+}
+
+int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double* probs,
+                         uint32_t n_labels, void* dev_scratch, size_t scratch_bytes) {
+  if (!h) return QSGS_ERR_INVALID;
+  if (!dev_labels) {  // back to an independent first phase
+    h->g.blocked = nullptr;
+    h->g.enter = nullptr;
+    h->g.labels = nullptr;
+    h->g.enter_thr = nullptr;
+    destroy_graph(h);
+    h->graph_tried = false;
+    return QSGS_OK;
+  }
+  if (n_labels > 255 || (n_labels && !probs) || !dev_scratch ||
+      (reinterpret_cast<uintptr_t>(dev_scratch) % 16))
+    return QSGS_ERR_INVALID;
+  if (h->mode != QSGS_MODE_LIETS) return QSGS_ERR_STATE;
+  for (uint32_t i = 0; i < 3 * n_labels; ++i)
+    if (!(probs[i] >= 0.0 && probs[i] <= 1.0)) return QSGS_ERR_INVALID;
+  const size_t nwords = h->g.nwords;
+  if (scratch_bytes < 4 * nwords * 4 + 256 * 3 * 4) return QSGS_ERR_WORKSPACE;
+  // Thresholds floor(I 2^32) - 1 per label and class (row 0: unassigned,
+  // unused); sets of the labels each class may enter; the largest per class.
+  h->enter_thr.assign(256 * 3, 0u);
+  uint32_t sets[3][8] = {};
+  for (uint32_t k = 0; k < 3; ++k) h->g.enter_max[k] = 0;
+  for (uint32_t m = 1; m <= n_labels; ++m)
+    for (uint32_t k = 0; k < 3; ++k) {
+      const double pr = probs[3 * (m - 1) + k];
+      const uint64_t T = (uint64_t)std::floor(pr * 4294967296.0);
+      if (T == 0) continue;
+      const uint32_t t1 = (uint32_t)(T - 1);
+      h->enter_thr[m * 3 + k] = t1;
+      sets[k][m >> 5] |= 1u << (m & 31u);
+      if (t1 > h->g.enter_max[k]) h->g.enter_max[k] = t1;
+    }
+  uint32_t* blocked = static_cast<uint32_t*>(dev_scratch);
+  uint32_t* enter = blocked + nwords;
+  uint32_t* thr = enter + 3 * nwords;
+  Geom g = h->g;
+  cudaError_t e = cudaMemcpyAsync(thr, h->enter_thr.data(), 256 * 3 * 4, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = launch_pack_labels(g, dev_labels, blocked, enter, sets, h->stream,
+                                               h->tracer);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->g.blocked = blocked;
+  h->g.enter = enter;
+  h->g.labels = dev_labels;
+  h->g.enter_thr = thr;
+  destroy_graph(h);  // the geometry (with the pointers) is baked into the graph
+  h->graph_tried = false;
+  return QSGS_OK;
+}
+
 int qsgs_set_mode(qsgs_handle* h, int mode) {
   if (!h || (mode != QSGS_MODE_LIETS && mode != QSGS_MODE_FULLFIELD)) return QSGS_ERR_INVALID;
+  if (mode == QSGS_MODE_FULLFIELD && h->g.enter) return QSGS_ERR_STATE;
   if (mode != h->mode) {
     h->mode = mode;
     destroy_graph(h);  // the step kernel is baked into the graph

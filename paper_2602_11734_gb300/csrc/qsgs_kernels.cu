@@ -354,18 +354,20 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
 // each neighbour row arrives in one coalesced load and the x-1 / x+1 bits
 // come from the neighbouring lanes.
 // Domain kind of a growth-path instantiation: the open domain (R6), the
-// torus (R11), or read from Geom at run time (batches mix both).
-enum DomainKind : int { kOpen = 0, kTorus = 1, kRuntime = 2 };
+// torus (R11), read from Geom at run time (batches mix both), or a phase
+// that enters cells of earlier phases (R13; periodic read at run time).
+enum DomainKind : int { kOpen = 0, kTorus = 1, kRuntime = 2, kInteract = 3 };
 
 template <int DK>
 __device__ __forceinline__ bool on_torus(const Geom& g) {
-  return DK == kRuntime ? g.periodic != 0u : DK == kTorus;
+  return (DK == kRuntime || DK == kInteract) ? g.periodic != 0u : DK == kTorus;
 }
 
-// Cells of earlier phases (R12) are only looked at by the run-time kind.
+// Cells of earlier phases (R12) are only looked at by the run-time and
+// interacting kinds.
 template <int DK>
 __device__ __forceinline__ bool has_blocked(const Geom& g) {
-  return DK == kRuntime && g.blocked != nullptr;
+  return DK == kInteract || (DK == kRuntime && g.blocked != nullptr);
 }
 
 template <int DK>
@@ -384,6 +386,11 @@ struct FrontCountPolicy {
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w, bool valid) const {
+    if (g.enter) {  // interacting phase: enterable neighbours count too (R13)
+      uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
+      if (valid) word_masks<kInteract>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
+      return Item{w, front, 0u};
+    }
     if (g.periodic || g.blocked) {  // the growth kernel's own neighbour masks
       uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
       if (valid) word_masks<kRuntime>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
@@ -930,10 +937,28 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
     yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
     zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
   }
+  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
+  constexpr int cls_x = dir_cls(dm);                   // class of the x-1 / x+1 directions
+  constexpr int cls_0 = d0 >= 0 ? dir_cls(d0) : 0;     // class of the centre direction
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
+  // Interacting phase (R13): enterable cells of earlier phases -- in the
+  // grid of the direction's class and not yet this phase's -- per class used
+  // by this row (x +-1: ex*, centre: e0*); outside the domain: none.
+  uint32_t exc = 0, exl = 0, exr = 0, e0c = 0;
   if (kInterior || (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz)) {
     const size_t ro = (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
     row_words<DK>(g, grid + ro, xw, c, l, rr);
+    if (DK == kInteract) {
+      uint32_t a, b, e;
+      row_words<DK>(g, g.enter + (size_t)cls_x * g.nwords + ro, xw, a, b, e);
+      exc = a & ~c;
+      exl = b & ~l;
+      exr = e & ~rr;
+      if (d0 >= 0) {
+        row_words<DK>(g, g.enter + (size_t)cls_0 * g.nwords + ro, xw, a, b, e);
+        e0c = a & ~c;
+      }
+    }
     if (has_blocked<DK>(g)) {  // cells of earlier phases are not void either
       uint32_t bc, bl, br;
       row_words<DK>(g, g.blocked + ro, xw, bc, bl, br);
@@ -944,19 +969,23 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
   }
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
   const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
-  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
-  front |= vm | vp;
-  V[dm] = vm & live[dir_cls(dm)];
+  // Enterable targets (R13) need no live class: their grid holds only
+  // labels with a positive interaction probability for that class.
+  const uint32_t em = DK == kInteract ? ((exc << 1) | (exl >> 31)) & self : 0u;
+  const uint32_t ep = DK == kInteract ? ((exc >> 1) | (exr << 31)) & self : 0u;
+  front |= vm | vp | em | ep;
+  V[dm] = (vm & live[cls_x]) | em;
   Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
     const uint32_t v0 = ~c & self;
-    front |= v0;
-    V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
+    const uint32_t e0 = DK == kInteract ? e0c & self : 0u;
+    front |= v0 | e0;
+    V[d] = (v0 & live[cls_0]) | e0;
     Bm[(d >> 2) % 7] |= V[d];
   }
-  V[dp] = vp & live[dir_cls(dp)];
+  V[dp] = (vp & live[cls_x]) | ep;
   Bm[dp >> 2] |= V[dp];
 }
 
@@ -969,12 +998,17 @@ struct GrowCounters {
 // (classes with T > 0).  Written by lanes 0..27 of a warp or block.
 // kComplement stores ~(T - 1) instead: r + ~(T - 1) carries out of 32 bits
 // exactly when r > T - 1, which fail_bits below reads off the carry flag.
+// enter_max (interacting phases, R13): per class the largest threshold of
+// entering an earlier phase's cell; the draw loop then tests against the
+// larger of the two and the claims apply the target's own threshold.
 template <bool kComplement = false>
-__device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr) {
+__device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr,
+                                                const uint32_t* enter_max = nullptr) {
   if (lane < 28) {
     const int d = (int)lane;
     const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
-    const uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+    uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+    if (enter_max && d < 26) t1 = max(t1, enter_max[dir_cls(d)]);
     reinterpret_cast<uint32_t*>(thr)[d] = kComplement ? ~t1 : t1;
   }
 }
@@ -1029,6 +1063,44 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
       claim_target<DK>(g, wo, i, (int)(4u * b + j), wq, bit);
       // Fire-and-forget: the claim grid collects New_t; nobody waits.
       atomicOr(claims + wq, bit);
+    }
+  }
+}
+
+// Claims of an interacting phase (R13).  The draw loop tested a block's
+// words against the larger of the Eq. 1 and the largest interaction
+// threshold of their class, so the block is drawn again here (a few per
+// cent of the pairs) and each candidate direction is tested against its own
+// target's threshold: Eq. 1 for a void cell, I^{n,m} for a cell of phase m.
+template <int DK>
+__device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims,
+                                                 const GrowWarpSmem& S, uint32_t nwin,
+                                                 uint32_t lane, uint32_t t,
+                                                 const PhiloxKeys& keys, const RunState* st) {
+  for (uint32_t k = lane; k < nwin; k += 32) {
+    const uint32_t x = S.win[k];
+    const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
+    const uint4 vm = S.V[owner][b];
+    uint32_t win = (x >> 16) & (((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
+                                (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3));
+    if (!win) continue;
+    const uint32_t wo = S.w[owner];
+    const uint32_t ro = fast_div(wo, g.div_W);
+    const uint32_t v = ro * g.nx + (wo - ro * g.W) * 32u + i;
+    const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
+    while (win) {
+      const uint32_t j = __ffs(win) - 1;
+      win &= win - 1;
+      const int d = (int)(4u * b + j);
+      uint32_t wq, bit;
+      claim_target<DK>(g, wo, i, d, wq, bit);
+      const uint32_t rq = fast_div(wq, g.div_W);
+      const uint32_t q = rq * g.nx + (wq - rq * g.W) * 32u + (uint32_t)(__ffs(bit) - 1);
+      const uint32_t lab = g.labels[q];
+      const unsigned long long T = st->thr[dir_cls(d)];
+      const uint32_t th = lab ? g.enter_thr[lab * 3u + (uint32_t)dir_cls(d)]
+                              : (T ? (uint32_t)(T - 1) : 0u);
+      if (u4_word(rnd, (int)j) <= th) atomicOr(claims + wq, bit);
     }
   }
 }
@@ -1123,7 +1195,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
                                            uint32_t w, uint32_t t, uint32_t live_dirs,
                                            const uint4* nthr,
                                            const PhiloxKeys& keys, GrowWarpSmem& S,
-                                           GrowCounters& cnt) {
+                                           GrowCounters& cnt, const RunState* st) {
   const uint32_t lane = threadIdx.x & 31;
   // Phase 1: masks of this lane's word.
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -1226,7 +1298,10 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     nwin += __popc(balb);
     if (nwin > (uint32_t)kGrowWins - 64u) {
       __syncwarp();
-      claim_wins<DK>(g, claims, S, nwin, lane);
+      if constexpr (DK == kInteract)
+        claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, st);
+      else
+        claim_wins<DK>(g, claims, S, nwin, lane);
       __syncwarp();
       nwin = 0;
     }
@@ -1234,7 +1309,10 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   for (uint32_t it = 0; it < full; ++it) draw2(true, true);
   if ((per & 1u) | extra) draw2(2u * full < n, 2u * full + 1u < n);
   __syncwarp();
-  claim_wins<DK>(g, claims, S, nwin, lane);
+  if constexpr (DK == kInteract)
+    claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, st);
+  else
+    claim_wins<DK>(g, claims, S, nwin, lane);
   __syncwarp();  // S.E, S.P, S.V and S.win are rewritten by the next chunk
 }
 
@@ -1286,7 +1364,8 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
   const uint32_t live_dirs = live_directions(st);
-  load_thresholds<true>(st, threadIdx.x, s_thr);  // complemented, for fail_bits
+  load_thresholds<true>(st, threadIdx.x, s_thr,  // complemented, for fail_bits
+                        DK == kInteract ? g.enter_max : nullptr);
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;
@@ -1302,7 +1381,8 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
       const uint32_t idx = c * 32u + lane;
       uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
       if (w >= g.nwords) w = 0xFFFFFFFFu;  // only after a timed-out scan (reported)
-      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
+      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt,
+                     st);
     }
   }
   flush_counters(st, cnt);
@@ -1517,6 +1597,9 @@ Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic) {
   Geom g{};
   g.periodic = periodic ? 1u : 0u;
   g.blocked = nullptr;
+  g.enter = nullptr;
+  g.labels = nullptr;
+  g.enter_thr = nullptr;
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -1565,6 +1648,9 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kInteract>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGrowSmemBytes);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch<kOpen>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGrowSmemBytes);
   if (e == cudaSuccess)
@@ -1581,6 +1667,9 @@ cudaError_t prepare_kernels() {
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow<kRuntime>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grow<kInteract>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grow_batch<kOpen>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1652,7 +1741,11 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
     QSGS_LAUNCH(tr, kClsGrow, s, k_grow_fullfield, blocks, 256, g, b.grid, b.aux, b.mark, b.st,
                 make_philox_keys((uint64_t)k1 << 32 | k0));
   } else {
-    if (g.blocked)
+    if (g.enter)
+      QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kInteract>, shape.blocks, kGrowThreads,
+                       kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                       make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+    else if (g.blocked)
       QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,
                        kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
                        make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
@@ -1748,9 +1841,58 @@ cudaError_t launch_or_words(uint32_t n, const uint32_t* src, uint32_t* dst, cuda
   return cudaSuccess;
 }
 
+// Interacting phases (R13): from the labels of earlier phases, the packed
+// grid of all their cells (blocked) and, per class k, of the cells whose
+// label may be entered along class k (bit `label` of sets[k]).  A thread per
+// word; bits at x >= nx stay 0.
+struct LabelSets {
+  uint32_t bits[3][8];  // per class: a 256-bit set of labels
+};
+
+__global__ void k_pack_labels(Geom g, const uint8_t* __restrict__ labels, uint32_t* blocked,
+                              uint32_t* enter, LabelSets sets) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < g.nwords;
+       w += gridDim.x * blockDim.x) {
+    const uint32_t r = fast_div(w, g.div_W);
+    const uint32_t x0 = (w - r * g.W) * 32u;
+    const uint32_t len = min(32u, g.nx - x0);
+    const uint8_t* row = labels + (size_t)r * g.nx + x0;
+    uint32_t b = 0, e0 = 0, e1 = 0, e2 = 0;
+    for (uint32_t i = 0; i < len; ++i) {
+      const uint32_t lab = row[i];
+      b |= (lab != 0u ? 1u : 0u) << i;
+      e0 |= ((sets.bits[0][lab >> 5] >> (lab & 31u)) & 1u) << i;
+      e1 |= ((sets.bits[1][lab >> 5] >> (lab & 31u)) & 1u) << i;
+      e2 |= ((sets.bits[2][lab >> 5] >> (lab & 31u)) & 1u) << i;
+    }
+    blocked[w] = b;
+    enter[w] = e0;
+    enter[(size_t)g.nwords + w] = e1;
+    enter[2 * (size_t)g.nwords + w] = e2;
+  }
+}
+
+cudaError_t launch_pack_labels(const Geom& g, const uint8_t* labels, uint32_t* blocked,
+                               uint32_t* enter, const uint32_t (&sets)[3][8], cudaStream_t s,
+                               Tracer& tr) {
+  LabelSets ls;
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 8; ++j) ls.bits[k][j] = sets[k][j];
+  uint64_t blocks = ((uint64_t)g.nwords + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  QSGS_LAUNCH(tr, kClsSeed, s, k_pack_labels, (uint32_t)(blocks ? blocks : 1), 256, g, labels,
+              blocked, enter, ls);
+  return cudaSuccess;
+}
+
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              GrowShape shape, cudaStream_t s, Tracer& tr) {
-  if (g.blocked)
+  if (g.enter)
+    QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kInteract>, shape.blocks, kGrowThreads,
+                     kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                     make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
+  else if (g.blocked)
     QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,
                      kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
                      make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);

@@ -201,6 +201,12 @@ cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thre
 // untouched); src words ORed into dst (n words).
 cudaError_t launch_label_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint8_t label,
                             cudaStream_t s, Tracer& tr);
+// Interacting phases (R13): packed grids of the earlier phases' cells and,
+// per class, of the enterable ones (three grids nwords apart) from a label
+// map; sets[k] holds the labels that class k may enter (bit m of word m>>5).
+cudaError_t launch_pack_labels(const Geom& g, const uint8_t* labels, uint32_t* blocked,
+                               uint32_t* enter, const uint32_t (&sets)[3][8], cudaStream_t s,
+                               Tracer& tr);
 cudaError_t launch_or_words(uint32_t n, const uint32_t* src, uint32_t* dst, cudaStream_t s,
                             Tracer& tr);
 // Voxels [vb, ve) of the grid as one byte each into out[0 .. ve - vb).

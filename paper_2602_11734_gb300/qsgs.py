@@ -99,6 +99,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_mode": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_set_blocked": ([H, ctypes.c_void_p], ctypes.c_int),
+                "qsgs_interaction_bytes": ([P], ctypes.c_size_t),
+                "qsgs_set_interaction": ([H, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32,
+                                          vp, ctypes.c_size_t], ctypes.c_int),
                 "qsgs_set_spin_limit": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_fetch_label": ([H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint8],
                                      ctypes.c_int),
@@ -321,6 +324,20 @@ def qsgs_set_blocked(h, dev_ptr: int) -> None:
            "qsgs_set_blocked")
 
 
+def qsgs_interaction_bytes(p: dict) -> int:
+    return int(load_library().qsgs_interaction_bytes(ctypes.byref(make_params(p))))
+
+
+def qsgs_set_interaction(h, labels_ptr: int, probs, scratch_ptr: int, scratch_bytes: int) -> None:
+    """probs: rows (I_face, I_edge, I_corner) of the labels 1, 2, ...; labels_ptr
+    0 clears the interaction."""
+    rows = [tuple(float(v) for v in r) for r in (probs if probs is not None else [])]
+    arr = (ctypes.c_double * max(1, 3 * len(rows)))(*[v for r in rows for v in r])
+    _check(load_library().qsgs_set_interaction(h, ctypes.c_void_p(labels_ptr or None), arr,
+                                               len(rows), ctypes.c_void_p(scratch_ptr or None),
+                                               scratch_bytes), "qsgs_set_interaction")
+
+
 def qsgs_fetch_label(h, dev_ptr: int, nbytes: int, label: int) -> None:
     _check(load_library().qsgs_fetch_label(h, ctypes.c_void_p(dev_ptr), nbytes, label),
            "qsgs_fetch_label")
@@ -439,6 +456,28 @@ class Generator:
         self._blocked = blocked
         qsgs_set_blocked(self.handle, 0 if blocked is None else blocked.data_ptr())
 
+    def set_interaction(self, labels, probs) -> None:
+        """Interacting phase (R13): `labels` is the uint8 device map of the
+        earlier phases (0 = unassigned), `probs` maps a label m to its
+        (I_face, I_edge, I_corner) (a dict, or rows for m = 1, 2, ...); the
+        phase also grows into those cells.  None clears it."""
+        import torch
+        if labels is None:
+            self._labels = self._inter_scratch = None
+            qsgs_set_interaction(self.handle, 0, [], 0, 0)
+            return
+        if isinstance(probs, dict):
+            n = max(probs) if probs else 0
+            rows = [tuple(probs.get(m, (0.0, 0.0, 0.0))) for m in range(1, n + 1)]
+        else:
+            rows = [tuple(r) for r in probs]
+        nbytes = qsgs_interaction_bytes(self.params)
+        with torch.cuda.device(self.device):
+            scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)  # the labels may come from torch's stream
+        self._labels, self._inter_scratch = labels, scratch
+        qsgs_set_interaction(self.handle, labels.data_ptr(), rows, scratch.data_ptr(), nbytes)
+
     def fetch_label(self, labels, label: int) -> None:
         """Writes `label` into the uint8 device map `labels` at this phase's cells."""
         qsgs_fetch_label(self.handle, labels.data_ptr(), labels.numel(), label)
@@ -544,11 +583,13 @@ def generate(params: dict, device=None, fmt: str = "u8"):
         g.close()
 
 
-def generate_phases(phases: list, device=None):
-    """Sec. 2.1 steps 4-5 with independent discrete phases: phase k (k = 1,
-    2, ...) grows on the cells no earlier phase holds; returns the uint8
-    label map (nz, ny, nx) on the device (0 = matrix) and every phase's
-    Stats.  All phases must have the same grid dims and domain kind."""
+def generate_phases(phases: list, device=None, interactions=None):
+    """Sec. 2.1 steps 4-5: phase k (k = 1, 2, ...) grows on the cells no
+    earlier phase holds -- and, when interactions[k - 1] is a dict {m:
+    (I_face, I_edge, I_corner)}, also into cells of the earlier phases m
+    (R13), which become phase k's.  Returns the uint8 label map (nz, ny, nx)
+    on the device (0 = matrix) and every phase's Stats.  All phases must
+    have the same grid dims and domain kind."""
     import torch
     if not phases or len(phases) > 255:
         raise ValueError("1 .. 255 phases")
@@ -566,8 +607,14 @@ def generate_phases(phases: list, device=None):
         if (q.nx, q.ny, q.nz, q.periodic) != dims:
             raise ValueError("all phases need the same grid")
         g = Generator(p, device=dev)
+        spec = interactions[k - 1] if interactions else None
         try:
-            g.set_blocked(blocked if k > 1 else None)
+            if spec:
+                if any(not 1 <= m < k for m in spec):
+                    raise ValueError(f"phase {k} can only enter earlier phases")
+                g.set_interaction(labels, spec)
+            else:
+                g.set_blocked(blocked if k > 1 else None)
             g.seed()
             stats.append(g.grow())
             g.fetch_label(labels, k)

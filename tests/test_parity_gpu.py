@@ -464,6 +464,78 @@ def test_phases_match_the_oracle(oracle, Q, periodic):
                    (r.solid_count, r.steps, r.status, r.n_accepted, r.front_size)
 
 
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_interacting_phase_matches_the_oracle(oracle, Q, periodic):
+    # Reading R13: the phase also grows into cells of earlier phases (random
+    # label maps and interaction tables); grid and statistics agree, the
+    # per-step front sums included.
+    rng = np.random.default_rng(320 + periodic)
+    for trial in range(5):
+        p = dict(workloads.small_64(), nx=int(rng.integers(20, 70)), ny=int(rng.integers(12, 40)),
+                 nz=int(rng.integers(10, 30)), periodic=periodic, cd=0.006,
+                 spacing_s=int(rng.integers(0, 5)), g_face=0.06, g_edge=0.02, g_corner=0.01,
+                 target_solid_fraction=float(rng.uniform(0.3, 0.7)),
+                 seed=int(rng.integers(0, 2**62)), max_steps=600)
+        shape = (p["nz"], p["ny"], p["nx"])
+        n_labels = int(rng.integers(1, 4))
+        lab = rng.integers(1, n_labels + 1, size=shape).astype(np.uint8)
+        lab[rng.random(shape) >= rng.uniform(0.2, 0.6)] = 0
+        inter = rng.uniform(0.0, 0.5, size=(n_labels, 3)) * (rng.random((n_labels, 3)) < 0.7)
+        want = oracle.run(p, blocked=lab, inter=inter)
+        g = Q.Generator(p)
+        try:
+            labels = torch.from_numpy(lab).cuda()
+            g.set_interaction(labels, inter.tolist())
+            g.seed()
+            st = g.grow()
+            got = g.fetch().cpu().numpy()
+            assert np.array_equal(got, want.phase), (trial, p)
+            assert (st.solid_count, st.steps, st.status, st.front_size, st.n_seeds) == \
+                   (want.solid_count, want.steps, want.status, want.front_size, want.n_accepted)
+            assert st.sum_front == int(want.log["front"].sum())
+        finally:
+            g.close()
+
+
+def test_interacting_phases_generate_matches_the_oracle(oracle, Q):
+    rng = np.random.default_rng(330)
+    for periodic in (0, 1):
+        dims = dict(nx=int(rng.integers(24, 60)), ny=int(rng.integers(16, 40)),
+                    nz=int(rng.integers(12, 30)), periodic=periodic)
+        phases = []
+        for frac, cd, s in ((0.35, 0.004, 3), (0.25, 0.01, 0), (0.2, 0.02, 4)):
+            phases.append(dict(workloads.small_64(), **dims, cd=cd, spacing_s=s,
+                               g_face=0.05, g_edge=0.02, g_corner=0.01, max_steps=600,
+                               target_solid_fraction=frac, seed=int(rng.integers(0, 2**62))))
+        spec = [None, {1: (0.3, 0.1, 0.05)}, {1: (0.2, 0.0, 0.0), 2: (0.0, 0.25, 0.3)}]
+        want, results = oracle.run_phases(phases, spec)
+        labels, stats = Q.generate_phases(phases, interactions=spec)
+        assert np.array_equal(labels.cpu().numpy(), want), periodic
+        for st, r in zip(stats, results):
+            assert (st.solid_count, st.steps, st.status, st.n_seeds, st.front_size) == \
+                   (r.solid_count, r.steps, r.status, r.n_accepted, r.front_size)
+
+
+def test_interaction_is_single_path_lists_only(Q):
+    p = dict(workloads.small_64(), nx=20, ny=20, nz=20)
+    g = Q.Generator(p)
+    b = Q.Batch(1, Q.word_count(p))
+    try:
+        labels = torch.zeros((20, 20, 20), dtype=torch.uint8, device="cuda")
+        labels[:, :, :5] = 1
+        g.set_interaction(labels, [(0.5, 0.5, 0.5)])
+        with pytest.raises(Q.QsgsError):
+            g.set_mode(Q.QSGS_MODE_FULLFIELD)
+        with pytest.raises(Q.QsgsError):
+            b.set_members([g])
+        g.set_interaction(None, None)       # cleared: both allowed again
+        b.set_members([g])
+        g.set_mode(Q.QSGS_MODE_FULLFIELD)
+    finally:
+        b.close()
+        g.close()
+
+
 def test_blocked_single_phase_and_batch(oracle, Q):
     rng = np.random.default_rng(310)
     params = [dict(workloads.random_small(rng, max_edge=26), cd=0.03, max_steps=0)
