@@ -325,26 +325,43 @@ def bench_fontainebleau(Q, torch, dev) -> dict:
                             for sp, v in sorted(per_s.items())]}
 
 
+# Interactions of the interacting variant of the phases workload: phase 2
+# enters phase 1 cells, phase 3 enters both (I per face / edge / corner).
+PHASE_INTERACTIONS = [None, {1: (0.01, 0.0025, 0.000625)},
+                      {1: (0.005, 0.0, 0.0), 2: (0.01, 0.0025, 0.0)}]
+
+
 def bench_phases(Q, torch, dev) -> dict:
-    """Three independent growing phases on the 400^3 box (Sec. 2.1 steps 4-5,
-    reading R12): volume fractions 0.45 / 0.20 / 0.10 of the domain, the
-    rest matrix; each phase with the single-phase parameters otherwise.
-    Wall time of the whole label map (seeding, growth, label and blocked
-    fetches of all three phases), after an untimed run."""
+    """Three growing phases on the 400^3 box (Sec. 2.1 steps 4-5): volume
+    fractions 0.45 / 0.20 / 0.10 of the domain, the rest matrix; each phase
+    with the single-phase parameters otherwise.  Independent phases
+    (reading R12), and the same phases interacting (R13,
+    PHASE_INTERACTIONS).  Wall time of the whole label map (seeding, growth,
+    label and blocked fetches of all three phases), after an untimed run."""
     base = workloads.single_400()
     phases = [dict(base, target_solid_fraction=f, seed=10 + k, spacing_s=s)
               for k, (f, s) in enumerate(((0.45, 30), (0.20, 15), (0.10, 0)))]
-    Q.generate_phases(phases, device=dev)  # untimed warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    labels, stats = Q.generate_phases(phases, device=dev)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    counts = torch.bincount(labels.view(-1), minlength=4).cpu().tolist()
+
+    def timed(interactions):
+        Q.generate_phases(phases, device=dev, interactions=interactions)  # untimed warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        labels, stats = Q.generate_phases(phases, device=dev, interactions=interactions)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        counts = torch.bincount(labels.view(-1), minlength=4).cpu().tolist()
+        return dt, counts, stats
+
+    dt, counts, stats = timed(None)
+    dti, counts_i, stats_i = timed(PHASE_INTERACTIONS)
     return {"workload": "phases_400", "phases": len(phases), "ms": round(dt * 1e3, 3),
             "nodes_per_s": 400**3 / dt,
             "label_counts": counts,
-            "exact_targets": all(st.solid_count == st.target_count for st in stats)}
+            "exact_targets": all(st.solid_count == st.target_count for st in stats),
+            "interacting": {"ms": round(dti * 1e3, 3), "nodes_per_s": 400**3 / dti,
+                            "label_counts": counts_i, "steps": [st.steps for st in stats_i],
+                            "exact_targets": all(st.solid_count == st.target_count
+                                                 for st in stats_i)}}
 
 
 def bench_sizes(Q, torch, dev) -> dict:
