@@ -161,8 +161,12 @@ struct qsgs_handle {
   bool list_stale;
   // The exact-target epilogue has run since the run ended (batch members).
   bool finalized;
-  // Interacting phase (R13): the label thresholds copied to the scratch.
+  // Interacting phase (R13): the label thresholds copied to the scratch, and
+  // the device pointers of GeomInter (nullptr for an independent phase).
   std::vector<uint32_t> enter_thr;
+  const uint32_t* dev_enter;
+  const uint8_t* dev_labels;
+  const uint32_t* dev_enter_thr;
 };
 
 namespace {
@@ -200,7 +204,9 @@ void fill_stats(const qsgs_handle* h, const RunState& s, qsgs_stats* out) {
 }
 
 StepBuffers step_buffers(const qsgs_handle* h) {
-  return StepBuffers{h->st, h->scan_status, h->grid, h->aux, h->mark, h->list};
+  return StepBuffers{h->st,   h->scan_status, h->grid,       h->aux,
+                     h->mark, h->list,        h->dev_enter,  h->dev_labels,
+                     h->dev_enter_thr};
 }
 
 // Seeding, spacing, the seed cap and the initial candidate list (Sec. 2.1
@@ -482,6 +488,9 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->iters_seen = 0;
   h->list_stale = false;
   h->finalized = false;
+  h->dev_enter = nullptr;
+  h->dev_labels = nullptr;
+  h->dev_enter_thr = nullptr;
   // The scan status words must start with flag 0; the run state is set by
   // qsgs_seed.
   cudaError_t e = cudaMemsetAsync(h->ws, 0, L.grid, h->stream);
@@ -725,7 +734,7 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   uint32_t open_only = 1;
   for (uint32_t m = 0; m < n; ++m) {
     qsgs_handle* h = members[m];
-    if (!h || h->g.enter) return QSGS_ERR_INVALID;  // interacting phases: single path only
+    if (!h || h->dev_enter) return QSGS_ERR_INVALID;  // interacting phases: single path only
     if (h->g.periodic || h->g.blocked) open_only = 0;
     MemberDesc& d = descs[m];
     std::memset(&d, 0, sizeof(d));
@@ -895,9 +904,9 @@ int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked) {
   if (!h) return QSGS_ERR_INVALID;
   if (dev_blocked && (reinterpret_cast<uintptr_t>(dev_blocked) % 4)) return QSGS_ERR_INVALID;
   h->g.blocked = static_cast<const uint32_t*>(dev_blocked);
-  h->g.enter = nullptr;  // an independent phase: no interaction
-  h->g.labels = nullptr;
-  h->g.enter_thr = nullptr;
+  h->dev_enter = nullptr;  // an independent phase: no interaction
+  h->dev_labels = nullptr;
+  h->dev_enter_thr = nullptr;
   destroy_graph(h);  // the geometry (with the pointer) is baked into the graph
   h->graph_tried = false;
   return QSGS_OK;
@@ -938,9 +947,9 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
   if (!h) return QSGS_ERR_INVALID;
   if (!dev_labels) {  // back to an independent first phase
     h->g.blocked = nullptr;
-    h->g.enter = nullptr;
-    h->g.labels = nullptr;
-    h->g.enter_thr = nullptr;
+    h->dev_enter = nullptr;
+    h->dev_labels = nullptr;
+    h->dev_enter_thr = nullptr;
     destroy_graph(h);
     h->graph_tried = false;
     return QSGS_OK;
@@ -953,11 +962,10 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
     if (!(probs[i] >= 0.0 && probs[i] <= 1.0)) return QSGS_ERR_INVALID;
   const size_t nwords = h->g.nwords;
   if (scratch_bytes < 4 * nwords * 4 + 256 * 3 * 4) return QSGS_ERR_WORKSPACE;
-  // Thresholds floor(I 2^32) - 1 per label and class (row 0: unassigned,
-  // unused); sets of the labels each class may enter; the largest per class.
+  // Thresholds floor(I 2^32) - 1 per label and class; row 0 (no label)
+  // holds the largest per class; sets of the labels each class may enter.
   h->enter_thr.assign(256 * 3, 0u);
   uint32_t sets[3][8] = {};
-  for (uint32_t k = 0; k < 3; ++k) h->g.enter_max[k] = 0;
   for (uint32_t m = 1; m <= n_labels; ++m)
     for (uint32_t k = 0; k < 3; ++k) {
       const double pr = probs[3 * (m - 1) + k];
@@ -966,7 +974,7 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
       const uint32_t t1 = (uint32_t)(T - 1);
       h->enter_thr[m * 3 + k] = t1;
       sets[k][m >> 5] |= 1u << (m & 31u);
-      if (t1 > h->g.enter_max[k]) h->g.enter_max[k] = t1;
+      if (t1 > h->enter_thr[k]) h->enter_thr[k] = t1;
     }
   uint32_t* blocked = static_cast<uint32_t*>(dev_scratch);
   uint32_t* enter = blocked + nwords;
@@ -979,9 +987,9 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->g.blocked = blocked;
-  h->g.enter = enter;
-  h->g.labels = dev_labels;
-  h->g.enter_thr = thr;
+  h->dev_enter = enter;
+  h->dev_labels = dev_labels;
+  h->dev_enter_thr = thr;
   destroy_graph(h);  // the geometry (with the pointers) is baked into the graph
   h->graph_tried = false;
   return QSGS_OK;
@@ -989,7 +997,7 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
 
 int qsgs_set_mode(qsgs_handle* h, int mode) {
   if (!h || (mode != QSGS_MODE_LIETS && mode != QSGS_MODE_FULLFIELD)) return QSGS_ERR_INVALID;
-  if (mode == QSGS_MODE_FULLFIELD && h->g.enter) return QSGS_ERR_STATE;
+  if (mode == QSGS_MODE_FULLFIELD && h->dev_enter) return QSGS_ERR_STATE;
   if (mode != h->mode) {
     h->mode = mode;
     destroy_graph(h);  // the step kernel is baked into the graph

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
       uint32_t* other = md.aux + (size_t)((t & 1u) ^ 1u) * md.g.nwords;
       GrowCounters cnt{0, 0};
       grow_chunk<DK>(md.g, md.grid, claims, other, md.mark, w, t, live_dirs, s_thr[warp], keys,
-                     smem[warp], cnt, md.st);
+                     smem[warp], cnt);
       flush_counters(md.st, cnt);
     }
   }

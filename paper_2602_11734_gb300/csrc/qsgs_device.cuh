@@ -58,13 +58,17 @@ struct Geom {
   uint32_t periodic; // 1: neighbours wrap around every axis (a torus)
   FastDiv div_nx, div_ny, div_W;
   const uint32_t* blocked;  // packed cells of earlier phases (R12), or nullptr
-  // Interacting phases (R13), all nullptr when the phase is independent:
+};
+
+// The geometry of an interacting phase (R13), passed to that kind's kernels
+// only (so that Geom, which every kernel takes, keeps its size).
+struct GeomInter : Geom {
   const uint32_t* enter;      // three packed grids (class face, edge, corner;
                               // nwords apart): cells of earlier phases that
                               // may be entered along that class
   const uint8_t* labels;      // labels of earlier phases, 0 = unassigned
-  const uint32_t* enter_thr;  // [label * 3 + class]: floor(I 2^32) - 1
-  uint32_t enter_max[3];      // per class: the largest enter_thr of any label
+  const uint32_t* enter_thr;  // [label * 3 + class]: floor(I 2^32) - 1; row
+                              // 0 (no label): per class the largest of them
 };
 
 // ---------------------------------------------------------------------------

@@ -386,11 +386,6 @@ struct FrontCountPolicy {
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w, bool valid) const {
-    if (g.enter) {  // interacting phase: enterable neighbours count too (R13)
-      uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
-      if (valid) word_masks<kInteract>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
-      return Item{w, front, 0u};
-    }
     if (g.periodic || g.blocked) {  // the growth kernel's own neighbour masks
       uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
       if (valid) word_masks<kRuntime>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
@@ -432,6 +427,29 @@ struct FrontCountPolicy {
       }
     }
     return Item{w, self & ~solid_all, 0u};
+  }
+  __device__ uint32_t count(const Item&) const { return 0u; }
+  __device__ uint32_t side(const Item& it, int k) const { return k == 0 ? __popc(it.bits) : 0u; }
+  __device__ unsigned long long* side_sum(int k) const { return k == 0 ? &st->front_n : nullptr; }
+  __device__ void emit(const Item&, unsigned long long) const {}
+  __device__ void total(unsigned long long) const {}
+};
+
+// The front count of an interacting phase (R13): a voxel is active if it has
+// a void neighbour or an enterable one -- the growth kernel's own masks.
+struct FrontCountInterPolicy {
+  GeomInter g;
+  RunState* st;
+  const uint32_t* grid;
+  using Item = WordItem;
+  __device__ void apply(const Item&, bool) const {}
+  __device__ bool active() const { return true; }
+  __device__ bool emit_empty() const { return false; }
+  __device__ uint32_t n_items() const { return g.nwords; }
+  __device__ Item load(uint32_t w, bool valid) const {
+    uint32_t V[28], Bm[7] = {0, 0, 0, 0, 0, 0, 0}, front = 0, r, xw;
+    if (valid) word_masks<kInteract>(g, grid, w, (1u << 26) - 1u, V, Bm, front, r, xw);
+    return Item{w, front, 0u};
   }
   __device__ uint32_t count(const Item&) const { return 0u; }
   __device__ uint32_t side(const Item& it, int k) const { return k == 0 ? __popc(it.bits) : 0u; }
@@ -937,28 +955,10 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
     yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
     zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
   }
-  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
-  constexpr int cls_x = dir_cls(dm);                   // class of the x-1 / x+1 directions
-  constexpr int cls_0 = d0 >= 0 ? dir_cls(d0) : 0;     // class of the centre direction
   uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
-  // Interacting phase (R13): enterable cells of earlier phases -- in the
-  // grid of the direction's class and not yet this phase's -- per class used
-  // by this row (x +-1: ex*, centre: e0*); outside the domain: none.
-  uint32_t exc = 0, exl = 0, exr = 0, e0c = 0;
   if (kInterior || (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz)) {
     const size_t ro = (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
     row_words<DK>(g, grid + ro, xw, c, l, rr);
-    if (DK == kInteract) {
-      uint32_t a, b, e;
-      row_words<DK>(g, g.enter + (size_t)cls_x * g.nwords + ro, xw, a, b, e);
-      exc = a & ~c;
-      exl = b & ~l;
-      exr = e & ~rr;
-      if (d0 >= 0) {
-        row_words<DK>(g, g.enter + (size_t)cls_0 * g.nwords + ro, xw, a, b, e);
-        e0c = a & ~c;
-      }
-    }
     if (has_blocked<DK>(g)) {  // cells of earlier phases are not void either
       uint32_t bc, bl, br;
       row_words<DK>(g, g.blocked + ro, xw, bc, bl, br);
@@ -969,18 +969,69 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
   }
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
   const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
+  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
-  // Enterable targets (R13) need no live class: their grid holds only
-  // labels with a positive interaction probability for that class.
-  const uint32_t em = DK == kInteract ? ((exc << 1) | (exl >> 31)) & self : 0u;
-  const uint32_t ep = DK == kInteract ? ((exc >> 1) | (exr << 31)) & self : 0u;
+  front |= vm | vp;
+  V[dm] = vm & live[dir_cls(dm)];
+  Bm[dm >> 2] |= V[dm];
+  if (d0 >= 0) {
+    constexpr int d = d0 < 0 ? 26 : d0;
+    const uint32_t v0 = ~c & self;
+    front |= v0;
+    V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
+    Bm[(d >> 2) % 7] |= V[d];
+  }
+  V[dp] = vp & live[dir_cls(dp)];
+  Bm[dp >> 2] |= V[dp];
+}
+
+// The same for an interacting phase (R13): besides the void targets, cells
+// of earlier phases that may be entered -- in the packed grid of the
+// direction's class and not yet this phase's -- are targets, and they make
+// a voxel active; they need no live class (their grid holds only labels
+// with a positive interaction probability for that class).
+template <int DZ, int DY>
+__device__ __forceinline__ void row_masks_inter(const Geom& g, const uint32_t* __restrict__ grid,
+                                                uint32_t y, uint32_t z, uint32_t xw, uint32_t self,
+                                                const uint32_t (&live)[3], uint32_t (&V)[28],
+                                                uint32_t (&Bm)[7], uint32_t& front) {
+  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
+  constexpr int cls_x = dir_cls(dm);                // class of the x-1 / x+1 directions
+  constexpr int cls_0 = d0 >= 0 ? dir_cls(d0) : 0;  // class of the centre direction
+  int yy = (int)y + DY, zz = (int)z + DZ;
+  if (g.periodic) {
+    yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
+    zz = zz < 0 ? zz + (int)g.nz : (zz >= (int)g.nz ? zz - (int)g.nz : zz);
+  }
+  uint32_t c = 0xFFFFFFFFu, l = 0xFFFFFFFFu, rr = 0xFFFFFFFFu;  // outside: solid
+  uint32_t exc = 0, exl = 0, exr = 0, e0c = 0;                   // outside: none
+  const GeomInter& gi = static_cast<const GeomInter&>(g);  // the kind's own geometry
+  if (yy >= 0 && yy < (int)g.ny && zz >= 0 && zz < (int)g.nz) {
+    const size_t ro = (size_t)((uint32_t)zz * g.ny + (uint32_t)yy) * g.W;
+    row_words<kInteract>(g, grid + ro, xw, c, l, rr);
+    uint32_t a, b, e;
+    row_words<kInteract>(g, gi.enter + (size_t)cls_x * g.nwords + ro, xw, a, b, e);
+    exc = a & ~c;
+    exl = b & ~l;
+    exr = e & ~rr;
+    if (d0 >= 0) {
+      row_words<kInteract>(g, gi.enter + (size_t)cls_0 * g.nwords + ro, xw, a, b, e);
+      e0c = a & ~c;
+    }
+    uint32_t bc, bl, br;  // cells of earlier phases are not void
+    row_words<kInteract>(g, g.blocked + ro, xw, bc, bl, br);
+    c |= bc;
+    l |= bl;
+    rr |= br;
+  }
+  const uint32_t vm = ~((c << 1) | (l >> 31)) & self, vp = ~((c >> 1) | (rr << 31)) & self;
+  const uint32_t em = ((exc << 1) | (exl >> 31)) & self, ep = ((exc >> 1) | (exr << 31)) & self;
   front |= vm | vp | em | ep;
   V[dm] = (vm & live[cls_x]) | em;
   Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
-    const uint32_t v0 = ~c & self;
-    const uint32_t e0 = DK == kInteract ? e0c & self : 0u;
+    const uint32_t v0 = ~c & self, e0 = e0c & self;
     front |= v0 | e0;
     V[d] = (v0 & live[cls_0]) | e0;
     Bm[(d >> 2) % 7] |= V[d];
@@ -998,18 +1049,33 @@ struct GrowCounters {
 // (classes with T > 0).  Written by lanes 0..27 of a warp or block.
 // kComplement stores ~(T - 1) instead: r + ~(T - 1) carries out of 32 bits
 // exactly when r > T - 1, which fail_bits below reads off the carry flag.
-// enter_max (interacting phases, R13): per class the largest threshold of
-// entering an earlier phase's cell; the draw loop then tests against the
-// larger of the two and the claims apply the target's own threshold.
 template <bool kComplement = false>
-__device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr,
-                                                const uint32_t* enter_max = nullptr) {
+__device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr) {
+  if (lane < 28) {
+    const int d = (int)lane;
+    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
+    const uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
+    reinterpret_cast<uint32_t*>(thr)[d] = kComplement ? ~t1 : t1;
+  }
+}
+
+// Interacting phases (R13): per direction the larger of the Eq. 1 threshold
+// and the largest threshold of entering an earlier phase's cell along its
+// class, complemented; the draw loop tests against it and the claims apply
+// the target's own threshold.
+// Eight entries: thr[7] = the Eq. 1 thresholds T - 1 of the three classes
+// themselves (not complemented), for the claims.
+__device__ __forceinline__ void load_thresholds_inter(const RunState* st, const GeomInter& g,
+                                                      uint32_t lane, uint4* thr) {
   if (lane < 28) {
     const int d = (int)lane;
     const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
     uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
-    if (enter_max && d < 26) t1 = max(t1, enter_max[dir_cls(d)]);
-    reinterpret_cast<uint32_t*>(thr)[d] = kComplement ? ~t1 : t1;
+    if (d < 26) t1 = max(t1, g.enter_thr[dir_cls(d)]);  // row 0: the largest per class
+    reinterpret_cast<uint32_t*>(thr)[d] = ~t1;
+  } else if (lane < 31) {
+    const unsigned long long T = st->thr[lane - 28];
+    reinterpret_cast<uint32_t*>(thr)[lane] = T ? (uint32_t)(T - 1) : 0u;
   }
 }
 
@@ -1076,7 +1142,9 @@ template <int DK>
 __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims,
                                                  const GrowWarpSmem& S, uint32_t nwin,
                                                  uint32_t lane, uint32_t t,
-                                                 const PhiloxKeys& keys, const RunState* st) {
+                                                 const PhiloxKeys& keys, const uint4* nthr) {
+  const GeomInter& gi = static_cast<const GeomInter&>(g);  // the kind's own geometry
+  const uint4 eq1 = nthr[7];  // Eq. 1 thresholds T - 1 per class (load_thresholds_inter)
   for (uint32_t k = lane; k < nwin; k += 32) {
     const uint32_t x = S.win[k];
     const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
@@ -1096,10 +1164,10 @@ __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims
       claim_target<DK>(g, wo, i, d, wq, bit);
       const uint32_t rq = fast_div(wq, g.div_W);
       const uint32_t q = rq * g.nx + (wq - rq * g.W) * 32u + (uint32_t)(__ffs(bit) - 1);
-      const uint32_t lab = g.labels[q];
-      const unsigned long long T = st->thr[dir_cls(d)];
-      const uint32_t th = lab ? g.enter_thr[lab * 3u + (uint32_t)dir_cls(d)]
-                              : (T ? (uint32_t)(T - 1) : 0u);
+      const uint32_t lab = gi.labels[q];
+      const int c = dir_cls(d);
+      const uint32_t th = lab ? gi.enter_thr[lab * 3u + (uint32_t)c]
+                              : (c == 0 ? eq1.x : (c == 1 ? eq1.y : eq1.z));
       if (u4_word(rnd, (int)j) <= th) atomicOr(claims + wq, bit);
     }
   }
@@ -1121,12 +1189,22 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   // Per class: all ones if its threshold is positive (live), else zero.
   const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
                             0u - ((live_dirs >> 18) & 1u)};
-  // On the open domain, words whose nine neighbour rows all lie inside the
-  // grid (almost all of them) take a copy without the per-row bounds tests
-  // and branches (4 % of the 400^3 growth time).  The torus and run-time
-  // kinds keep one copy: there the second one costs more in register
-  // spills than it saves.
-  if (DK == kOpen && y >= 1 && y + 1 < g.ny && z >= 1 && z + 1 < g.nz) {
+  if constexpr (DK == kInteract) {
+    row_masks_inter<-1, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<-1, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<-1, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<0, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<0, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<0, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<1, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<1, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<1, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
+  } else if (DK == kOpen && y >= 1 && y + 1 < g.ny && z >= 1 && z + 1 < g.nz) {
+    // On the open domain, words whose nine neighbour rows all lie inside the
+    // grid (almost all of them) take a copy without the per-row bounds tests
+    // and branches (4 % of the 400^3 growth time).  The torus and run-time
+    // kinds keep one copy: there the second one costs more in register
+    // spills than it saves.
     row_masks<-1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
     row_masks<-1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
     row_masks<-1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
@@ -1195,7 +1273,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
                                            uint32_t w, uint32_t t, uint32_t live_dirs,
                                            const uint4* nthr,
                                            const PhiloxKeys& keys, GrowWarpSmem& S,
-                                           GrowCounters& cnt, const RunState* st) {
+                                           GrowCounters& cnt) {
   const uint32_t lane = threadIdx.x & 31;
   // Phase 1: masks of this lane's word.
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -1299,7 +1377,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     if (nwin > (uint32_t)kGrowWins - 64u) {
       __syncwarp();
       if constexpr (DK == kInteract)
-        claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, st);
+        claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, nthr);
       else
         claim_wins<DK>(g, claims, S, nwin, lane);
       __syncwarp();
@@ -1310,7 +1388,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   if ((per & 1u) | extra) draw2(2u * full < n, 2u * full + 1u < n);
   __syncwarp();
   if constexpr (DK == kInteract)
-    claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, st);
+    claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, nthr);
   else
     claim_wins<DK>(g, claims, S, nwin, lane);
   __syncwarp();  // S.E, S.P, S.V and S.win are rewritten by the next chunk
@@ -1353,19 +1431,32 @@ __device__ __forceinline__ void finish_dispenser(uint32_t* next, uint32_t* done)
   }
 }
 
+// The kernel-parameter geometry of a kind: GeomInter for interacting phases.
+template <int DK>
+struct GeomOf {
+  using type = Geom;
+};
+template <>
+struct GeomOf<kInteract> {
+  using type = GeomInter;
+};
+
 template <int DK>
 __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
-    k_grow(Geom g, const uint32_t* __restrict__ cand, const uint32_t* __restrict__ grid,
+    k_grow(typename GeomOf<DK>::type g, const uint32_t* __restrict__ cand,
+           const uint32_t* __restrict__ grid,
            uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys, uint32_t tile) {
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
-  __shared__ uint4 s_thr[7];
+  __shared__ uint4 s_thr[DK == kInteract ? 8 : 7];  // kInteract: + the Eq. 1 slot
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
   const uint32_t live_dirs = live_directions(st);
-  load_thresholds<true>(st, threadIdx.x, s_thr,  // complemented, for fail_bits
-                        DK == kInteract ? g.enter_max : nullptr);
+  if constexpr (DK == kInteract)
+    load_thresholds_inter(st, g, threadIdx.x, s_thr);
+  else
+    load_thresholds<true>(st, threadIdx.x, s_thr);  // complemented, for fail_bits
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;  // this step's claim grid
   uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;
@@ -1381,8 +1472,7 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
       const uint32_t idx = c * 32u + lane;
       uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
       if (w >= g.nwords) w = 0xFFFFFFFFu;  // only after a timed-out scan (reported)
-      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt,
-                     st);
+      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
     }
   }
   flush_counters(st, cnt);
@@ -1597,9 +1687,6 @@ Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic) {
   Geom g{};
   g.periodic = periodic ? 1u : 0u;
   g.blocked = nullptr;
-  g.enter = nullptr;
-  g.labels = nullptr;
-  g.enter_thr = nullptr;
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -1613,6 +1700,17 @@ Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic) {
   g.div_ny = make_fastdiv(ny);
   g.div_W = make_fastdiv(g.W);
   return g;
+}
+
+// The geometry of an interacting phase's kernels: Geom plus the step
+// buffers' interaction pointers.
+GeomInter geom_inter(const Geom& g, const StepBuffers& b) {
+  GeomInter gi{};
+  static_cast<Geom&>(gi) = g;
+  gi.enter = b.enter;
+  gi.labels = b.labels;
+  gi.enter_thr = b.enter_thr;
+  return gi;
 }
 
 // Every launch goes through LAUNCH so that the tracer counts (and, when
@@ -1741,9 +1839,9 @@ cudaError_t launch_step(const Geom& g, const StepBuffers& b, uint32_t k0, uint32
     QSGS_LAUNCH(tr, kClsGrow, s, k_grow_fullfield, blocks, 256, g, b.grid, b.aux, b.mark, b.st,
                 make_philox_keys((uint64_t)k1 << 32 | k0));
   } else {
-    if (g.enter)
+    if (b.enter)
       QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kInteract>, shape.blocks, kGrowThreads,
-                       kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                       kGrowSmemBytes, geom_inter(g, b), b.list, b.grid, b.aux, b.mark, b.st,
                        make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
     else if (g.blocked)
       QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,
@@ -1771,6 +1869,13 @@ cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_l
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
               ctl);
   QSGS_LAUNCH(tr, kClsTrim, s, k_zero_front, 1, 1, b.st);
+  if (b.enter) {  // an interacting phase counts enterable neighbours too
+    FrontCountInterPolicy fi{geom_inter(g, b), b.st, b.grid};
+    QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontCountInterPolicy>, scan_grid(g.nwords),
+                kScanThreads, fi, ctl);
+    QSGS_LAUNCH(tr, kClsTrim, s, k_trim_done, 1, 1, b.st);
+    return cudaSuccess;
+  }
   FrontCountPolicy fp{g, b.st, b.grid};
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontCountPolicy>, scan_grid(g.nwords),
               kScanThreads, fp, ctl);
@@ -1888,9 +1993,9 @@ cudaError_t launch_pack_labels(const Geom& g, const uint8_t* labels, uint32_t* b
 
 cudaError_t launch_grow_only(const Geom& g, const StepBuffers& b, uint32_t k0, uint32_t k1,
                              GrowShape shape, cudaStream_t s, Tracer& tr) {
-  if (g.enter)
+  if (b.enter)
     QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kInteract>, shape.blocks, kGrowThreads,
-                     kGrowSmemBytes, g, b.list, b.grid, b.aux, b.mark, b.st,
+                     kGrowSmemBytes, geom_inter(g, b), b.list, b.grid, b.aux, b.mark, b.st,
                      make_philox_keys((uint64_t)k1 << 32 | k0), shape.tile);
   else if (g.blocked)
     QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow<kRuntime>, shape.blocks, kGrowThreads,

@@ -132,6 +132,10 @@ struct StepBuffers {
   uint32_t* aux;   // two claim grids (step parity)
   uint32_t* mark;  // one bit per word: still holds front voxels
   uint32_t* list;  // candidate word list (ascending)
+  // Interacting phase (R13): the fields of GeomInter, all nullptr otherwise.
+  const uint32_t* enter;
+  const uint8_t* labels;
+  const uint32_t* enter_thr;
 };
 
 Geom make_geom(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t periodic);
