@@ -249,7 +249,9 @@ int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks);
  * list-driven step, so the realization is the same bit for bit; only its
  * cost and stats.sum_draws (every block drawn) differ.  QSGS_MODE_LIETS
  * (the default) switches back.  Batches always use the list-driven step;
- * qsgs_time_grow always times it.  Returns QSGS_OK or QSGS_ERR_INVALID. */
+ * qsgs_time_grow always times it.  Returns QSGS_OK, QSGS_ERR_INVALID, or
+ * QSGS_ERR_STATE for QSGS_MODE_FULLFIELD on an interacting phase
+ * (qsgs_set_interaction). */
 int qsgs_set_mode(qsgs_handle* h, int mode);
 
 /* Failure-detection knob (no counterpart in the paper): how many polls a
@@ -382,12 +384,14 @@ size_t qsgs_batch_workspace_bytes(uint32_t max_members, uint64_t max_words);
 int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_workspace, size_t bytes,
                       void* cuda_stream, qsgs_batch** out);
 
-/* Sets the members (host array of n handles; replaces the previous set).  Members keep their run state: a member may join mid-run and leave
+/* Sets the members (host array of n handles; replaces the previous set).
+ * Members keep their run state: a member may join mid-run and leave
  * mid-run (qsgs_grow_until on a handle that left rebuilds its candidate
  * list first).  The batch stream waits for each member's own stream.
  * Blocks until the member table is on the device.  Must not be called while
- * an advance is in flight.  Returns QSGS_OK, QSGS_ERR_INVALID,
- * QSGS_ERR_WORKSPACE (too many words) or QSGS_ERR_CUDA. */
+ * an advance is in flight.  Returns QSGS_OK, QSGS_ERR_INVALID (also for a
+ * handle of an interacting phase, qsgs_set_interaction), QSGS_ERR_WORKSPACE
+ * (too many words) or QSGS_ERR_CUDA. */
 int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t n);
 
 /* Seeds (or re-seeds) every member, up to 8 at a time on private streams;
