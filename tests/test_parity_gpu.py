@@ -117,6 +117,15 @@ def test_edge_case_parity(oracle, Q, extra):
     assert_same(oracle, Q, p)
 
 
+@pytest.mark.parametrize("s", [8, 10])
+def test_dense_conflict_lists_parity(oracle, Q, s):
+    """Dense candidates (cd = 0.02 on 64^3, about 5.2 k of them) with
+    27 k (s = 8) and 53 k (s = 10) earlier conflicts: long conflict lists
+    for the spacing rounds, whose decisions stay in shared memory."""
+    p = dict(workloads.small_64(), cd=0.02, spacing_s=s, seed=11 + s)
+    assert_same(oracle, Q, p)
+
+
 def test_chunked_growth_equals_one_shot(oracle, Q):
     p = dict(workloads.small_64(), nx=48, ny=40, nz=36, spacing_s=3)
     for chunk in (1, 3, 5):
