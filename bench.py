@@ -120,19 +120,26 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """nvidia-smi clock/throttle samples while the timed region runs.
+
+    Sampling starts before the region (``wait_first`` returns once the first
+    sample is in, so nvidia-smi's start-up is not inside the region); each
+    sample is stamped on arrival, and ``stop`` keeps the samples that arrived
+    between ``begin`` and ``end``.  Only when the region is shorter than the
+    sampling interval does it fall back to the samples around it."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 25
 
     def __init__(self, gpu_id: str):
-        self.rows = []
+        self.rows = []  # (arrival time, fields)
         self.proc = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -143,26 +150,45 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) == 8:
-                self.rows.append(parts)
+                self.rows.append((time.perf_counter(), parts))
 
-    def stop(self):
+    def wait_first(self, timeout_s: float = 5.0) -> None:
+        t0 = time.perf_counter()
+        while (self.proc is not None and not self.rows and self.proc.poll() is None
+               and time.perf_counter() - t0 < timeout_s):
+            time.sleep(0.005)
+
+    def stop(self, begin: float, end: float):
         if self.proc is None:
             return None
+        time.sleep(2 * self.INTERVAL_MS / 1000.0)  # the sample in flight at `end`
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=5)
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
-                          if r[4 + i].lower() == "active"})
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(sm)}
+        return summarize_clocks(self.rows, begin, end)
+
+
+def summarize_clocks(rows, begin: float, end: float):
+    """Median SM clock, maximum clock and active throttle reasons of the
+    samples stamped inside [begin, end]; with none inside, of the last
+    sample before and the first after the region."""
+    inside = [r for t, r in rows if begin <= t <= end]
+    used = inside
+    if not used:
+        before = [r for t, r in rows if t < begin][-1:]
+        after = [r for t, r in rows if t > end][:1]
+        used = before + after
+    sm = [float(r[0]) for r in used if r[0].replace(".", "").isdigit()]
+    mx = [float(r[1]) for r in used if r[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in used for i in range(4) if r[4 + i].lower() == "active"})
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(sm), "samples_in_region": len(inside)}
 
 
 def cpu_baseline(edge: int):
@@ -548,8 +574,10 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
     sampler = ClockSampler(gpu_id)
+    sampler.wait_first()
     barrier()
     torch.cuda.synchronize()
+    region_begin = time.perf_counter()
     times = []
     launches0 = g.query().launches
     launches_timed = 0
@@ -568,7 +596,7 @@ def main():
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(region_begin, time.perf_counter())
     del launches0
     total_ms = max_over_ranks(sum(times), world, dev)
     value = job_rate(n_vox * a.steps, world, total_ms)
