@@ -178,47 +178,67 @@ __device__ __forceinline__ void emit_word_bits(const Geom& g, const WordItem& it
   }
 }
 
-// Sec. 2.1 step 2: the Bernoulli candidates of one word, drawn from Philox
-// block (v >> 2) word (v & 3) with the seeding tag.
+// Sec. 2.1 step 2: the Bernoulli candidate bits of one word, drawn from
+// Philox block (v >> 2) word (v & 3) with the seeding tag.
+__device__ __forceinline__ uint32_t seed_bits(const Geom& g, uint32_t w,
+                                              unsigned long long t_seed,
+                                              const PhiloxKeys& keys) {
+  uint32_t bits = 0;
+  if (t_seed != 0) {
+    const uint32_t r = fast_div(w, g.div_W);
+    const uint32_t xw = w - r * g.W;
+    const uint32_t x0 = xw * 32u;
+    const int len = (int)min(32u, g.nx - x0);
+    const uint32_t v0 = r * g.nx + x0;
+    const uint32_t g0 = v0 >> 2;        // first Philox block of the word
+    const int s0 = (int)(v0 & 3u);      // bit i is voxel 4 * (g0 + j) + q with i = 4j + q - s0
+    // The word's 32 voxels touch blocks g0 .. g0 + 8 (g0 + 7 when aligned).
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      if (j == 8 && s0 == 0) break;
+      const U4 blk = philox4x32_10(U4{g0 + (uint32_t)j, 0u, 0xFFFFFFFFu, kSeedTag}, keys);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * j + q - s0;
+        if (i >= 0 && i < len && (unsigned long long)u4_word(blk, q) < t_seed) bits |= 1u << i;
+      }
+    }
+  }
+  if (g.blocked != nullptr && bits) bits &= ~g.blocked[w];  // R12: only unassigned cells
+  return bits;
+}
+
+// The candidate bits of every word, written into the occupancy grid (empty
+// until the seeds are placed): a grid-stride pass, one word per thread and
+// iteration, so the Philox work runs at full occupancy and outside the
+// ordered scan that lists the candidates.
+__global__ void __launch_bounds__(256) k_seed_bits(Geom g, const RunState* st, uint32_t* grid,
+                                                  const PhiloxKeys keys) {
+  const unsigned long long t_seed = st->t_seed;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < g.nwords;
+       w += gridDim.x * blockDim.x)
+    grid[w] = seed_bits(g, w, t_seed, keys);
+}
+
+// Lists the candidates of k_seed_bits in ascending voxel order and clears
+// their bits from the grid again.
 struct SeedCompactPolicy {
   Geom g;
   RunState* st;
+  uint32_t* grid;          // candidate bits in, zero out
   uint32_t* cand;
   unsigned long long cap;  // entries cand can hold
-  PhiloxKeys keys;
   using Item = WordItem;
   __device__ uint32_t side(const Item&, int) const { return 0; }
   __device__ unsigned long long* side_sum(int) const { return nullptr; }
-  __device__ void apply(const Item&, bool) const {}
+  __device__ void apply(const Item& it, bool valid) const {
+    if (valid && it.bits) grid[it.w] = 0u;
+  }
   __device__ bool active() const { return true; }
   __device__ bool emit_empty() const { return false; }
   __device__ uint32_t n_items() const { return g.nwords; }
   __device__ Item load(uint32_t w, bool valid) const {
-    if (!valid) return Item{};
-    const unsigned long long t_seed = st->t_seed;
-    uint32_t bits = 0;
-    if (t_seed != 0) {
-      const uint32_t r = fast_div(w, g.div_W);
-      const uint32_t xw = w - r * g.W;
-      const uint32_t x0 = xw * 32u;
-      const int len = (int)min(32u, g.nx - x0);
-      const uint32_t v0 = r * g.nx + x0;
-      const uint32_t g0 = v0 >> 2;        // first Philox block of the word
-      const int s0 = (int)(v0 & 3u);      // bit i is voxel 4 * (g0 + j) + q with i = 4j + q - s0
-      // The word's 32 voxels touch blocks g0 .. g0 + 8 (g0 + 7 when aligned).
-#pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        if (j == 8 && s0 == 0) break;
-        const U4 blk = philox4x32_10(U4{g0 + (uint32_t)j, 0u, 0xFFFFFFFFu, kSeedTag}, keys);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = 4 * j + q - s0;
-          if (i >= 0 && i < len && (unsigned long long)u4_word(blk, q) < t_seed) bits |= 1u << i;
-        }
-      }
-    }
-    if (g.blocked != nullptr && bits) bits &= ~g.blocked[w];  // R12: only unassigned cells
-    return Item{w, bits, 0u};
+    return Item{w, valid ? grid[w] : 0u, 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
   __device__ void emit(const Item& it, unsigned long long off) const {
@@ -1666,6 +1686,12 @@ static uint32_t scan_grid(uint64_t max_items) {
   return (uint32_t)(blocks ? blocks : 1);
 }
 
+static uint32_t seed_bits_grid(uint64_t nwords) {
+  const uint64_t need = (nwords + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 8;  // 8 blocks of 256 threads per SM
+  return (uint32_t)(need < cap ? (need ? need : 1) : cap);
+}
+
 static uint32_t commit_grid(uint64_t nwords) {
   constexpr uint64_t kTile = kCommitThreads * kCommitItems;
   const uint64_t tiles = (nwords + kTile - 1) / kTile;
@@ -1787,8 +1813,11 @@ cudaError_t launch_init_state(RunState* st, const StateInit& init, cudaStream_t 
 cudaError_t launch_seed(const Geom& g, const SeedBuffers& b, uint32_t k0, uint32_t k1,
                         uint32_t spin_limit, cudaStream_t s, Tracer& tr) {
   ScanCtl ctl{b.st, b.scan_status, spin_limit};
-  // Candidates (ascending) into the list buffer.
-  SeedCompactPolicy sp{g, b.st, b.list, b.cand_cap, make_philox_keys((uint64_t)k1 << 32 | k0)};
+  // Candidate bits into the empty grid, then the candidates (ascending) into
+  // the list buffer.
+  QSGS_LAUNCH(tr, kClsSeed, s, k_seed_bits, seed_bits_grid(g.nwords), 256, g, b.st, b.grid,
+              make_philox_keys((uint64_t)k1 << 32 | k0));
+  SeedCompactPolicy sp{g, b.st, b.grid, b.list, b.cand_cap};
   QSGS_LAUNCH(tr, kClsSeed, s, k_lookback_scan<SeedCompactPolicy>, scan_grid(g.nwords),
               kScanThreads, sp, ctl);
   const uint8_t* decision = nullptr;
