@@ -126,3 +126,58 @@ def test_periodic_params_checked_like_the_oracle(lib, oracle):
                 oracle.run(p)
     with pytest.raises(Q.QsgsError):
         Q.qsgs_check_params(dict(nx=8, ny=8, nz=8, target_solid_fraction=0.5, periodic=2))
+
+
+def test_every_handle_call_rejects_a_null_handle(lib):
+    """Each entry point that takes a handle returns QSGS_ERR_INVALID for
+    NULL before it touches a device (include/qsgs.h: no exceptions, no
+    crash across the ABI)."""
+    inv = Q.QSGS_ERR_INVALID
+    s = Q.QsgsStats()
+    prof = (Q.QsgsProfileEntry * 8)()
+    ms = ctypes.c_double()
+    probs = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    assert lib.qsgs_set_profiling(None, 1) == inv
+    assert lib.qsgs_profile(None, prof, 8) == inv
+    assert lib.qsgs_set_grow_blocks(None, 0) == inv
+    assert lib.qsgs_set_grow_tile(None, 1) == inv
+    assert lib.qsgs_set_mode(None, 0) == inv
+    assert lib.qsgs_set_spin_limit(None, 0) == inv
+    assert lib.qsgs_set_blocked(None, None) == inv
+    assert lib.qsgs_set_interaction(None, None, probs, 1, None, 0) == inv
+    assert lib.qsgs_fetch_label(None, None, 0, 1) == inv
+    assert lib.qsgs_fetch_or(None, None, 0) == inv
+    assert lib.qsgs_time_grow(None, 0, 1, ctypes.byref(ms)) == inv
+    assert lib.qsgs_batch_set_members(None, None, 0) == inv
+    assert lib.qsgs_batch_seed(None) == inv
+    assert lib.qsgs_batch_advance(None, 0) == inv
+    assert lib.qsgs_batch_query(None, ctypes.byref(s), 1) == inv
+    assert lib.qsgs_batch_run(None, 0, ctypes.byref(s), 1) == inv
+    assert lib.qsgs_batch_set_grow_blocks(None, 0) == inv
+    assert lib.qsgs_batch_set_grow_tile(None, 1) == inv
+    assert lib.qsgs_batch_set_profiling(None, 1) == inv
+    assert lib.qsgs_batch_profile(None, prof, 8) == inv
+    lib.qsgs_batch_destroy(None)
+
+
+def test_batch_and_interaction_sizing_on_the_host(lib):
+    # batch workspace: members 1 .. 1024, words below 2^32; 0 = invalid
+    assert lib.qsgs_batch_workspace_bytes(0, 1000) == 0
+    assert lib.qsgs_batch_workspace_bytes(1025, 1000) == 0
+    assert lib.qsgs_batch_workspace_bytes(4, 1 << 32) == 0
+    a = lib.qsgs_batch_workspace_bytes(4, 1000)
+    b = lib.qsgs_batch_workspace_bytes(4, 2000)
+    assert a > 0 and b - a >= 4000  # one u32 list entry per word
+    h = ctypes.c_void_p()
+    assert lib.qsgs_batch_create(0, 10, None, 0, None, ctypes.byref(h)) == Q.QSGS_ERR_INVALID
+    assert lib.qsgs_batch_create(4, 1000, None, a, None, ctypes.byref(h)) == Q.QSGS_ERR_WORKSPACE
+    assert lib.qsgs_batch_create(4, 1000, ctypes.c_void_p(256), a - 1, None,
+                                 ctypes.byref(h)) == Q.QSGS_ERR_WORKSPACE
+    assert lib.qsgs_batch_create(4, 1000, None, a, None, None) == Q.QSGS_ERR_INVALID
+    # interaction scratch: four packed grids (blocked + three per-class
+    # enterable grids) and 256 x 3 thresholds
+    for p in (workloads.small_64(), dict(workloads.small_64(), nx=70, ny=33, nz=29)):
+        words = ((p["nx"] + 31) // 32) * p["ny"] * p["nz"]
+        assert lib.qsgs_interaction_bytes(ctypes.byref(Q.make_params(p))) == 16 * words + 3072
+    bad = Q.make_params(dict(workloads.small_64(), cd=2.0))
+    assert lib.qsgs_interaction_bytes(ctypes.byref(bad)) == 0
