@@ -210,8 +210,8 @@ __device__ __forceinline__ uint32_t seed_bits(const Geom& g, uint32_t w,
 
 // The candidate bits of every word, written into the occupancy grid (empty
 // until the seeds are placed): a grid-stride pass, one word per thread and
-// iteration, so the Philox work runs at full occupancy and outside the
-// ordered scan that lists the candidates.
+// iteration, so the Philox work runs with many resident warps and outside
+// the ordered scan that lists the candidates.
 __global__ void __launch_bounds__(256) k_seed_bits(Geom g, const RunState* st, uint32_t* grid,
                                                   const PhiloxKeys keys) {
   const unsigned long long t_seed = st->t_seed;
