@@ -31,6 +31,7 @@ class Request:
     finished: float | None = None
     stats: Q.Stats | None = None
     result: object | None = None        # pinned host uint8 tensor (nz, ny, nx)
+    rejected: str | None = None         # why it can never be admitted
     gen: Q.Generator | None = field(default=None, repr=False)
 
     @property
@@ -61,6 +62,14 @@ class Server:
         self.rounds = 0
 
     # -- admission ----------------------------------------------------------
+    def _never_fits(self, r: Request) -> str | None:
+        """Why the request cannot be admitted even into an empty server."""
+        if Q.word_count(r.params) > self.max_words:
+            return "more grid words than the batch word space"
+        if Q.qsgs_workspace_bytes(r.params) > self.hbm_budget:
+            return "workspace larger than the memory budget"
+        return None
+
     def _fits(self, r: Request, n_members: int) -> bool:
         need = Q.qsgs_workspace_bytes(r.params)
         return (n_members < self.max_members and
@@ -93,8 +102,12 @@ class Server:
     # -- main loop ----------------------------------------------------------
     def serve(self, requests: list[Request], timeout_s: float = 600.0) -> list[Request]:
         """Runs until every request is finished; arrivals are honoured in
-        real time (requests are not admitted before their arrival)."""
-        pending = sorted(requests, key=lambda r: r.arrival)
+        real time (requests are not admitted before their arrival).  A
+        request that could not be admitted even into an empty server is
+        marked ``rejected`` at once instead of holding up the queue."""
+        for r in requests:
+            r.rejected = self._never_fits(r)
+        pending = sorted((r for r in requests if r.rejected is None), key=lambda r: r.arrival)
         running: list[Request] = []
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0  # noqa: E731
@@ -135,14 +148,20 @@ class Server:
 
 
 def summarize(requests: list[Request], wall_s: float | None = None) -> dict:
-    """p50 / p99 latency, throughput in requests/s and nodes/s."""
+    """p50 / p99 latency, throughput in requests/s and nodes/s of the
+    finished requests (rejected ones are counted apart)."""
     import numpy as np
-    lat = np.array([r.latency for r in requests if r.latency is not None])
-    fin = max(r.finished for r in requests if r.finished is not None)
-    start = min(r.arrival for r in requests)
+    done = [r for r in requests if r.finished is not None]
+    lat = np.array([r.latency for r in done])
+    fin = max(r.finished for r in done)
+    start = min(r.arrival for r in done)
     span = wall_s if wall_s is not None else fin - start
-    voxels = sum(r.voxels for r in requests)
-    return {"requests": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "span_s": span, "requests_per_s": len(requests) / span,
-            "nodes_per_s": voxels / span}
+    voxels = sum(r.voxels for r in done)
+    out = {"requests": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+           "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+           "span_s": span, "requests_per_s": len(done) / span,
+           "nodes_per_s": voxels / span}
+    rejected = sum(1 for r in requests if r.rejected is not None)
+    if rejected:
+        out["rejected"] = rejected
+    return out
