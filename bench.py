@@ -33,26 +33,31 @@ from paper_2602_11734_gb300 import workloads  # noqa: E402
 METRIC = "nodes/s"
 WORKLOAD = "single_400"
 L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2: written between timed steps
-CPU_SAMPLE_EDGE = 160            # oracle sample: same parameters on a 160^3 box
 REF_SAMPLE_EDGE = 112            # --impl reference: per-step oracle sample
 PEAK_PROBE_BLOCKS = 1 << 34      # Philox blocks timed by the Philox-only probe
-# Issue-bound ALU peak of the growth kernel's work unit: each SM has four
-# warp schedulers issuing one warp-instruction (32 lanes) per clock, and a
-# Philox4x32-10 block is at least 40 lane-instructions (ten rounds of two
-# 32x32->64 multiplies and two three-input XORs), so the ceiling is
-# SMs x 4 x clock x 32 / 40 blocks per second (152 SMs at 2070 MHz:
-# 1.007e12 blocks/s).
-SCHEDULERS_PER_SM = 4
-PHILOX_BLOCK_INSTRUCTIONS = 40
+# ALU peak of the growth kernel's work unit.  A Philox4x32-10 block is ten
+# rounds of two 32x32->64 products, i.e. 40 32-bit multiply results (low and
+# high halves), and an SM retires 64 32-bit integer multiplies per clock (the
+# CUDA C++ Programming Guide's arithmetic-throughput table; 16 per clock in
+# each of the 4 SM sub-partitions), so the ceiling is SMs x 64 x clock / 40
+# blocks per second: 503.4 G blocks/s on 152 SMs at 2070 MHz.
+INT_MULS_PER_SM_CLOCK = 64
+PHILOX_BLOCK_MULS = 40
 DEFAULT_SM_MHZ = 2070.0           # maximum SM clock of a GB300
-# DRAM bytes (read + write) per k_grow launch of the 400^3 realization, from
-# an ncu capture of a 160^3 run (65.1 MB over its 56 launches and 1.024e8
-# Philox blocks) scaled by Philox blocks to the 1.569e9 blocks of the 400^3
-# run; to be reset to None whenever the kernel changes.
-K_GROW_TRAFFIC_BYTES = 17.8e6
-# L2 load of the same kernel: lts__throughput of its mid-run launches (ncu
-# --set full, launches 31-32 of the 400^3 run); reset to None with the above.
-K_GROW_L2_PCT = 10.7
+# L2 probes: a 32 MiB buffer (resident in the 129 MB L2) read 64 times, and
+# 2^30 scattered atomicOr reductions into the same buffer.
+L2_PROBE_BYTES = 32 << 20
+L2_PROBE_PASSES = 64
+L2_PROBE_ATOMICS = 1 << 30
+# Algorithmic bytes of one growth step (the per-step byte model of the
+# method): read the front list (4 B per front voxel), gather its 3 x 3
+# neighbour rows (36 B), one atomicOr per claim (4 B per claimed voxel),
+# the prune test of the old front and the claimed voxels (36 B each) and
+# the write of the next front (4 B per voxel of it).
+BYTES_PER_FRONT_VOXEL = 4 + 36 + 36
+BYTES_PER_CLAIM = 4 + 36
+BYTES_PER_NEXT_FRONT_VOXEL = 4
+CPU_BASELINE_TIMEOUT_S = 900
 
 
 def parse():
@@ -191,16 +196,50 @@ def summarize_clocks(rows, begin: float, end: float):
             "reasons": reasons, "samples": len(sm), "samples_in_region": len(inside)}
 
 
-def cpu_baseline(edge: int):
-    from oracle import oracle as O
-    p = dict(workloads.single_400(), nx=edge, ny=edge, nz=edge)
-    O.lib()
-    t0 = time.perf_counter()
-    O.run(p)
-    dt = time.perf_counter() - t0
-    return {"value": edge**3 / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"one full realization of the 400^3 parameters on a {edge}^3 box "
-                      f"({dt:.1f} s, single-threaded C oracle)"}
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def start_cpu_baseline(p: dict):
+    """Times the CPU oracle on one full realization of ``p`` in a child
+    process (one thread), started before the GPU work so that both run side
+    by side; ``finish_cpu_baseline`` collects it."""
+    code = ("import json, sys, time; sys.path.insert(0, %r)\n"
+            "from oracle import oracle as O\n"
+            "p = json.loads(%r)\n"
+            "O.lib()\n"
+            "t0 = time.perf_counter(); r = O.run(p); dt = time.perf_counter() - t0\n"
+            "print(json.dumps({'seconds': dt, 'solid': int(r.solid_count), "
+            "'steps': int(r.steps)}))\n") % (ROOT, json.dumps(p))
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True), time.perf_counter()
+
+
+def finish_cpu_baseline(handle, p: dict):
+    proc, t_start = handle
+    left = max(1.0, CPU_BASELINE_TIMEOUT_S - (time.perf_counter() - t_start))
+    n = p["nx"] * p["ny"] * p["nz"]
+    try:
+        out, err = proc.communicate(timeout=left)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
+        return {"value": None, "unit": METRIC, "cores": 1, "host_cores": host_cores(),
+                "kind": "oracle", "sample": f"one full {p['nx']}^3 realization: did not finish "
+                                            f"within {CPU_BASELINE_TIMEOUT_S} s"}
+    if proc.returncode != 0:
+        return {"value": None, "unit": METRIC, "cores": 1, "host_cores": host_cores(),
+                "kind": "oracle", "sample": "oracle failed: " + err.strip()[-200:]}
+    r = json.loads(out.strip().splitlines()[-1])
+    return {"value": n / r["seconds"], "unit": METRIC, "cores": 1, "host_cores": host_cores(),
+            "kind": "oracle",
+            "sample": (f"one full realization of the timed workload itself ({p['nx']}^3, "
+                       f"{r['seconds']:.1f} s, {r['steps']} steps; the single-threaded C "
+                       f"oracle on one of the {host_cores()} host cores, run beside the GPU "
+                       f"legs)")}
 
 
 def run_reference(a):
@@ -529,10 +568,16 @@ def main():
     a.e2e_steps = max(1, a.e2e_steps)
     if a.impl == "reference":
         return run_reference(a)
+    rank, world, local = dist_env()
+    # The CPU baseline (rank 0, one GPU) starts first, as a child process:
+    # the oracle's full realization of the timed workload runs on a host core
+    # while the GPU legs run.
+    cpu_handle = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.serve:
+        cpu_handle = start_cpu_baseline(rank_workload(0, a.edge))
     import torch
     from paper_2602_11734_gb300 import build, qsgs as Q
 
-    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if a.serve:
@@ -603,9 +648,12 @@ def main():
 
     # Kernel-level pass with the library's event profiler (not timed above).
     # k_grow is bound by integer ALU work: one Philox4x32-10 block per
-    # (front voxel, direction block) pair.  Its ceiling is the issue-bound
-    # Philox rate derived from the SM count and clock; the rate the library's
-    # Philox-only probe reaches on this GPU is reported beside it.
+    # (front voxel, direction block) pair.  Its ceiling is the integer
+    # multiply rate derived from the SM count and the sampled clock; the
+    # rate the library's Philox-only probe reaches on this GPU is reported
+    # beside it.  The L2 roof of the method's per-step byte model is set
+    # against the L2 read bandwidth and atomic rate measured by the
+    # library's own probes on this GPU, in this run.
     g.set_profiling(True)
     g.seed()
     st_prof = g.grow()
@@ -616,24 +664,51 @@ def main():
     probe_ms = min(Q.qsgs_bench_philox(PEAK_PROBE_BLOCKS, probe_out.data_ptr(), s.cuda_stream)
                    for _ in range(3))
     probe = PEAK_PROBE_BLOCKS / (probe_ms / 1000.0) / 1e9
+    l2buf = torch.zeros(L2_PROBE_BYTES, dtype=torch.uint8, device=dev)
+    l2_ms = min(Q.qsgs_bench_l2_read(l2buf.data_ptr(), L2_PROBE_BYTES, L2_PROBE_PASSES,
+                                     probe_out.data_ptr(), s.cuda_stream) for _ in range(3))
+    l2_gbs = L2_PROBE_BYTES * L2_PROBE_PASSES / (l2_ms / 1000.0) / 1e9
+    red_ms = min(Q.qsgs_bench_l2_atomic(l2buf.data_ptr(), L2_PROBE_BYTES, L2_PROBE_ATOMICS,
+                                        s.cuda_stream) for _ in range(3))
+    red_gops = L2_PROBE_ATOMICS / (red_ms / 1000.0) / 1e9
+    del l2buf
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or DEFAULT_SM_MHZ
-    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 * 32 / PHILOX_BLOCK_INSTRUCTIONS / 1e9
+    sm_mhz = (clocks or {}).get("sm_mhz") or DEFAULT_SM_MHZ
+    peak = sms * INT_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / PHILOX_BLOCK_MULS / 1e9
     achieved = st_prof.sum_draws / (grow_ms / 1000.0) / 1e9
     pk, pk_kind = peaks()
+    # The method's bytes of all growth steps of the realization: sum_front
+    # is the sum of |A_t|, the claims are the voxels grown (solid - seeds),
+    # and the next fronts sum to about the same as the fronts.
+    claims = st_prof.solid_count - st_prof.n_seeds
+    step_bytes = ((BYTES_PER_FRONT_VOXEL + BYTES_PER_NEXT_FRONT_VOXEL) * st_prof.sum_front
+                  + BYTES_PER_CLAIM * claims)
+    step_ms = sum(prof[k][1] for k in ("grow", "commit", "step_ctl"))
+    l2_achieved = step_bytes / (step_ms / 1000.0) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gblock/s",
-                "frac": achieved / peak,
-                "traffic": K_GROW_TRAFFIC_BYTES if a.edge == 400 else None, "kernel": "k_grow",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_grow",
                 "work": "Philox4x32-10 blocks drawn per second",
-                "peak_kind": (f"derived: {sms} SMs x {SCHEDULERS_PER_SM} warp schedulers x "
-                              f"{sm_mhz:.0f} MHz x 32 lanes / {PHILOX_BLOCK_INSTRUCTIONS} "
-                              f"instructions per Philox4x32-10 block (issue bound)"),
+                "peak_kind": (f"derived: {sms} SMs x {INT_MULS_PER_SM_CLOCK} 32-bit integer "
+                              f"multiplies per SM clock x {sm_mhz:.0f} MHz (sampled) / "
+                              f"{PHILOX_BLOCK_MULS} multiplies per Philox4x32-10 block"),
                 "probe": {"value": probe, "unit": "Gblock/s", "frac": achieved / probe,
+                          "frac_of_peak": probe / peak,
                           "what": "qsgs_bench_philox: Philox4x32-10 alone on this GPU"},
                 "draws": st_prof.sum_draws, "launches": grow_launches,
                 "mean_launch_ms": grow_ms / max(1, grow_launches),
                 "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
-                "l2_throughput_pct": K_GROW_L2_PCT if a.edge == 400 else None,
+                "l2": {"bound": "l2", "unit": "GB/s",
+                       "algorithmic_bytes": step_bytes,
+                       "bytes_model": (f"{BYTES_PER_FRONT_VOXEL + BYTES_PER_NEXT_FRONT_VOXEL} B "
+                                       f"per front voxel-step + {BYTES_PER_CLAIM} B per claim"),
+                       "step_ms": step_ms, "achieved": l2_achieved, "peak": l2_gbs,
+                       "frac": l2_achieved / l2_gbs,
+                       "frac_of_hbm": l2_achieved / pk["hbm_gbs"],
+                       "peak_kind": (f"measured in this run: qsgs_bench_l2_read, "
+                                     f"{L2_PROBE_BYTES >> 20} MiB x {L2_PROBE_PASSES} passes"),
+                       "atomic_peak_gops": red_gops,
+                       "claims_per_s": claims / (grow_ms / 1000.0) / 1e9,
+                       "frac_atomic": claims / (grow_ms / 1000.0) / 1e9 / red_gops},
                 "phases_ms": {k: round(v[1], 4) for k, v in prof.items()}}
     growth_ms = sum(prof[k][1] for k in ("grow", "commit", "step_ctl", "epilogue"))
     rates = {"growth_only_nodes_per_s": n_vox / (growth_ms / 1000.0),
@@ -662,8 +737,8 @@ def main():
            "h2d_bytes_per_step": ctypes.sizeof(Q.QsgsParams), "d2h_bytes_per_step": n_vox}
 
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(CPU_SAMPLE_EDGE)
+    if cpu_handle is not None:
+        cpu = finish_cpu_baseline(cpu_handle, p)
     batched = served = sweep = sizes = fullfield = fontainebleau = phases = None
     del g
     if not a.no_phases and a.edge == 400:

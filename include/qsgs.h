@@ -226,6 +226,34 @@ int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries);
  * Blocks until done.  Returns QSGS_OK, QSGS_ERR_INVALID or QSGS_ERR_CUDA. */
 int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, double* ms);
 
+/* Calibration probes of the L2 roof (no counterpart in the paper).  The
+ * growth step reads neighbour words of an L2-resident bit grid and claims
+ * voxels with fire-and-forget atomicOr; these two kernels measure what the
+ * L2 itself sustains for that kind of traffic on this GPU, so a step's
+ * bytes and claims can be set against a measured peak.
+ *
+ * qsgs_bench_l2_read: reads the whole buffer `passes` times with 16-byte
+ * loads that bypass L1 (each pass shifts every thread to other elements),
+ * after one untimed pass that brings it into L2.
+ *   dev_buf   device, read only, 16-byte aligned; bytes a multiple of 16,
+ *             at least 64 bytes per probe thread (4 blocks of 512 threads
+ *             per SM: 19.9 MB on 152 SMs) and below 64 GiB; pick it well
+ *             below the L2 size (129 MB) to stay resident
+ *   dev_out   device, 8 bytes, 8-byte aligned: receives a checksum
+ *   ms        host: elapsed milliseconds of the timed passes
+ *             (bytes read = bytes * passes)
+ * qsgs_bench_l2_atomic: n_ops atomicOr reductions (no value returned) to
+ * scattered words of the buffer, after an untimed warm-up.
+ *   dev_buf   device, 4-byte aligned, bytes / 4 words (< 2^32); its
+ *             contents are overwritten
+ *   ms        host: elapsed milliseconds scaled to n_ops reductions
+ * Both block until done and return QSGS_OK, QSGS_ERR_INVALID or
+ * QSGS_ERR_CUDA. */
+int qsgs_bench_l2_read(const void* dev_buf, size_t bytes, uint32_t passes, void* dev_out,
+                       void* cuda_stream, double* ms);
+int qsgs_bench_l2_atomic(void* dev_buf, size_t bytes, uint64_t n_ops, void* cuda_stream,
+                         double* ms);
+
 /* Releases the handle (host memory only).  NULL is ignored. */
 void qsgs_destroy(qsgs_handle* h);
 
@@ -333,26 +361,28 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
  * run) of a grid in the library's packed layout: bit x of word
  * (z * ny + y) * ceil(nx / 32) + x / 32, pad bits zero.
  *
- * For callers that may not allocate device memory: code inside a stream
- * capture or a pool-only allocator region (cudaMalloc would break the
- * capture or bypass the pool), or a real-time path where an allocation may
- * block or fail.  The call uses 64 KiB of scratch that lives in the
- * library's own device image (a static __device__ array) and allocates
- * nothing, on the device or the host.
+ * For callers that may not allocate device memory: code that runs under a
+ * pool-only allocator (a framework that owns all device memory, where a
+ * stray cudaMalloc would bypass its accounting or fail once the pool holds
+ * the device), or a real-time path where an allocation may block or fail.
+ * The call uses 64 KiB of scratch that lives in the library's own device
+ * image (a static __device__ array, held by every device that loads the
+ * library until the process exits) and allocates nothing, on the device or
+ * the host.
  *   dev_grid     device, read only, ceil(nx/32) * ny * nz words
  *   nx, ny, nz   grid size (nx * ny * nz < 2^32)
  *   cuda_stream  stream to run on (NULL = legacy default stream)
  *   front_out    host: receives the count
- * Limit: at most 16,707,584 words (e.g. 800^3 fits, 1024^3 does not);
- * larger grids return QSGS_ERR_WORKSPACE before touching the device.
- * The first call on a device looks up the scratch address (this may load
- * the library's device code), so make it before any stream capture.  Each
- * call zeroes the scratch it uses (run state and tile status words) on the
- * stream before the count.  Calls share the one scratch per device:
- * overlapping calls (other streams or host threads) race and must be
- * serialised by the caller.  Blocks until the count is in *front_out.
- * Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE, QSGS_ERR_TIMEOUT or
- * QSGS_ERR_CUDA. */
+ * Limit: at most 16,707,584 words (e.g. 800^3 or 32 x 4096 x 4079 fit,
+ * 1024^3 does not); larger grids return QSGS_ERR_WORKSPACE before touching
+ * the device.  The first call on a device looks up the scratch address
+ * (this may load the library's device code).  Each call zeroes the scratch
+ * it uses (run state and tile status words) on the stream before the count.
+ * Calls share the one scratch per device: overlapping calls (other streams
+ * or host threads) race and must be serialised by the caller.  The call
+ * copies the count to the host and synchronises cuda_stream before it
+ * returns.  Returns QSGS_OK, QSGS_ERR_INVALID, QSGS_ERR_WORKSPACE,
+ * QSGS_ERR_TIMEOUT or QSGS_ERR_CUDA. */
 int qsgs_front_count_static(const uint32_t* dev_grid, uint32_t nx, uint32_t ny, uint32_t nz,
                             void* cuda_stream, uint64_t* front_out);
 

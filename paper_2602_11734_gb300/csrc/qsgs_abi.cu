@@ -405,6 +405,26 @@ int batch_fail(qsgs_batch* b, cudaError_t e) {
 
 }  // namespace
 
+namespace {
+
+// Times `fn` (which enqueues one probe launch on s) between two events.
+template <class F>
+int time_probe(cudaStream_t s, F fn, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return e == cudaSuccess ? QSGS_OK : QSGS_ERR_CUDA;
+}
+
+}  // namespace
+
 extern "C" {
 
 int qsgs_version(void) { return 100; }
@@ -670,6 +690,50 @@ int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, doubl
   if (b) cudaEventDestroy(b);
   if (e != cudaSuccess) return QSGS_ERR_CUDA;
   *ms = (double)t * (double)n_blocks / (double)(threads * per);  // scaled to n_blocks
+  return QSGS_OK;
+}
+
+int qsgs_bench_l2_read(const void* dev_buf, size_t bytes, uint32_t passes, void* dev_out,
+                       void* cuda_stream, double* ms) {
+  if (!dev_buf || !dev_out || !ms || passes == 0 || bytes % 16 ||
+      (reinterpret_cast<uintptr_t>(dev_buf) % 16) || (reinterpret_cast<uintptr_t>(dev_out) % 8))
+    return QSGS_ERR_INVALID;
+  const uint64_t n16 = bytes / 16;
+  if (n16 < 4ull * l2_read_threads() || n16 >= (1ull << 32)) return QSGS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long* out = static_cast<unsigned long long*>(dev_out);
+  // One untimed pass brings the buffer into L2.
+  cudaError_t e = launch_l2_read(dev_buf, n16, 1, out, s);
+  if (e != cudaSuccess) return QSGS_ERR_CUDA;
+  float t = 0.f;
+  const int rc = time_probe(s, [&] { return launch_l2_read(dev_buf, n16, passes, out, s); }, &t);
+  if (rc != QSGS_OK) return rc;
+  *ms = t;
+  return QSGS_OK;
+}
+
+int qsgs_bench_l2_atomic(void* dev_buf, size_t bytes, uint64_t n_ops, void* cuda_stream,
+                         double* ms) {
+  if (!dev_buf || !ms || n_ops == 0 || bytes < 4 || (reinterpret_cast<uintptr_t>(dev_buf) % 4))
+    return QSGS_ERR_INVALID;
+  const uint64_t nwords = bytes / 4;
+  if (nwords >= (1ull << 32)) return QSGS_ERR_INVALID;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return QSGS_ERR_CUDA;
+  const uint32_t blocks = (uint32_t)sms * 4u;
+  const uint64_t threads = (uint64_t)blocks * 512u;
+  const uint64_t per = (n_ops + threads - 1) / threads;
+  if (per > 0xFFFFFFFFull) return QSGS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = launch_l2_red(dev_buf, nwords, 4, blocks, s);  // untimed warm-up
+  if (e != cudaSuccess) return QSGS_ERR_CUDA;
+  float t = 0.f;
+  const int rc = time_probe(
+      s, [&] { return launch_l2_red(dev_buf, nwords, (uint32_t)per, blocks, s); }, &t);
+  if (rc != QSGS_OK) return rc;
+  *ms = (double)t * (double)n_ops / (double)(threads * per);  // scaled to n_ops
   return QSGS_OK;
 }
 

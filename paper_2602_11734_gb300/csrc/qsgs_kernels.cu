@@ -241,8 +241,20 @@ struct SeedCompactPolicy {
     return Item{w, valid ? grid[w] : 0u, 0u};
   }
   __device__ uint32_t count(const Item& it) const { return __popc(it.bits); }
+  // The word that straddles the capacity emits only its lowest (cap - off)
+  // candidates, so the list holds exactly the first cap candidates.
   __device__ void emit(const Item& it, unsigned long long off) const {
-    if (off + __popc(it.bits) <= cap) emit_word_bits(g, it, cand, off);
+    if (off >= cap) return;
+    Item keep = it;
+    if (off + __popc(it.bits) > cap) {
+      uint32_t b = it.bits, low = 0;
+      for (unsigned long long k = off; k < cap; ++k) {
+        low |= b & (0u - b);  // lowest remaining candidate bit
+        b &= b - 1;
+      }
+      keep.bits = low;
+    }
+    emit_word_bits(g, keep, cand, off);
   }
   // More candidates than the workspace holds (probability < 1e-15): the run
   // reports an overflow and keeps going on the first cap candidates.
@@ -1605,6 +1617,80 @@ __global__ void __launch_bounds__(256) k_philox_rate(PhiloxKeys keys, uint32_t p
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
                                unsigned long long* out, cudaStream_t s) {
   k_philox_rate<<<blocks, 256, 0, s>>>(make_philox_keys(seed), per_thread, out);
+  return cudaGetLastError();
+}
+
+static int num_sms();
+
+// ---------------------------------------------------------------------------
+// L2 probes: the roof the growth step's gathers and claims would hit if the
+// L2 bound it.  k_l2_read streams an L2-resident buffer `passes` times with
+// 16-byte loads that bypass L1 (ld.global.cg), each pass starting every
+// thread at a different 16-byte element so no SM re-reads its own lines;
+// k_l2_red issues fire-and-forget atomicOr (reductions without a return
+// value, the claims' kind) to scattered words of an L2-resident buffer.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_l2_read(const uint4* __restrict__ buf, uint32_t n16,
+                                                 uint32_t passes, unsigned long long* out) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  uint32_t acc = 0;
+  for (uint32_t p = 0; p < passes; ++p) {
+    // Pass p shifts every thread by p * 4099 elements (mod n16): the
+    // elements a thread reads change from pass to pass.
+    uint32_t i = (uint32_t)(((unsigned long long)tid + (unsigned long long)p * 4099u) % n16);
+    uint32_t k = tid;
+    // Four independent loads per iteration keep enough bytes in flight.  The
+    // launcher guarantees n16 >= 4 * nthreads, so i stays below n16 with one
+    // conditional subtraction per step.
+    for (; k + 3u * nthreads < n16; k += 4u * nthreads) {
+      uint32_t i1 = i + nthreads, i2 = i + 2u * nthreads, i3 = i + 3u * nthreads;
+      i1 = i1 >= n16 ? i1 - n16 : i1;
+      i2 = i2 >= n16 ? i2 - n16 : i2;
+      i3 = i3 >= n16 ? i3 - n16 : i3;
+      const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i1), c = __ldcg(buf + i2),
+                  d = __ldcg(buf + i3);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^
+             d.z ^ d.w;
+      i += 4u * nthreads;
+      i = i >= n16 ? i - n16 : i;
+    }
+    for (; k < n16; k += nthreads) {
+      const uint4 a = __ldcg(buf + i);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w;
+      i += nthreads;
+      i = i >= n16 ? i - n16 : i;
+    }
+  }
+  const uint32_t wsum = __reduce_add_sync(0xffffffffu, acc & 0xFFFFu);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, (unsigned long long)wsum);
+}
+
+__global__ void __launch_bounds__(512) k_l2_red(uint32_t* buf, uint32_t nwords,
+                                                uint32_t per_thread) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  // A multiplicative walk over the words (odd stride: a permutation mod a
+  // power of two, scattered otherwise): neighbouring lanes hit words far
+  // apart, like claims into a large grid.
+  uint32_t x = tid * 2654435761u;
+  for (uint32_t k = 0; k < per_thread; ++k) {
+    atomicOr(buf + (x % nwords), 1u << (k & 31u));
+    x += 0x9E3779B9u;
+  }
+}
+
+cudaError_t launch_l2_read(const void* buf, uint64_t n16, uint32_t passes,
+                           unsigned long long* out, cudaStream_t s) {
+  const uint32_t blocks = (uint32_t)num_sms() * 4u;
+  k_l2_read<<<blocks, 512, 0, s>>>(static_cast<const uint4*>(buf), (uint32_t)n16, passes, out);
+  return cudaGetLastError();
+}
+
+uint32_t l2_read_threads() { return (uint32_t)num_sms() * 4u * 512u; }
+
+cudaError_t launch_l2_red(void* buf, uint64_t nwords, uint32_t per_thread, uint32_t blocks,
+                          cudaStream_t s) {
+  k_l2_red<<<blocks, 512, 0, s>>>(static_cast<uint32_t*>(buf), (uint32_t)nwords, per_thread);
   return cudaGetLastError();
 }
 

@@ -201,6 +201,14 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowSh
                               int use_cond);
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t blocks, uint32_t per_thread,
                                unsigned long long* out, cudaStream_t s);
+// L2 probes: `passes` reads of n16 16-byte elements through L2 (the grid is
+// 4 blocks of 512 threads per SM; needs n16 >= 4 * that many threads), and
+// blocks x 512 threads issuing per_thread reductions each into nwords words.
+uint32_t l2_read_threads();
+cudaError_t launch_l2_read(const void* buf, uint64_t n16, uint32_t passes,
+                           unsigned long long* out, cudaStream_t s);
+cudaError_t launch_l2_red(void* buf, uint64_t nwords, uint32_t per_thread, uint32_t blocks,
+                          cudaStream_t s);
 // Phase maps: `label` into out[v] for every solid voxel v (other bytes
 // untouched); src words ORed into dst (n words).
 cudaError_t launch_label_u8(const Geom& g, const uint32_t* grid, uint8_t* out, uint8_t label,

@@ -94,6 +94,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.c_int),
                 "qsgs_bench_philox": ([ctypes.c_uint64, vp, vp, ctypes.POINTER(ctypes.c_double)],
                                       ctypes.c_int),
+                "qsgs_bench_l2_read": ([vp, ctypes.c_size_t, ctypes.c_uint32, vp, vp,
+                                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+                "qsgs_bench_l2_atomic": ([vp, ctypes.c_size_t, ctypes.c_uint64, vp,
+                                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
                 "qsgs_destroy": ([H], None),
                 "qsgs_set_grow_blocks": ([H, ctypes.c_uint32], ctypes.c_int),
                 "qsgs_set_grow_tile": ([H, ctypes.c_uint32], ctypes.c_int),
@@ -229,6 +233,28 @@ def qsgs_bench_philox(n_blocks: int, dev_out_ptr: int, stream_ptr: int) -> float
                                           ctypes.c_void_p(stream_ptr), ctypes.byref(ms))
     if rc != QSGS_OK:
         raise QsgsError(rc, "qsgs_bench_philox")
+    return ms.value
+
+
+def qsgs_bench_l2_read(buf_ptr: int, nbytes: int, passes: int, dev_out_ptr: int,
+                       stream_ptr: int) -> float:
+    """Milliseconds for ``passes`` reads of an L2-resident device buffer."""
+    ms = ctypes.c_double()
+    rc = load_library().qsgs_bench_l2_read(ctypes.c_void_p(buf_ptr), nbytes, passes,
+                                           ctypes.c_void_p(dev_out_ptr),
+                                           ctypes.c_void_p(stream_ptr), ctypes.byref(ms))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_bench_l2_read")
+    return ms.value
+
+
+def qsgs_bench_l2_atomic(buf_ptr: int, nbytes: int, n_ops: int, stream_ptr: int) -> float:
+    """Milliseconds for n_ops scattered atomicOr reductions into a device buffer."""
+    ms = ctypes.c_double()
+    rc = load_library().qsgs_bench_l2_atomic(ctypes.c_void_p(buf_ptr), nbytes, n_ops,
+                                             ctypes.c_void_p(stream_ptr), ctypes.byref(ms))
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_bench_l2_atomic")
     return ms.value
 
 

@@ -152,6 +152,10 @@ def summarize(requests: list[Request], wall_s: float | None = None) -> dict:
     finished requests (rejected ones are counted apart)."""
     import numpy as np
     done = [r for r in requests if r.finished is not None]
+    rejected = sum(1 for r in requests if r.rejected is not None)
+    if not done:  # every request rejected (or none finished): no latency to report
+        return {"requests": 0, "rejected": rejected, "p50_ms": None, "p99_ms": None,
+                "mean_ms": None, "span_s": wall_s, "requests_per_s": None, "nodes_per_s": None}
     lat = np.array([r.latency for r in done])
     fin = max(r.finished for r in done)
     start = min(r.arrival for r in done)
@@ -161,7 +165,6 @@ def summarize(requests: list[Request], wall_s: float | None = None) -> dict:
            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
            "span_s": span, "requests_per_s": len(done) / span,
            "nodes_per_s": voxels / span}
-    rejected = sum(1 for r in requests if r.rejected is not None)
     if rejected:
         out["rejected"] = rejected
     return out

@@ -6,6 +6,7 @@ Each line holds the parameters, the summary, the per-step front and claim
 counts, and the SHA-256 of the final phase map as uint8[N] (x fastest).
 
     python tests/golden/make_golden.py small_64 single_400 sweep_500 batch_96 --jobs 6
+    python tests/golden/make_golden.py serve_large --jobs 8
 """
 from __future__ import annotations
 
@@ -28,6 +29,11 @@ SETS = {
     "sweep_500": workloads.sweep_500,
     "batch_96": workloads.batch_96,
     "serve_small": lambda: [p for p in workloads.serve_requests() if p["nx"] <= 128][:40],
+    # The large requests of the serving mix: the first three requests of
+    # each of the edges 256, 400 and 512 among the 2000 (request ids 5, 7,
+    # 15; 12, 20, 28; 14, 23, 34).
+    "serve_large": lambda: [p for e in (256, 400, 512)
+                            for p in [q for q in workloads.serve_requests() if q["nx"] == e][:3]],
 }
 
 

@@ -45,3 +45,24 @@ def statistics_median(xs):
     xs = sorted(xs)
     k = len(xs) // 2
     return xs[k] if len(xs) % 2 else (xs[k - 1] + xs[k]) / 2
+
+
+def test_cpu_baseline_child_times_one_full_oracle_realization():
+    # The oracle runs in a child process on a host core beside the GPU legs;
+    # its rate is voxels per second of one whole realization.
+    p = dict(bench.rank_workload(0, 24))
+    c = bench.finish_cpu_baseline(bench.start_cpu_baseline(p), p)
+    assert c["kind"] == "oracle" and c["cores"] == 1
+    assert c["host_cores"] >= 1
+    assert c["value"] is not None and c["value"] > 0
+    assert "24^3" in c["sample"]
+
+
+def test_step_byte_model_matches_its_definition():
+    # 4 B read + 36 B gather + 36 B prune test per front voxel, 4 B per voxel
+    # of the next front, 4 B atomicOr + 36 B prune test per claim.
+    assert bench.BYTES_PER_FRONT_VOXEL + bench.BYTES_PER_NEXT_FRONT_VOXEL == 80
+    assert bench.BYTES_PER_CLAIM == 40
+    # The derived multiply-rate ceiling on 152 SMs at 2070 MHz.
+    peak = 152 * bench.INT_MULS_PER_SM_CLOCK * 2070e6 / bench.PHILOX_BLOCK_MULS
+    assert abs(peak - 503.4e9) < 0.1e9

@@ -134,3 +134,23 @@ def test_a_request_that_can_never_fit_is_rejected_at_once(monkeypatch, limit):
     assert all(r.rejected is None and r.finished is not None for r in (reqs[0], reqs[2]))
     s = S.summarize(reqs)
     assert s["requests"] == 2 and s["rejected"] == 1
+
+
+def test_summary_when_every_request_is_rejected(monkeypatch):
+    # No finished request: the summary reports the rejections and no
+    # latency or rate instead of failing on an empty set.
+    log = Log()
+    small, big = params(0, 32), params(1, 128)
+    budget = Q.qsgs_workspace_bytes(small)
+    gen_cls, batch_cls = make_fakes(log, 4, 1 << 20, budget)
+    monkeypatch.setattr(Q, "Generator", gen_cls)
+    monkeypatch.setattr(Q, "Batch", batch_cls)
+    srv = S.Server(device="cuda:0", max_members=4, max_words=1 << 20, hbm_budget=budget,
+                   step_quantum=2, keep_results=False)
+    reqs = [S.Request(rid=i, params=dict(big, seed=i), arrival=0.0) for i in range(3)]
+    srv.serve(reqs, timeout_s=5.0)
+    assert all(r.rejected and r.finished is None for r in reqs)
+    assert log.rounds == []
+    s = S.summarize(reqs)
+    assert s["requests"] == 0 and s["rejected"] == 3
+    assert s["p50_ms"] is None and s["p99_ms"] is None and s["requests_per_s"] is None

@@ -76,6 +76,35 @@ def test_static_front_count_mid_run_and_default_stream(Q):
         g.close()
 
 
+# The stated limit of the static scratch: 16,707,584 words.  A grid of
+# 32 x 4096 x 4079 voxels (one word per row) has exactly that many.
+LIMIT_WORDS = 16_707_584
+
+
+def test_static_front_count_at_its_word_limit(Q):
+    # The largest grid the scratch serves: the count must use the tile
+    # status words up to the end of the static array, and still equal the
+    # front the generator reports, on two calls in a row; one plane more is
+    # refused before the device is touched.
+    p = dict(workloads.small_64(), nx=32, ny=4096, nz=4079, cd=0.002, seed=77)
+    assert (p["nx"] + 31) // 32 * p["ny"] * p["nz"] == LIMIT_WORDS
+    g = Q.Generator(p)
+    try:
+        g.seed()
+        st = g.grow()
+        assert st.status == Q.QSGS_OK
+        grid = g.fetch(fmt="packed")
+        torch.cuda.synchronize()
+        assert grid.numel() == LIMIT_WORDS
+        assert _count(Q, grid, p, g.stream.cuda_stream) == (Q.QSGS_OK, st.front_size)
+        assert _count(Q, grid, p) == (Q.QSGS_OK, st.front_size)
+        assert st.front_size > 0
+        over = dict(p, nz=p["nz"] + 1)
+        assert _count(Q, grid, over)[0] == Q.QSGS_ERR_WORKSPACE
+    finally:
+        g.close()
+
+
 def test_static_front_count_rejects_oversized_grids(Q):
     small = torch.zeros(4, dtype=torch.int32, device="cuda")
     # 1024^3 needs 34,603,008 words: more than the static scratch serves.
