@@ -205,6 +205,44 @@ int qsgs_fetch(qsgs_handle* h, void* dst, size_t bytes, int fmt, int dst_is_devi
  * QSGS_ERR_WORKSPACE (more seed candidates than the workspace holds). */
 int qsgs_query(qsgs_handle* h, qsgs_stats* out);
 
+/* Checkpoint and resume of a realization (Sec. 2.3, Algorithm 3: what one
+ * growth step carries to the next is the phase array, the active front, the
+ * step counter t and the solid count c_t; the front is a function of the
+ * phase array, and every draw is keyed by (seed, voxel, t, direction), so a
+ * realization resumed from a snapshot takes exactly the steps it would
+ * have taken uninterrupted).
+ *
+ * qsgs_snapshot_bytes: bytes of a snapshot of a realization with these
+ * params (256-byte header, 256-byte run state, the packed grid: 512 + 4
+ * nz ny ceil(nx/32)), or 0 if the params are invalid.  Host only.
+ *
+ * qsgs_snapshot: writes the realization's state between growth calls --
+ * after qsgs_seed, or after a qsgs_grow_until that returned any status --
+ * into dst.
+ *   dst        host or device buffer of >= qsgs_snapshot_bytes bytes, owned
+ *              by the caller; dst_kind is QSGS_DST_HOST, QSGS_DST_DEVICE or
+ *              QSGS_DST_HOST_MAPPED (written like QSGS_DST_HOST)
+ * Blocks until the snapshot is complete.  Returns QSGS_OK, QSGS_ERR_INVALID
+ * (argument, size or kind), QSGS_ERR_STATE (not seeded, or a batch member
+ * whose exact-target trim is still pending: call qsgs_batch_query first),
+ * QSGS_ERR_TIMEOUT / QSGS_ERR_WORKSPACE (the run already failed) or
+ * QSGS_ERR_CUDA.
+ *
+ * qsgs_restore: makes the handle continue the snapshotted realization.
+ *   src        host or device buffer written by qsgs_snapshot; src_kind as
+ *              dst_kind above; read during the call only
+ * The handle must have been created with the same params (every field
+ * equal); its earlier state, if any, is replaced.  Cells of earlier phases
+ * and interactions (qsgs_set_blocked, qsgs_set_interaction) are not part of
+ * a snapshot: set them on the handle as for the original run, before the
+ * restore.  The next qsgs_grow_until (alone or in a batch) rebuilds the
+ * candidate list from the grid first.  Blocks.  Returns QSGS_OK,
+ * QSGS_ERR_INVALID (argument, size, kind, or a buffer that is not a
+ * snapshot of a realization with these params) or QSGS_ERR_CUDA. */
+size_t qsgs_snapshot_bytes(const qsgs_params* params);
+int qsgs_snapshot(qsgs_handle* h, void* dst, size_t bytes, int dst_kind);
+int qsgs_restore(qsgs_handle* h, const void* src, size_t bytes, int src_kind);
+
 /* Turns the event profiler on (enable != 0) or off and clears its totals.
  * While on, every kernel launch of the handle is bracketed by CUDA events
  * on its stream; totals are collected at each host synchronisation.  Adds

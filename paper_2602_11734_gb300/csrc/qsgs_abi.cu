@@ -103,7 +103,7 @@ Layout make_layout(const qsgs_params* p) {
   L.scan_status = off; off = align_up(off + L.ntiles * sizeof(unsigned long long));
   L.grid = off; off = align_up(off + nwords * 4);
   L.aux = off; off = align_up(off + 2 * nwords * 4);  // claim grids of even / odd steps
-  L.mark = off; off = align_up(off + (nwords / 32 + 1) * 4);
+  L.mark = off; off = align_up(off + 2 * (nwords / 32 + 1) * 4);  // marks, touched bits
   // Seed candidates (at most cand_cap), then the candidate word list (at
   // most nwords); u32 entries.
   L.list_bytes = (L.cand_cap > nwords ? L.cand_cap : nwords) * 4;
@@ -215,7 +215,7 @@ int seed_on_stream(qsgs_handle* h, cudaStream_t stream) {
   const size_t grids = (size_t)h->g.nwords * 4;
   cudaError_t e = cudaMemsetAsync(h->grid, 0, grids, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->mark, 0, (h->g.nwords / 32 + 1) * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->mark, 0, 2 * (size_t)bitmap_words(h->g) * 4, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   StateInit init{};
   init.nt = h->ints.nt;
@@ -407,6 +407,41 @@ int batch_fail(qsgs_batch* b, cudaError_t e) {
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// Snapshots: [0, 256) header, [256, 512) the run state, then the packed
+// grid (4 nwords bytes).
+// ---------------------------------------------------------------------------
+constexpr char kSnapMagic[8] = {'Q', 'S', 'G', 'S', 'S', 'N', 'P', '1'};
+constexpr uint32_t kSnapVersion = 1;
+constexpr size_t kSnapHeader = 256;
+constexpr size_t kSnapState = kSnapHeader + sizeof(RunState);
+
+struct SnapHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t nwords;
+  uint64_t total_bytes;
+  qsgs_params params;
+};
+static_assert(sizeof(SnapHeader) <= kSnapHeader, "snapshot header fits its slot");
+static_assert(sizeof(RunState) == 256, "run state slot");
+
+size_t snapshot_bytes(const Geom& g) { return kSnapState + (size_t)g.nwords * 4; }
+
+// The generation parameters two handles must share for a snapshot of one
+// to continue on the other (compared field by field: no padding bytes).
+bool same_params(const qsgs_params& a, const qsgs_params& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.cd == b.cd && a.g_face == b.g_face &&
+         a.g_edge == b.g_edge && a.g_corner == b.g_corner && a.spacing_s == b.spacing_s &&
+         a.target_solid_fraction == b.target_solid_fraction && a.target_count == b.target_count &&
+         a.seed == b.seed && a.max_steps == b.max_steps && a.periodic == b.periodic;
+}
+
+cudaMemcpyKind copy_kind(int kind, bool to_device_buffer) {
+  if (kind == QSGS_DST_DEVICE) return cudaMemcpyDeviceToDevice;
+  return to_device_buffer ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+}
+
 // Times `fn` (which enqueues one probe launch on s) between two events.
 template <class F>
 int time_probe(cudaStream_t s, F fn, float* ms) {
@@ -557,8 +592,12 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
     h->tracer.launches += 3ull * (s.iters - h->iters_seen) + 4ull;
     h->iters_seen = s.iters;
   } else {
+    // At most kStepsPerSync steps between host checks, and no more than
+    // the call's budget (a step that is not active returns at once, but is
+    // still a launch the profiler would time).
+    const uint32_t burst = max_steps && max_steps < kStepsPerSync ? max_steps : kStepsPerSync;
     for (;;) {
-      for (uint32_t k = 0; k < kStepsPerSync; ++k) {
+      for (uint32_t k = 0; k < burst; ++k) {
         e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, GrowShape{h->grow_blocks, h->grow_tile},
                         h->stream, h->tracer, (cudaGraphConditionalHandle)0, 0,
                         h->mode == QSGS_MODE_FULLFIELD);
@@ -690,6 +729,107 @@ int qsgs_bench_philox(uint64_t n_blocks, void* dev_out, void* cuda_stream, doubl
   if (b) cudaEventDestroy(b);
   if (e != cudaSuccess) return QSGS_ERR_CUDA;
   *ms = (double)t * (double)n_blocks / (double)(threads * per);  // scaled to n_blocks
+  return QSGS_OK;
+}
+
+size_t qsgs_snapshot_bytes(const qsgs_params* params) {
+  Ints ints{};
+  if (check_params(params, &ints) != QSGS_OK) return 0;
+  return snapshot_bytes(make_geom(params->nx, params->ny, params->nz, params->periodic));
+}
+
+int qsgs_snapshot(qsgs_handle* h, void* dst, size_t bytes, int dst_kind) {
+  if (!h || !dst) return QSGS_ERR_INVALID;
+  if (dst_kind != QSGS_DST_HOST && dst_kind != QSGS_DST_DEVICE &&
+      dst_kind != QSGS_DST_HOST_MAPPED)
+    return QSGS_ERR_INVALID;
+  const size_t need = snapshot_bytes(h->g);
+  if (bytes < need) return QSGS_ERR_INVALID;
+  if (!h->seeded) return QSGS_ERR_STATE;
+  RunState s{};
+  const int rc = read_state(h, &s);  // synchronises: the step is closed
+  if (rc != QSGS_OK) return rc;
+  // Between calls the exact-target trim has run (a batch member's only at
+  // qsgs_batch_query); a pending trim needs the claim grid, which a
+  // snapshot does not hold.
+  if (s.trim_pending) return QSGS_ERR_STATE;
+  SnapHeader hd{};
+  std::memcpy(hd.magic, kSnapMagic, sizeof(kSnapMagic));
+  hd.version = kSnapVersion;
+  hd.nwords = h->g.nwords;
+  hd.total_bytes = need;
+  hd.params = h->p;
+  unsigned char head[kSnapState] = {};
+  std::memcpy(head, &hd, sizeof(hd));
+  std::memcpy(head + kSnapHeader, &s, sizeof(s));
+  uint8_t* out = static_cast<uint8_t*>(dst);
+  cudaError_t e = cudaSuccess;
+  if (dst_kind == QSGS_DST_DEVICE)
+    e = cudaMemcpyAsync(out, head, kSnapState, cudaMemcpyHostToDevice, h->stream);
+  else
+    std::memcpy(out, head, kSnapState);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out + kSnapState, h->grid, (size_t)h->g.nwords * 4,
+                        copy_kind(dst_kind, false), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `head` is on this stack
+  return e == cudaSuccess ? QSGS_OK : cuda_fail(h, e);
+}
+
+int qsgs_restore(qsgs_handle* h, const void* src, size_t bytes, int src_kind) {
+  if (!h || !src) return QSGS_ERR_INVALID;
+  if (src_kind != QSGS_DST_HOST && src_kind != QSGS_DST_DEVICE &&
+      src_kind != QSGS_DST_HOST_MAPPED)
+    return QSGS_ERR_INVALID;
+  const size_t need = snapshot_bytes(h->g);
+  if (bytes < need) return QSGS_ERR_INVALID;
+  const uint8_t* in = static_cast<const uint8_t*>(src);
+  unsigned char head[kSnapState];
+  cudaError_t e = cudaSuccess;
+  if (src_kind == QSGS_DST_DEVICE) {
+    e = cudaMemcpyAsync(head, in, kSnapState, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  } else {
+    std::memcpy(head, in, kSnapState);
+  }
+  SnapHeader hd;
+  std::memcpy(&hd, head, sizeof(hd));
+  if (std::memcmp(hd.magic, kSnapMagic, sizeof(kSnapMagic)) != 0 || hd.version != kSnapVersion ||
+      hd.nwords != h->g.nwords || hd.total_bytes != need || !same_params(hd.params, h->p))
+    return QSGS_ERR_INVALID;
+  RunState s;
+  std::memcpy(&s, head + kSnapHeader, sizeof(s));
+  if (s.trim_pending || s.error || s.nt != h->ints.nt) return QSGS_ERR_INVALID;
+  // Everything a step carries over is the grid and these counters; the
+  // transient fields of a step and of the look-back scans start afresh.
+  s.claimed = 0;
+  s.live = 0;
+  s.front_acc = 0;
+  s.active = 0;
+  s.step_limit = 0xFFFFFFFFu;
+  s.scan_tile = 0;
+  s.scan_done = 0;
+  s.grow_next = 0;
+  s.grow_done = 0;
+  s.list_next = 0;
+  s.front_words = 0;
+  const size_t grids = (size_t)h->g.nwords * 4;
+  e = cudaMemcpyAsync(h->grid, in + kSnapState, grids, copy_kind(src_kind, true), h->stream);
+  // Claim grids, marks and touched bits are all zero between steps of a
+  // fresh run; so are the look-back status words before their first use.
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, 2 * grids, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->mark, 0, 2 * (size_t)bitmap_words(h->g) * 4, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->scan_status, 0, h->L.ntiles * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `s` is on this stack
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->seeded = true;
+  h->list_stale = true;  // the candidate list is rebuilt from the grid
+  h->finalized = s.status != kRunning;
+  h->iters_seen = s.iters;
   return QSGS_OK;
 }
 

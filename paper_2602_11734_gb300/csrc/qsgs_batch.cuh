@@ -3,9 +3,9 @@
 // Included at the end of qsgs_kernels.cu (one translation unit): it reuses
 // the growth chunk, the step logic and the look-back scan of the single
 // realization path.  A batch step is three launches for all members
-// together -- growth over the concatenated candidate list, one ordered
-// commit scan over the batch word space, and one control kernel with a
-// thread per member -- so uneven realizations (different sizes, targets,
+// together -- growth over the concatenated candidate list, one commit over
+// the marked and touched words of all members, and one control kernel with
+// a thread per member -- so uneven realizations (different sizes, targets,
 // step counts) advance side by side and each member's result is the one it
 // gets alone: every draw is keyed by the member's own seed, step and voxel.
 #pragma once
@@ -25,43 +25,21 @@ __device__ __forceinline__ uint32_t find_member(const MemberDesc* d, uint32_t n,
   return lo;
 }
 
-// Commit over the batch word space (the work of k_commit, per member).
-// Prologue mode lists every solid word of each running member (a superset
-// of its front, used when the batch starts or its membership changed);
-// step mode ORs the claims of the members that ran a step into their grids,
-// counts them, and lists marked or claimed words.  Member m's list entries
-// (member-local word indices, any order) go to the batch list from
-// word_base(m) on, counted by its run state's list_next.  A warp takes 8
-// consecutive 32-word groups per iteration (all loads first); groups of one
-// member share one atomic per counter.
+// Prologue of a batch advance: lists every solid word of each running
+// member (a superset of its front), used when the batch starts or its
+// membership changed.  Member m's list entries (member-local word indices,
+// any order) go to the batch list from word_base(m) on, counted by its run
+// state's list_next.  A warp takes 8 consecutive 32-word groups per
+// iteration (all loads first); groups of one member share one atomic.
 constexpr int kBatchCommitGroups = 8;
 
 // One 32-word group of member md (the slow path, at member boundaries).
-__device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_t gs, bool valid,
-                                                   uint32_t* list, int prologue) {
+__device__ __forceinline__ void batch_list_group(const MemberDesc& md, uint32_t gs,
+                                                 uint32_t* list) {
   const uint32_t lane = threadIdx.x & 31u;
   RunState* st = md.st;
   const uint32_t w = gs + lane - md.word_base;
-  const bool in = valid && gs + lane < md.word_end;
-  bool keep = false;
-  uint32_t c = 0;
-  if (prologue) {
-    keep = in && st->status == kRunning && md.grid[w] != 0;
-  } else if (st->active) {
-    const uint32_t par = st->t & 1u;
-    uint32_t mk = 0;
-    if (lane == 0 && valid) mk = md.mark[(gs - md.word_base) >> 5];
-    if (in) {
-      c = md.aux[(size_t)par * md.g.nwords + w];
-      const uint32_t old = md.grid[w];
-      if (c) md.grid[w] = old | c;
-    }
-    if (mk) md.mark[(gs - md.word_base) >> 5] = 0;
-    mk = __shfl_sync(0xffffffffu, mk, 0);
-    keep = in && (((mk >> lane) & 1u) || c != 0);
-    const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(c));
-    if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
-  }
+  const bool keep = gs + lane < md.word_end && st->status == kRunning && md.grid[w] != 0;
   const uint32_t bal = __ballot_sync(0xffffffffu, keep);
   uint32_t base = 0;
   if (lane == 0 && bal) base = atomicAdd(&st->list_next, (uint32_t)__popc(bal));
@@ -70,8 +48,7 @@ __device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_
 }
 
 __global__ void __launch_bounds__(256, 2)
-    k_batch_commit(const MemberDesc* __restrict__ d, const BatchState* bs, uint32_t* list,
-                   int prologue) {
+    k_batch_list_solid(const MemberDesc* __restrict__ d, const BatchState* bs, uint32_t* list) {
   constexpr int G = kBatchCommitGroups;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = bs->n_members;
@@ -94,53 +71,155 @@ __global__ void __launch_bounds__(256, 2)
       uint32_t m = m0;
       for (uint32_t gi = g0; gi <= glast; ++gi) {
         while (m + 1 < n && d[m + 1].word_base <= gi * 32u) ++m;  // uniform
-        batch_commit_group(d[m], gi * 32u, true, list, prologue);
+        batch_list_group(d[m], gi * 32u, list);
       }
       continue;
     }
     // Common case: every group of this warp belongs to one member.
     const MemberDesc& md = d[m0];
     RunState* st = md.st;
-    const uint32_t* grid = md.grid;
+    if (st->status != kRunning) continue;
     const uint32_t lw0 = g0 * 32u - md.word_base;  // member-local first word
     const uint32_t nloc = md.word_end - md.word_base;
-    uint32_t bal[G];
-    if (prologue) {
-      if (st->status != kRunning) continue;
-      uint32_t v[G];
+    uint32_t v[G], bal[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const uint32_t w = lw0 + j * 32u + lane;
+      v[j] = (g0 + j <= glast && w < nloc) ? md.grid[w] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) bal[j] = __ballot_sync(0xffffffffu, v[j] != 0);
+    uint32_t total = 0;
+#pragma unroll
+    for (int j = 0; j < G; ++j) total += (uint32_t)__popc(bal[j]);
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(&st->list_next, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      if ((bal[j] >> lane) & 1u) list[md.word_base + base + __popc(bal[j] & lt)] = lw0 + j * 32u + lane;
+      base += (uint32_t)__popc(bal[j]);
+    }
+  }
+}
+
+// Step commit of the batch (the work of k_commit, per member) over the
+// batch word space: a warp takes 8 consecutive 32-word groups per
+// iteration.  When they belong to one member (all but the groups at member
+// boundaries) their loads are issued together and list space is reserved
+// with one atomic; as in k_commit, a member whose step list is under
+// 1/kSparseFraction of its words takes the sparse path (bitmaps first, then
+// only marked or touched words), the others the dense one (everything at
+// once).  Member m's list entries (member-local word indices, any order) go
+// to the batch list from word_base(m) on, counted by its list_next.
+
+// One 32-word group of member md (the slow path, at member boundaries).
+__device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_t gs,
+                                                   uint32_t* list) {
+  const uint32_t lane = threadIdx.x & 31u;
+  RunState* st = md.st;
+  if (!st->active) return;  // uniform
+  const uint32_t w = gs + lane - md.word_base;
+  const bool in = gs + lane < md.word_end;
+  const uint32_t jl = (gs - md.word_base) >> 5;
+  uint32_t* touched = md.mark + bitmap_words(md.g);
+  uint32_t mk = 0;
+  if (lane == 0) {
+    mk = md.mark[jl];
+    const uint32_t tc = touched[jl];
+    if (mk) md.mark[jl] = 0u;
+    if (tc) touched[jl] = 0u;
+  }
+  mk = __shfl_sync(0xffffffffu, mk, 0);
+  const uint32_t* claims = md.aux + (size_t)(st->t & 1u) * md.g.nwords;
+  const uint32_t c = in ? claims[w] : 0u;
+  const uint32_t old = in ? md.grid[w] : 0u;
+  if (c) md.grid[w] = old | c;
+  const bool keep = in && (((mk >> lane) & 1u) || c != 0);  // touched = claimed
+  const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(c));
+  if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
+  const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+  uint32_t base = 0;
+  if (lane == 0 && bal) base = atomicAdd(&st->list_next, (uint32_t)__popc(bal));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) list[md.word_base + base + __popc(bal & ((1u << lane) - 1u))] = w;
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_batch_commit(const MemberDesc* __restrict__ d, const BatchState* bs, uint32_t* list) {
+  constexpr int G = kBatchCommitGroups;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = bs->n_members;
+  if (n == 0) return;
+  const uint32_t ngroups = bs->total_words / 32u;  // member ranges are 32-aligned
+  const uint32_t nsuper = (ngroups + G - 1) / G;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nsuper; sg += nwarps) {
+    const uint32_t g0 = sg * G;
+    const uint32_t glast = min(g0 + G, ngroups) - 1;
+    uint32_t mm = 0;
+    if (lane < 2)
+      mm = find_member(d, n, (lane ? glast : g0) * 32u,
+                       [](const MemberDesc& x) { return x.word_base; });
+    const uint32_t m0 = __shfl_sync(0xffffffffu, mm, 0);
+    const uint32_t m1 = __shfl_sync(0xffffffffu, mm, 1);
+    if (m0 != m1) {
+      uint32_t m = m0;
+      for (uint32_t gi = g0; gi <= glast; ++gi) {
+        while (m + 1 < n && d[m + 1].word_base <= gi * 32u) ++m;  // uniform
+        batch_commit_group(d[m], gi * 32u, list);
+      }
+      continue;
+    }
+    const MemberDesc& md = d[m0];
+    RunState* st = md.st;
+    if (!st->active) continue;
+    const uint32_t nloc = md.word_end - md.word_base;
+    const uint32_t lw0 = g0 * 32u - md.word_base;  // member-local first word
+    uint32_t* touched = md.mark + bitmap_words(md.g);
+    const uint32_t* cur = md.aux + (size_t)(st->t & 1u) * md.g.nwords;
+    const bool sparse = (unsigned long long)st->front_words * kSparseFraction < nloc;
+    const bool jv = lane < (uint32_t)G && g0 + lane <= glast;
+    const uint32_t jl = (lw0 >> 5) + lane;
+    const uint32_t mk = jv ? md.mark[jl] : 0u, tc = jv ? touched[jl] : 0u;
+    uint32_t c[G], old[G], bal[G];
+    if (sparse) {
+      if (mk) md.mark[jl] = 0u;
+      if (tc) touched[jl] = 0u;
+      const uint32_t mt = mk | tc;
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t w = lw0 + j * 32u + lane;
-        v[j] = (g0 + j <= glast && w < nloc) ? grid[w] : 0u;
+        const bool act = (__shfl_sync(0xffffffffu, mt, j) >> lane) & 1u;  // set bits lie below nloc
+        c[j] = act ? cur[w] : 0u;
+        old[j] = act ? md.grid[w] : 0u;
+        bal[j] = __ballot_sync(0xffffffffu, act);
       }
-#pragma unroll
-      for (int j = 0; j < G; ++j) bal[j] = __ballot_sync(0xffffffffu, v[j] != 0);
     } else {
-      if (!st->active) continue;
-      const uint32_t par = st->t & 1u;
-      const uint32_t* cur = md.aux + (size_t)par * md.g.nwords;
-      uint32_t c[G], old[G], mk = 0;
-      if (lane < (uint32_t)G && g0 + lane <= glast) mk = md.mark[(lw0 >> 5) + lane];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t w = lw0 + j * 32u + lane;
         const bool in = g0 + j <= glast && w < nloc;
         c[j] = in ? cur[w] : 0u;
-        old[j] = in ? grid[w] : 0u;
+        old[j] = in ? md.grid[w] : 0u;
       }
-      if (mk) md.mark[(lw0 >> 5) + lane] = 0;
-      uint32_t claims = 0;
+      if (mk) md.mark[jl] = 0u;
+      if (tc) touched[jl] = 0u;
 #pragma unroll
       for (int j = 0; j < G; ++j) {
-        const uint32_t w = lw0 + j * 32u + lane;
-        if (c[j]) md.grid[w] = old[j] | c[j];
-        claims += (uint32_t)__popc(c[j]);
         const uint32_t mkw = __shfl_sync(0xffffffffu, mk, j);
         bal[j] = __ballot_sync(0xffffffffu, ((mkw >> lane) & 1u) || c[j] != 0);
       }
-      const uint32_t wc = __reduce_add_sync(0xffffffffu, claims);
-      if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
     }
+    uint32_t claims = 0;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      if (c[j]) md.grid[lw0 + j * 32u + lane] = old[j] | c[j];
+      claims += (uint32_t)__popc(c[j]);
+    }
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, claims);
+    if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
     uint32_t total = 0;
 #pragma unroll
     for (int j = 0; j < G; ++j) total += (uint32_t)__popc(bal[j]);
@@ -236,7 +315,7 @@ __global__ void __launch_bounds__(kGrowThreads, 3)
                  const uint32_t* __restrict__ list, uint32_t tile) {
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
-  __shared__ uint4 s_thr[kGrowWarps][7];
+  __shared__ uint4 s_thr[kGrowWarps][8];  // seven blocks and a padding row, as in k_grow
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = bs->total_chunks, n = bs->n_members;
   const uint32_t nwarps = gridDim.x * kGrowWarps;

@@ -60,6 +60,14 @@ struct Geom {
   const uint32_t* blocked;  // packed cells of earlier phases (R12), or nullptr
 };
 
+// Word bitmaps: one bit per grid word (bit w & 31 of word w >> 5).  The mark
+// area of a workspace holds two of them: the marks (words that hold front
+// voxels in the current step, set by the growth kernel) and, right after,
+// the touched bits (words that received a claim in the current step).
+__host__ __device__ __forceinline__ uint32_t bitmap_words(const Geom& g) {
+  return (g.nwords >> 5) + 1u;
+}
+
 // The geometry of an interacting phase (R13), passed to that kind's kernels
 // only (so that Geom, which every kernel takes, keeps its size).
 struct GeomInter : Geom {

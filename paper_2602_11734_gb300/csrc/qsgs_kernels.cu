@@ -303,76 +303,122 @@ struct InitialListPolicy {
 };
 
 // Commit of a growth step: ORs the step's claims into the grid, counts them,
-// appends marked or claimed words to the next candidate list and clears the
-// marks (the growth kernel has already cleared the other claim grid).  The
-// list is appended in any order (one atomic per block and tile), so no tile
-// waits on another: the growth step gives the same result for any order of
-// its list, every draw being keyed by (voxel, step, block) and claims ORed.
+// appends marked or touched words to the next candidate list and clears the
+// marks and touched bits (the growth kernel has already cleared the other
+// claim grid).  A touched word holds claims and a marked one front voxels
+// of this step: exactly the words of A_t U New_t.  Tiles are appended in
+// any order (one atomic per block and tile) -- the growth step gives the
+// same result for any order of its list, every draw being keyed by (voxel,
+// step, block) and claims ORed -- but the words of a tile in ascending
+// order, so that a growth warp's 32 list entries are mostly neighbouring
+// words, whose rows it reads from L1 (2 % of a 400^3 realization).
+//
 // Thread t of a block takes words base + k * 256 + t (k < 8) of a 2048-word
-// tile; all loads of a tile are issued before its stores.
+// tile, so warp w's eight 32-word rows are the bitmap words base / 32 + 8 k
+// + w, which lane k loads.  Two paths, chosen per step by the size of the
+// step's list (uniform):
+//   - sparse (list < nwords / kSparseFraction): the bitmaps come first, and
+//     only marked or touched words are loaded -- the work follows the front,
+//     and a tile far from it costs two bitmap loads per lane k;
+//   - dense: every word's claims and grid word are loaded together with the
+//     bitmaps (no dependent round trip), as a sweep -- cheaper once the
+//     front occupies most words.
 constexpr int kCommitThreads = 256;
 constexpr int kCommitItems = 8;
+constexpr uint32_t kSparseFraction = 8;
 
 __global__ void __launch_bounds__(kCommitThreads, 3)
     k_commit(Geom g, RunState* st, uint32_t* grid, uint32_t* aux, uint32_t* mark,
              uint32_t* list) {
   constexpr int kWarps = kCommitThreads / 32;
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_off[kCommitItems * kWarps];
   __shared__ uint32_t s_base;
   __shared__ unsigned long long s_claimed;
   if (!st->active) return;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t par = st->t & 1u;
   const uint32_t nw = g.nwords;
-  const uint32_t* claims = aux + (size_t)par * nw;
+  uint32_t* touched = mark + bitmap_words(g);
+  const uint32_t* claims = aux + (size_t)(st->t & 1u) * nw;
+  const bool sparse = (unsigned long long)st->front_words * kSparseFraction < nw;
   if (threadIdx.x == 0) s_claimed = 0;
   uint32_t claimed = 0;
   constexpr uint32_t kTile = kCommitThreads * kCommitItems;
   for (uint32_t base = blockIdx.x * kTile; base < nw; base += gridDim.x * kTile) {
-    uint32_t m[kCommitItems], c[kCommitItems], old[kCommitItems];
-#pragma unroll
-    for (int k = 0; k < kCommitItems; ++k) {
-      const uint32_t w = base + k * kCommitThreads + threadIdx.x;
-      const bool valid = w < nw;
-      m[k] = (lane == 0 && valid) ? mark[w >> 5] : 0u;
-      c[k] = valid ? claims[w] : 0u;
-      old[k] = valid ? grid[w] : 0u;
-    }
+    // Lane k < 8: the bitmap word of this warp's row k.
+    const uint32_t row0 = base + lane * kCommitThreads + warp * 32u;
+    const bool jv = lane < (uint32_t)kCommitItems && row0 < nw;
+    const uint32_t jk = row0 >> 5;
+    uint32_t c[kCommitItems], old[kCommitItems];
     uint32_t keep = 0;  // bit k: word k is listed
+    if (sparse) {
+      const uint32_t mk = jv ? mark[jk] : 0u, tc = jv ? touched[jk] : 0u;
+      if (mk) mark[jk] = 0u;
+      if (tc) touched[jk] = 0u;
+      const uint32_t mt = mk | tc;
+#pragma unroll
+      for (int k = 0; k < kCommitItems; ++k) {
+        const uint32_t w = base + k * kCommitThreads + threadIdx.x;
+        const bool act = (__shfl_sync(0xffffffffu, mt, k) >> lane) & 1u;  // set bits lie below nw
+        c[k] = act ? claims[w] : 0u;
+        old[k] = act ? grid[w] : 0u;
+        if (act) keep |= 1u << k;
+      }
+    } else {
+      const uint32_t mk = jv ? mark[jk] : 0u, tc = jv ? touched[jk] : 0u;
+#pragma unroll
+      for (int k = 0; k < kCommitItems; ++k) {
+        const uint32_t w = base + k * kCommitThreads + threadIdx.x;
+        const bool valid = w < nw;
+        c[k] = valid ? claims[w] : 0u;
+        old[k] = valid ? grid[w] : 0u;
+      }
+      if (mk) mark[jk] = 0u;
+      if (tc) touched[jk] = 0u;
+#pragma unroll
+      for (int k = 0; k < kCommitItems; ++k) {
+        const uint32_t mkk = __shfl_sync(0xffffffffu, mk, k);
+        if (((mkk >> lane) & 1u) | (c[k] ? 1u : 0u)) keep |= 1u << k;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < kCommitItems; ++k) {
-      const uint32_t w = base + k * kCommitThreads + threadIdx.x;
-      if (m[k]) mark[w >> 5] = 0;
-      if (c[k]) grid[w] = old[k] | c[k];
-      claimed += __popc(c[k]);
-      const uint32_t mk = __shfl_sync(0xffffffffu, m[k], 0);
-      if (((mk >> lane) & 1u) | (c[k] ? 1u : 0u)) keep |= 1u << k;
+      if (c[k]) grid[base + k * kCommitThreads + threadIdx.x] = old[k] | c[k];
+      claimed += (uint32_t)__popc(c[k]);
     }
-    // Block-wide exclusive offsets of the kept words, one atomic for the tile.
-    const uint32_t mine = __popc(keep);
-    uint32_t incl = mine;
+    // The tile's kept words in ascending order (k-major, then warp, then
+    // lane), one atomic for the tile: a growth warp's 32 list entries are
+    // then mostly neighbouring words, whose rows it reads from L1.
+    uint32_t bk[kCommitItems], cnt_mine = 0;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= (uint32_t)off) incl += y;
+    for (int k = 0; k < kCommitItems; ++k) {
+      bk[k] = __ballot_sync(0xffffffffu, (keep >> k) & 1u);
+      if (lane == (uint32_t)k) cnt_mine = (uint32_t)__popc(bk[k]);
     }
-    if (lane == 31) s_warp[warp] = incl;
+    if (lane < (uint32_t)kCommitItems) s_off[lane * kWarps + warp] = cnt_mine;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t run = 0;
-      for (int i = 0; i < kWarps; ++i) {
-        const uint32_t x = s_warp[i];
-        s_warp[i] = run;
-        run += x;
+    if (warp == 0) {
+      static_assert(kCommitItems * kWarps == 64, "two counts per lane");
+      const uint32_t a0 = s_off[2 * lane], a1 = s_off[2 * lane + 1];
+      uint32_t incl = a0 + a1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= (uint32_t)off) incl += y;
       }
-      s_base = run ? atomicAdd(&st->list_next, run) : 0u;
+      s_off[2 * lane] = incl - a0 - a1;
+      s_off[2 * lane + 1] = incl - a1;
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) s_base = tot ? atomicAdd(&st->list_next, tot) : 0u;
     }
     __syncthreads();
-    uint32_t pos = s_base + s_warp[warp] + incl - mine;
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < kCommitItems; ++k)
-      if (keep & (1u << k)) list[pos++] = base + k * kCommitThreads + threadIdx.x;
-    __syncthreads();  // s_warp / s_base are reused by the next tile
+      if ((keep >> k) & 1u)
+        list[s_base + s_off[k * kWarps + warp] + __popc(bk[k] & lt)] =
+            base + k * kCommitThreads + threadIdx.x;
+    __syncthreads();  // s_off / s_base are reused by the next tile
+
   }
   const uint32_t wc = __reduce_add_sync(0xffffffffu, claimed);
   if (lane == 0 && wc) atomicAdd(&s_claimed, (unsigned long long)wc);
@@ -926,6 +972,9 @@ constexpr int kGrowWarps = kGrowThreads / 32;
 #define QSGS_GROW_MIN_BLOCKS 3  // resident blocks per SM the register budget aims for
 #endif
 constexpr int kGrowEntries = 7 * 32 + 1;  // non-empty masks of a chunk, plus one spare
+#ifndef QSGS_GROW_THR_CURSOR
+#define QSGS_GROW_THR_CURSOR 0
+#endif
 constexpr int kGrowWins = 256;            // deferred claims buffered per warp
 
 struct GrowWarpSmem {
@@ -1144,9 +1193,18 @@ __device__ __forceinline__ void claim_target(const Geom& g, uint32_t w, uint32_t
 
 // Claims of buffered draws: a draw's direction j wins when it passed its
 // threshold and its target is a void in-domain neighbour (bit i of V_{4b+j}).
+// Every claim also sets its word's touched bit, so that the commit visits
+// only marked and touched words.
+__device__ __forceinline__ void claim(uint32_t* claims, uint32_t* touched, uint32_t wq,
+                                      uint32_t bit) {
+  // Fire-and-forget: the claim grid collects New_t; nobody waits.
+  atomicOr(claims + wq, bit);
+  atomicOr(touched + (wq >> 5), 1u << (wq & 31u));
+}
+
 template <int DK>
-__device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, const GrowWarpSmem& S,
-                                           uint32_t nwin, uint32_t lane) {
+__device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, uint32_t* touched,
+                                           const GrowWarpSmem& S, uint32_t nwin, uint32_t lane) {
   for (uint32_t k = lane; k < nwin; k += 32) {
     const uint32_t x = S.win[k];
     const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
@@ -1159,8 +1217,7 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
       win &= win - 1;
       uint32_t wq, bit;
       claim_target<DK>(g, wo, i, (int)(4u * b + j), wq, bit);
-      // Fire-and-forget: the claim grid collects New_t; nobody waits.
-      atomicOr(claims + wq, bit);
+      claim(claims, touched, wq, bit);
     }
   }
 }
@@ -1172,7 +1229,8 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, cons
 // target's threshold: Eq. 1 for a void cell, I^{n,m} for a cell of phase m.
 template <int DK>
 __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims,
-                                                 const GrowWarpSmem& S, uint32_t nwin,
+                                                 uint32_t* touched, const GrowWarpSmem& S,
+                                                 uint32_t nwin,
                                                  uint32_t lane, uint32_t t,
                                                  const PhiloxKeys& keys, const uint4* nthr) {
   const GeomInter& gi = static_cast<const GeomInter&>(g);  // the kind's own geometry
@@ -1200,7 +1258,7 @@ __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims
       const int c = dir_cls(d);
       const uint32_t th = lab ? gi.enter_thr[lab * 3u + (uint32_t)c]
                               : (c == 0 ? eq1.x : (c == 1 ? eq1.y : eq1.z));
-      if (u4_word(rnd, (int)j) <= th) atomicOr(claims + wq, bit);
+      if (u4_word(rnd, (int)j) <= th) claim(claims, touched, wq, bit);
     }
   }
 }
@@ -1307,6 +1365,7 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
                                            const PhiloxKeys& keys, GrowWarpSmem& S,
                                            GrowCounters& cnt) {
   const uint32_t lane = threadIdx.x & 31;
+  uint32_t* touched = mark + bitmap_words(g);
   // Phase 1: masks of this lane's word.
   uint32_t Bm[7] = {0, 0, 0, 0, 0, 0, 0};
   uint32_t v0 = 0;
@@ -1371,6 +1430,10 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   uint4 E = S.E[k];
   uint32_t m = E.x;
   for (uint32_t j = S.P[k]; j < s; ++j) m ^= bit_at(top_bit(m));  // pairs before s
+#if QSGS_GROW_THR_CURSOR
+  // The complemented thresholds of the cursor's entry, loaded once per entry.
+  uint4 th = nthr[E.z & 7u];
+#endif
   // Each lane draws two pairs per iteration (two independent Philox chains
   // in flight hide the multiply latency).  After a lane's pair empties the
   // cursor's mask the cursor moves to the next entry (index at most n_ent:
@@ -1384,21 +1447,38 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     const uint32_t ia = top_bit(m);
     m ^= bit_at(ia);
     const uint32_t xa = E.y + ia, cwa = E.z, ta = E.w | ia;
+#if QSGS_GROW_THR_CURSOR
+    const uint4 tha = th;
+#endif
     if (va && m == 0) {
       E = S.E[++k];
       m = E.x;
+#if QSGS_GROW_THR_CURSOR
+      th = nthr[E.z & 7u];
+#endif
     }
     const uint32_t ib = top_bit(m);
     m ^= bit_at(ib);
     const uint32_t xb = E.y + ib, cwb = E.z, tb = E.w | ib;
+#if QSGS_GROW_THR_CURSOR
+    const uint4 thb = th;
+#endif
     if (vb && m == 0) {
       E = S.E[++k];
       m = E.x;
+#if QSGS_GROW_THR_CURSOR
+      th = nthr[E.z & 7u];
+#endif
     }
     const U4 ra = philox4x32_10(U4{xa, 0u, t, cwa}, keys);
     const U4 rb = philox4x32_10(U4{xb, 0u, t, cwb}, keys);
+#if QSGS_GROW_THR_CURSOR
+    const uint32_t pa = va ? fail_bits(ra, tha) ^ 0xFu : 0u;  // passing words
+    const uint32_t pb = vb ? fail_bits(rb, thb) ^ 0xFu : 0u;
+#else
     const uint32_t pa = va ? fail_bits(ra, nthr[cwa & 7u]) ^ 0xFu : 0u;  // passing words
     const uint32_t pb = vb ? fail_bits(rb, nthr[cwb & 7u]) ^ 0xFu : 0u;
+#endif
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
     const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
@@ -1409,9 +1489,9 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     if (nwin > (uint32_t)kGrowWins - 64u) {
       __syncwarp();
       if constexpr (DK == kInteract)
-        claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, nthr);
+        claim_wins_inter<DK>(g, claims, touched, S, nwin, lane, t, keys, nthr);
       else
-        claim_wins<DK>(g, claims, S, nwin, lane);
+        claim_wins<DK>(g, claims, touched, S, nwin, lane);
       __syncwarp();
       nwin = 0;
     }
@@ -1420,9 +1500,9 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   if ((per & 1u) | extra) draw2(2u * full < n, 2u * full + 1u < n);
   __syncwarp();
   if constexpr (DK == kInteract)
-    claim_wins_inter<DK>(g, claims, S, nwin, lane, t, keys, nthr);
+    claim_wins_inter<DK>(g, claims, touched, S, nwin, lane, t, keys, nthr);
   else
-    claim_wins<DK>(g, claims, S, nwin, lane);
+    claim_wins<DK>(g, claims, touched, S, nwin, lane);
   __syncwarp();  // S.E, S.P, S.V and S.win are rewritten by the next chunk
 }
 
@@ -1480,7 +1560,9 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
            uint32_t* aux, uint32_t* mark, RunState* st, const PhiloxKeys keys, uint32_t tile) {
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
-  __shared__ uint4 s_thr[DK == kInteract ? 8 : 7];  // kInteract: + the Eq. 1 slot
+  // Seven Philox blocks, and an eighth row: kInteract's Eq. 1 slot, else
+  // padding, so that every index (b & 7) a cursor may form is in the array.
+  __shared__ uint4 s_thr[8];
   if (!st->active) return;
   const uint32_t n = st->front_words;
   const uint32_t t = st->t;
@@ -1562,7 +1644,7 @@ __global__ void __launch_bounds__(256)
           win &= win - 1;
           uint32_t wq, bit;
           claim_target<kRuntime>(g, w, i, 4 * b + (int)j, wq, bit);
-          atomicOr(claims + wq, bit);
+          claim(claims, mark + bitmap_words(g), wq, bit);
         }
       }
     }
@@ -2198,8 +2280,8 @@ cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cu
                                   Tracer& tr, cudaGraphConditionalHandle cond, int use_cond) {
   (void)spin_limit;  // no waits in the batch commit
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_limits, (b.max_members + 255) / 256, 256, b.d, b.bs);
-  QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
-              b.list, 1);
+  QSGS_LAUNCH(tr, kClsFront, s, k_batch_list_solid, batch_commit_grid(b.max_words), 256, b.d,
+              b.bs, b.list);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
               1);
   return cudaSuccess;
@@ -2216,7 +2298,7 @@ cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowSh
     QSGS_LAUNCH_SMEM(tr, kClsGrow, s, k_grow_batch<kRuntime>, shape.blocks, kGrowThreads,
                      kGrowSmemBytes, b.d, b.bs, b.list, shape.tile);
   QSGS_LAUNCH(tr, kClsFront, s, k_batch_commit, batch_commit_grid(b.max_words), 256, b.d, b.bs,
-              b.list, 0);
+              b.list);
   QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_control, 1, kMaxBatchMembers, b.d, b.bs, cond, use_cond,
               0);
   return cudaSuccess;

@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                 "qsgs_grow_until": ([H, ctypes.c_uint32, S], ctypes.c_int),
                 "qsgs_fetch": ([H, vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int], ctypes.c_int),
                 "qsgs_query": ([H, S], ctypes.c_int),
+                "qsgs_snapshot_bytes": ([P], ctypes.c_size_t),
+                "qsgs_snapshot": ([H, vp, ctypes.c_size_t, ctypes.c_int], ctypes.c_int),
+                "qsgs_restore": ([H, vp, ctypes.c_size_t, ctypes.c_int], ctypes.c_int),
                 "qsgs_set_profiling": ([H, ctypes.c_int], ctypes.c_int),
                 "qsgs_profile": ([H, ctypes.POINTER(QsgsProfileEntry), ctypes.c_int],
                                  ctypes.c_int),
@@ -208,6 +211,22 @@ def qsgs_query(h) -> dict:
     if rc != QSGS_OK:
         raise QsgsError(rc, "qsgs_query")
     return s.as_dict()
+
+
+def qsgs_snapshot_bytes(p: dict) -> int:
+    return int(load_library().qsgs_snapshot_bytes(ctypes.byref(make_params(p))))
+
+
+def qsgs_snapshot(h, dst_ptr: int, nbytes: int, dst_kind: int) -> None:
+    rc = load_library().qsgs_snapshot(h, ctypes.c_void_p(dst_ptr), nbytes, dst_kind)
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_snapshot")
+
+
+def qsgs_restore(h, src_ptr: int, nbytes: int, src_kind: int) -> None:
+    rc = load_library().qsgs_restore(h, ctypes.c_void_p(src_ptr), nbytes, src_kind)
+    if rc != QSGS_OK:
+        raise QsgsError(rc, "qsgs_restore")
 
 
 def qsgs_set_profiling(h, enable: bool) -> None:
@@ -459,6 +478,24 @@ class Generator:
                QSGS_DST_HOST_MAPPED if out.is_pinned() else QSGS_DST_HOST)
         qsgs_fetch(self.handle, out.data_ptr(), out.numel() * out.element_size(), f, dst)
         return out
+
+    def snapshot(self, out=None):
+        """The realization's state between growth calls, as a uint8 tensor
+        (pinned host memory by default; ``out`` may be any CPU or CUDA
+        uint8 tensor of at least ``qsgs_snapshot_bytes`` bytes)."""
+        import torch
+        n = qsgs_snapshot_bytes(self.params)
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        kind = QSGS_DST_DEVICE if out.is_cuda else QSGS_DST_HOST
+        qsgs_snapshot(self.handle, out.data_ptr(), out.numel() * out.element_size(), kind)
+        return out
+
+    def restore(self, snap) -> None:
+        """Continues the realization saved in ``snap`` (a tensor written by
+        ``snapshot`` of a generator with the same parameters)."""
+        kind = QSGS_DST_DEVICE if snap.is_cuda else QSGS_DST_HOST
+        qsgs_restore(self.handle, snap.data_ptr(), snap.numel() * snap.element_size(), kind)
 
     def set_profiling(self, enable: bool = True) -> None:
         qsgs_set_profiling(self.handle, enable)

@@ -43,7 +43,8 @@ class Server:
     """Admission by free memory, resident state, interleaved steps."""
 
     def __init__(self, device=None, max_members: int = 256, max_words: int = 1 << 27,
-                 hbm_budget: int | None = None, step_quantum: int = 8, keep_results: bool = True):
+                 hbm_budget: int | None = None, step_quantum: int = 8, keep_results: bool = True,
+                 staging_voxels: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device(
@@ -57,6 +58,12 @@ class Server:
         self.hbm_budget = hbm_budget
         self.step_quantum = step_quantum
         self.keep_results = keep_results
+        # Results that are not kept still land in host memory: one pinned
+        # buffer, reused, sized for the largest request (grown on demand;
+        # staging_voxels sizes it up front, outside any timed region).
+        self._staging = None
+        if staging_voxels:
+            self._staging_buffer(staging_voxels)
         self.used_bytes = 0
         self.used_words = 0
         self.rounds = 0
@@ -84,15 +91,25 @@ class Server:
         self.used_bytes += r.gen.nbytes
         self.used_words += Q.word_count(r.params)
 
+    def _staging_buffer(self, voxels: int):
+        torch = self.torch
+        if self._staging is None or self._staging.numel() < voxels:
+            self._staging = torch.empty(voxels, dtype=torch.uint8,
+                                        pin_memory=torch.cuda.is_available())
+        return self._staging
+
     def _retire(self, r: Request, st: Q.Stats, clock) -> None:
         torch = self.torch
         r.stats = st
+        # The uint8 phase map goes to pinned host memory, written by the
+        # device; the request finishes when it is there.
         if self.keep_results:
             host = torch.empty(r.gen.shape, dtype=torch.uint8, pin_memory=True)
             r.gen.fetch(out=host)
             r.result = host
         else:
-            r.gen.fetch(fmt="packed")   # still bring the result off the device
+            n = r.voxels
+            r.gen.fetch(out=self._staging_buffer(n)[:n].view(r.gen.shape))
         r.finished = clock()
         self.used_bytes -= r.gen.nbytes
         self.used_words -= Q.word_count(r.params)

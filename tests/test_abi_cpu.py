@@ -181,3 +181,12 @@ def test_batch_and_interaction_sizing_on_the_host(lib):
         assert lib.qsgs_interaction_bytes(ctypes.byref(Q.make_params(p))) == 16 * words + 3072
     bad = Q.make_params(dict(workloads.small_64(), cd=2.0))
     assert lib.qsgs_interaction_bytes(ctypes.byref(bad)) == 0
+
+
+def test_snapshot_size_is_header_state_and_grid(lib):
+    # 256-byte header + 256-byte run state + the packed grid; host only.
+    for p in (workloads.small_64(), workloads.single_400(),
+              dict(workloads.small_64(), nx=33, ny=5, nz=7)):
+        words = (p["nx"] + 31) // 32 * p["ny"] * p["nz"]
+        assert Q.qsgs_snapshot_bytes(p) == 512 + 4 * words
+    assert Q.qsgs_snapshot_bytes(dict(workloads.small_64(), nx=0)) == 0
