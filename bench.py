@@ -516,12 +516,34 @@ def bench_batch(Q, torch, dev, tune_on: bool, repeats: int = 2) -> dict:
     run_single()
     torch.cuda.synchronize()
     single_ms = 1000 * (time.perf_counter() - t0)
+
+    # The same members as single instances on concurrent streams: one host
+    # thread per stream, each growing every SERVE_STREAMS-th member (every
+    # generator has its own stream).
+    import concurrent.futures as cf
+
+    def worker(k):
+        for i in range(k, len(gens), SERVE_STREAMS):
+            gens[i].seed()
+            gens[i].grow()
+
+    with cf.ThreadPoolExecutor(SERVE_STREAMS) as ex:
+        list(ex.map(worker, range(SERVE_STREAMS)))  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(SERVE_STREAMS) as ex:
+        list(ex.map(worker, range(SERVE_STREAMS)))
+    torch.cuda.synchronize()
+    streams_ms = 1000 * (time.perf_counter() - t0)
     out = {"workload": "batch_96", "members": len(params), "voxels": voxels,
            "batch_ms": batch_ms, "realizations_per_s": len(params) / (batch_ms / 1000),
            "nodes_per_s": voxels / (batch_ms / 1000),
            "single_path_ms": single_ms,
            "single_path_realizations_per_s": len(params) / (single_ms / 1000),
            "speedup_vs_single_path": single_ms / batch_ms,
+           "concurrent_streams_ms": streams_ms, "streams": SERVE_STREAMS,
+           "concurrent_streams_realizations_per_s": len(params) / (streams_ms / 1000),
+           "speedup_vs_concurrent_streams": streams_ms / batch_ms,
            "all_done": all(st.status == Q.QSGS_OK for st in stats),
            "grow_shape": {k: bshape.get(k) for k in ("blocks", "tile", "cached")}}
     batch.close()

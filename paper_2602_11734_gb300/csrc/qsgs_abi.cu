@@ -595,8 +595,12 @@ int qsgs_grow_until(qsgs_handle* h, uint32_t max_steps, qsgs_stats* out) {
     // At most kStepsPerSync steps between host checks, and no more than
     // the call's budget (a step that is not active returns at once, but is
     // still a launch the profiler would time).
-    const uint32_t burst = max_steps && max_steps < kStepsPerSync ? max_steps : kStepsPerSync;
+    uint32_t launched = 0;
     for (;;) {
+      const uint32_t left = max_steps ? max_steps - launched : kStepsPerSync;
+      const uint32_t burst = left < kStepsPerSync ? left : kStepsPerSync;
+      if (burst == 0) break;  // the call's budget is spent
+      launched += burst;
       for (uint32_t k = 0; k < burst; ++k) {
         e = launch_step(h->g, b, h->k0, h->k1, kSpinLimit, GrowShape{h->grow_blocks, h->grow_tile},
                         h->stream, h->tracer, (cudaGraphConditionalHandle)0, 0,

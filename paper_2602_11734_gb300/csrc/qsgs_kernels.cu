@@ -306,26 +306,105 @@ struct InitialListPolicy {
 // appends marked or touched words to the next candidate list and clears the
 // marks and touched bits (the growth kernel has already cleared the other
 // claim grid).  A touched word holds claims and a marked one front voxels
-// of this step: exactly the words of A_t U New_t.  Tiles are appended in
-// any order (one atomic per block and tile) -- the growth step gives the
-// same result for any order of its list, every draw being keyed by (voxel,
-// step, block) and claims ORed -- but the words of a tile in ascending
-// order, so that a growth warp's 32 list entries are mostly neighbouring
-// words, whose rows it reads from L1 (2 % of a 400^3 realization).
+// of this step: exactly the words of A_t U New_t.  The list is appended in
+// any order -- the growth step gives the same result for any order of its
+// list, every draw being keyed by (voxel, step, block) and claims ORed --
+// but neighbouring words in ascending runs, so that a growth warp's 32 list
+// entries are mostly neighbouring words, whose rows it reads from L1 (2 %
+// of a 400^3 realization against lane-interleaved entries).
 //
-// Thread t of a block takes words base + k * 256 + t (k < 8) of a 2048-word
-// tile, so warp w's eight 32-word rows are the bitmap words base / 32 + 8 k
-// + w, which lane k loads.  Two paths, chosen per step by the size of the
-// step's list (uniform):
-//   - sparse (list < nwords / kSparseFraction): the bitmaps come first, and
-//     only marked or touched words are loaded -- the work follows the front,
-//     and a tile far from it costs two bitmap loads per lane k;
-//   - dense: every word's claims and grid word are loaded together with the
-//     bitmaps (no dependent round trip), as a sweep -- cheaper once the
-//     front occupies most words.
+// Two paths, chosen per step by the size of the step's list (uniform):
+//   - sparse (list < nwords / kSparseFraction): a warp reads 4 x 32 words
+//     of both bitmaps (4096 grid words) at a time and serves the non-zero ones
+//     in groups of kCommitGroup, a lane per grid word, loads first; the
+//     work follows the front -- a region without it costs one coalesced
+//     bitmap read per 1024 words, and no warp waits on another;
+//   - dense: tiles of 2048 words, thread t of a block taking words base +
+//     k * 256 + t (k < 8), every word's claims and grid word loaded together
+//     with the bitmaps (no dependent round trip), one atomic per tile --
+//     cheaper once the front occupies most words.
 constexpr int kCommitThreads = 256;
 constexpr int kCommitItems = 8;
-constexpr uint32_t kSparseFraction = 8;
+constexpr int kCommitGroup = 8;
+constexpr uint32_t kSparseFraction = 32;
+
+// Lanes of a warp: the next (up to) kCommitGroup set bits of the uniform
+// mask nz, as source lanes src[k] with their bitmap words mm[k] (0 past the
+// last set bit); nz loses those bits.
+__device__ __forceinline__ void next_group(uint32_t& nz, uint32_t m, uint32_t (&src)[kCommitGroup],
+                                           uint32_t (&mm)[kCommitGroup]) {
+#pragma unroll
+  for (int k = 0; k < kCommitGroup; ++k) {
+    const bool any = nz != 0u;
+    src[k] = any ? (uint32_t)(__ffs(nz) - 1) : 0u;
+    const uint32_t v = __shfl_sync(0xffffffffu, m, src[k]);
+    mm[k] = any ? v : 0u;
+    nz &= nz - 1u;
+  }
+}
+
+// The sparse path (all lanes of the warp together): returns this lane's
+// count of claimed voxels.  A warp reads kSparseRows rows of 32 bitmap
+// words per iteration, all loads in flight together.
+constexpr int kSparseRows = 4;
+
+__device__ __forceinline__ uint32_t commit_sparse(const Geom& g, RunState* st, uint32_t* grid,
+                                                  const uint32_t* claims, uint32_t* mark,
+                                                  uint32_t* touched, uint32_t* list) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nb = bitmap_words(g), nw = g.nwords;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t claimed = 0;
+  for (uint32_t r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32u * kSparseRows);
+       r0 < nb; r0 += nwarps * 32u * kSparseRows) {
+    uint32_t mk[kSparseRows], tc[kSparseRows];
+#pragma unroll
+    for (int r = 0; r < kSparseRows; ++r) {
+      const uint32_t j = r0 + r * 32u + lane;
+      mk[r] = j < nb ? mark[j] : 0u;
+      tc[r] = j < nb ? touched[j] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSparseRows; ++r) {
+      const uint32_t j0 = r0 + r * 32u;
+      if (mk[r]) mark[j0 + lane] = 0u;
+      if (tc[r]) touched[j0 + lane] = 0u;
+      const uint32_t m = mk[r] | tc[r];
+      uint32_t nz = __ballot_sync(0xffffffffu, m != 0u);
+      while (nz) {  // warp-uniform
+        uint32_t src[kCommitGroup], mm[kCommitGroup], c[kCommitGroup], old[kCommitGroup];
+        bool act[kCommitGroup];
+        next_group(nz, m, src, mm);
+#pragma unroll
+        for (int k = 0; k < kCommitGroup; ++k) {
+          // (64-bit: near N = 2^32 with nx < 32 the word count nears 2^32
+          // too; bits past nw are never set.)
+          const unsigned long long w = (unsigned long long)(j0 + src[k]) * 32u + lane;
+          act[k] = ((mm[k] >> lane) & 1u) && w < nw;
+          c[k] = act[k] ? claims[w] : 0u;
+          old[k] = act[k] ? grid[w] : 0u;
+        }
+        uint32_t total = 0;
+#pragma unroll
+        for (int k = 0; k < kCommitGroup; ++k) {
+          if (c[k]) grid[(j0 + src[k]) * 32u + lane] = old[k] | c[k];
+          claimed += (uint32_t)__popc(c[k]);
+          total += (uint32_t)__popc(mm[k]);
+        }
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&st->list_next, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+        for (int k = 0; k < kCommitGroup; ++k) {
+          if (act[k]) list[base + __popc(mm[k] & lt)] = (j0 + src[k]) * 32u + lane;
+          base += (uint32_t)__popc(mm[k]);
+        }
+      }
+    }
+  }
+  return claimed;
+}
 
 __global__ void __launch_bounds__(kCommitThreads, 3)
     k_commit(Geom g, RunState* st, uint32_t* grid, uint32_t* aux, uint32_t* mark,
@@ -343,42 +422,28 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
   if (threadIdx.x == 0) s_claimed = 0;
   uint32_t claimed = 0;
   constexpr uint32_t kTile = kCommitThreads * kCommitItems;
-  for (uint32_t base = blockIdx.x * kTile; base < nw; base += gridDim.x * kTile) {
+  if (sparse) claimed = commit_sparse(g, st, grid, claims, mark, touched, list);
+  for (uint32_t base = blockIdx.x * kTile; !sparse && base < nw; base += gridDim.x * kTile) {
     // Lane k < 8: the bitmap word of this warp's row k.
     const uint32_t row0 = base + lane * kCommitThreads + warp * 32u;
     const bool jv = lane < (uint32_t)kCommitItems && row0 < nw;
     const uint32_t jk = row0 >> 5;
     uint32_t c[kCommitItems], old[kCommitItems];
     uint32_t keep = 0;  // bit k: word k is listed
-    if (sparse) {
-      const uint32_t mk = jv ? mark[jk] : 0u, tc = jv ? touched[jk] : 0u;
-      if (mk) mark[jk] = 0u;
-      if (tc) touched[jk] = 0u;
-      const uint32_t mt = mk | tc;
+    const uint32_t mk = jv ? mark[jk] : 0u, tc = jv ? touched[jk] : 0u;
 #pragma unroll
-      for (int k = 0; k < kCommitItems; ++k) {
-        const uint32_t w = base + k * kCommitThreads + threadIdx.x;
-        const bool act = (__shfl_sync(0xffffffffu, mt, k) >> lane) & 1u;  // set bits lie below nw
-        c[k] = act ? claims[w] : 0u;
-        old[k] = act ? grid[w] : 0u;
-        if (act) keep |= 1u << k;
-      }
-    } else {
-      const uint32_t mk = jv ? mark[jk] : 0u, tc = jv ? touched[jk] : 0u;
+    for (int k = 0; k < kCommitItems; ++k) {
+      const uint32_t w = base + k * kCommitThreads + threadIdx.x;
+      const bool valid = w < nw;
+      c[k] = valid ? claims[w] : 0u;
+      old[k] = valid ? grid[w] : 0u;
+    }
+    if (mk) mark[jk] = 0u;
+    if (tc) touched[jk] = 0u;
 #pragma unroll
-      for (int k = 0; k < kCommitItems; ++k) {
-        const uint32_t w = base + k * kCommitThreads + threadIdx.x;
-        const bool valid = w < nw;
-        c[k] = valid ? claims[w] : 0u;
-        old[k] = valid ? grid[w] : 0u;
-      }
-      if (mk) mark[jk] = 0u;
-      if (tc) touched[jk] = 0u;
-#pragma unroll
-      for (int k = 0; k < kCommitItems; ++k) {
-        const uint32_t mkk = __shfl_sync(0xffffffffu, mk, k);
-        if (((mkk >> lane) & 1u) | (c[k] ? 1u : 0u)) keep |= 1u << k;
-      }
+    for (int k = 0; k < kCommitItems; ++k) {
+      const uint32_t mkk = __shfl_sync(0xffffffffu, mk, k);
+      if (((mkk >> lane) & 1u) | (c[k] ? 1u : 0u)) keep |= 1u << k;
     }
 #pragma unroll
     for (int k = 0; k < kCommitItems; ++k) {
