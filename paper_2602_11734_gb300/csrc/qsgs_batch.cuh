@@ -303,10 +303,6 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
   }
 }
 
-#ifndef QSGS_BATCH_SMEM_KEYS
-#define QSGS_BATCH_SMEM_KEYS 0
-#endif
-
 // Growth over the batch candidate list: warp chunk c belongs to the member
 // whose chunk range holds c, so every warp serves one member at a time.
 // Three blocks per SM like k_grow (the register cap costs a few spilled
@@ -323,15 +319,14 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_BATCH_GROW_MIN_BLOCKS)
   extern __shared__ uint4 grow_smem_[];
   GrowWarpSmem* smem = reinterpret_cast<GrowWarpSmem*>(grow_smem_);
   __shared__ uint4 s_thr[kGrowWarps][8];  // seven blocks and a padding row, as in k_grow
-#if QSGS_BATCH_SMEM_KEYS
-  __shared__ PhiloxKeys s_keys[kGrowWarps];
-#endif
+  __shared__ PhiloxKeys s_keys[kGrowWarps];  // the warp's member's round keys
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = bs->total_chunks, n = bs->n_members;
   const uint32_t nwarps = gridDim.x * kGrowWarps;
   const uint32_t ntiles = (total + tile - 1) / tile;
-  // The member of the warp's last chunk, its chunk range and thresholds (in
-  // s_thr[warp]) stay while the next chunk is the same member's.
+  // The member of the warp's last chunk, its chunk range, thresholds (in
+  // s_thr[warp]) and round keys (in s_keys[warp]) stay while the next chunk
+  // is the same member's.
   uint32_t cur = 0xFFFFFFFFu, lo = 0, hi = 0, live_dirs = 0;
   for (uint32_t ti = blockIdx.x * kGrowWarps + warp; ti < ntiles;
        ti = next_chunk(&bs->scan.grow_next, nwarps)) {
@@ -344,21 +339,18 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_BATCH_GROW_MIN_BLOCKS)
         live_dirs = live_directions(d[cur].st);
         __syncwarp();  // the previous member's thresholds are no longer read
         load_thresholds<true>(d[cur].st, lane, s_thr[warp]);  // complemented, for fail_bits
-#if QSGS_BATCH_SMEM_KEYS
         if (lane < 20) reinterpret_cast<uint32_t*>(&s_keys[warp])[lane] =
             reinterpret_cast<const uint32_t*>(&d[cur].keys)[lane];
-#endif
         __syncwarp();
       }
       const MemberDesc& md = d[cur];
       const uint32_t t = md.st->t;
       const uint32_t j = (c - lo) * 32u + lane;
       const uint32_t w = j < md.list_n ? list[md.list_base + j] : 0xFFFFFFFFu;
-#if QSGS_BATCH_SMEM_KEYS
-      const PhiloxKeys& keys = s_keys[warp];  // read by the rounds from shared memory
-#else
-      const PhiloxKeys keys = md.keys;
-#endif
+      // The member's round keys are read by the Philox rounds from shared
+      // memory: held in registers (k_grow takes them from the constant bank)
+      // they made this kernel spill (100 vs 97 ms for the 96-member batch).
+      const PhiloxKeys& keys = s_keys[warp];
       uint32_t* claims = md.aux + (size_t)(t & 1u) * md.g.nwords;
       uint32_t* other = md.aux + (size_t)((t & 1u) ^ 1u) * md.g.nwords;
       GrowCounters cnt{0, 0};

@@ -365,6 +365,16 @@ __device__ __forceinline__ uint32_t commit_sparse(const Geom& g, RunState* st, u
       mk[r] = j < nb ? mark[j] : 0u;
       tc[r] = j < nb ? touched[j] : 0u;
     }
+    // One list reservation for all words of the kSparseRows rows (a single
+    // counter takes every step's appends: one atomic per warp iteration, not
+    // per group).
+    uint32_t words = 0;
+#pragma unroll
+    for (int r = 0; r < kSparseRows; ++r) words += (uint32_t)__popc(mk[r] | tc[r]);
+    words = __reduce_add_sync(0xffffffffu, words);
+    uint32_t base = 0;
+    if (lane == 0 && words) base = atomicAdd(&st->list_next, words);
+    base = __shfl_sync(0xffffffffu, base, 0);
 #pragma unroll
     for (int r = 0; r < kSparseRows; ++r) {
       const uint32_t j0 = r0 + r * 32u;
@@ -385,16 +395,11 @@ __device__ __forceinline__ uint32_t commit_sparse(const Geom& g, RunState* st, u
           c[k] = act[k] ? claims[w] : 0u;
           old[k] = act[k] ? grid[w] : 0u;
         }
-        uint32_t total = 0;
 #pragma unroll
         for (int k = 0; k < kCommitGroup; ++k) {
           if (c[k]) grid[(j0 + src[k]) * 32u + lane] = old[k] | c[k];
           claimed += (uint32_t)__popc(c[k]);
-          total += (uint32_t)__popc(mm[k]);
         }
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&st->list_next, total);
-        base = __shfl_sync(0xffffffffu, base, 0);
 #pragma unroll
         for (int k = 0; k < kCommitGroup; ++k) {
           if (act[k]) list[base + __popc(mm[k] & lt)] = (j0 + src[k]) * 32u + lane;
