@@ -413,8 +413,10 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
  *   front_out    host: receives the count
  * Limit: at most 16,707,584 words (e.g. 800^3 or 32 x 4096 x 4079 fit,
  * 1024^3 does not); larger grids return QSGS_ERR_WORKSPACE before touching
- * the device.  The first call on a device looks up the scratch address
- * (this may load the library's device code).  Each call zeroes the scratch
+ * the device.  The first call on a device does the set-up: it looks up the
+ * scratch address with that device current (this may load the library's
+ * device code), so make that first call before any stream capture.  Each
+ * call zeroes the scratch
  * it uses (run state and tile status words) on the stream before the count.
  * Calls share the one scratch per device: overlapping calls (other streams
  * or host threads) race and must be serialised by the caller.  The call

@@ -1096,6 +1096,31 @@ __device__ __forceinline__ void row_words(const Geom& g, const uint32_t* __restr
   }
 }
 
+// The masks of the three directions that land in row (y+DY, z+DZ), from the
+// row's words around the voxel's word (c) as occupancy, its x-1 / x+1
+// neighbour words in l / rr; `front` collects every void neighbour.
+template <int DZ, int DY>
+__device__ __forceinline__ void row_masks_from(uint32_t c, uint32_t l, uint32_t rr, uint32_t self,
+                                               const uint32_t (&live)[3], uint32_t (&V)[28],
+                                               uint32_t (&Bm)[7], uint32_t& front) {
+  const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
+  const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
+  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
+  const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
+  front |= vm | vp;
+  V[dm] = vm & live[dir_cls(dm)];
+  Bm[dm >> 2] |= V[dm];
+  if (d0 >= 0) {
+    constexpr int d = d0 < 0 ? 26 : d0;
+    const uint32_t v0 = ~c & self;
+    front |= v0;
+    V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
+    Bm[(d >> 2) % 7] |= V[d];
+  }
+  V[dp] = vp & live[dir_cls(dp)];
+  Bm[dp >> 2] |= V[dp];
+}
+
 template <int DZ, int DY, int DK, bool kInterior = false>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
@@ -1118,22 +1143,7 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
       rr |= br;
     }
   }
-  const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
-  const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
-  constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
-  const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
-  front |= vm | vp;
-  V[dm] = vm & live[dir_cls(dm)];
-  Bm[dm >> 2] |= V[dm];
-  if (d0 >= 0) {
-    constexpr int d = d0 < 0 ? 26 : d0;
-    const uint32_t v0 = ~c & self;
-    front |= v0;
-    V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
-    Bm[(d >> 2) % 7] |= V[d];
-  }
-  V[dp] = vp & live[dir_cls(dp)];
-  Bm[dp >> 2] |= V[dp];
+  row_masks_from<DZ, DY>(c, l, rr, self, live, V, Bm, front);
 }
 
 // The same for an interacting phase (R13): besides the void targets, cells
@@ -1649,15 +1659,17 @@ __global__ void __launch_bounds__(kGrowThreads, QSGS_GROW_MIN_BLOCKS)
   const uint32_t nchunks = (n + 31) / 32;
   const uint32_t ntiles = (nchunks + tile - 1) / tile;
   GrowCounters cnt{0, 0};
+  auto entry = [&](uint32_t c) -> uint32_t {
+    const uint32_t idx = c * 32u + lane;
+    const uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
+    return w < g.nwords ? w : 0xFFFFFFFFu;  // >= nwords only after a timed-out scan (reported)
+  };
   for (uint32_t ti = blockIdx.x * kGrowWarps + warp; ti < ntiles;
        ti = next_chunk(&st->grow_next, nwarps)) {
     const uint32_t c_end = min(ti * tile + tile, nchunks);
-    for (uint32_t c = ti * tile; c < c_end; ++c) {
-      const uint32_t idx = c * 32u + lane;
-      uint32_t w = idx < n ? cand[idx] : 0xFFFFFFFFu;
-      if (w >= g.nwords) w = 0xFFFFFFFFu;  // only after a timed-out scan (reported)
-      grow_chunk<DK>(g, grid, claims, other, mark, w, t, live_dirs, s_thr, keys, smem[warp], cnt);
-    }
+    for (uint32_t c = ti * tile; c < c_end; ++c)
+      grow_chunk<DK>(g, grid, claims, other, mark, entry(c), t, live_dirs, s_thr, keys,
+                     smem[warp], cnt);
   }
   flush_counters(st, cnt);
   finish_dispenser(&st->grow_next, &st->grow_done);
