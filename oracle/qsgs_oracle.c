@@ -14,8 +14,13 @@
  *       Here every draw is one 32-bit word of Philox4x32-10 (Salmon et al.,
  *       SC'11) keyed by the 64-bit realization seed:
  *         seeding draw of voxel v      : word v&3 of ctr (lo(v>>2), hi(v>>2), 0xFFFFFFFF, 0x100)
- *         growth draw of source a, step t, direction d
- *                                      : word d&3 of ctr (lo(a), hi(a), t, 0x200 | d>>2)
+ *         growth draw of source a, step t, direction d, the r-th target of
+ *         d's class c among a's targets at the start of step t (r counted
+ *         in the direction order of R4):
+ *                                      : word r&3 of ctr (lo(a), hi(a), t, 0x200 | B_c + r>>2)
+ *       with B = 0 (faces), 2 (edges), 5 (corners).  A target is a neighbour
+ *       inside the domain that is void (or, R13, may be entered) with a
+ *       positive threshold; distinct attempts of a step use distinct words.
  *   R2  "u <= p" (Sec. 2.1 steps 2-3) and "rand < G" (Algorithms 1-3) are
  *       both read as r < floor(p 2^32) on the 32-bit word r, so the
  *       probability is exactly floor(p 2^32) / 2^32.
@@ -263,6 +268,47 @@ static int has_void_neighbour(const oq_params* p, const uint8_t* phase, uint64_t
   return 0;
 }
 
+/* R1 (growth draws): the targets of a source at the start of a step, as a
+ * 26-bit mask over the directions -- neighbours inside the domain that are
+ * void with a positive threshold of their class, or (R13) cells of an
+ * earlier phase that may be entered along that direction. */
+static uint32_t target_mask(const oq_params* p, const uint8_t* phase, uint64_t a,
+                            const int32_t dirs[78], const int32_t cls[26], const uint64_t thr[3]) {
+  uint32_t m = 0;
+  for (int d = 0; d < 26; ++d) {
+    uint64_t q;
+    if (!neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) || phase[q] != 0)
+      continue;
+    const uint64_t th = blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]];
+    if (th > 0) m |= 1u << d;
+  }
+  return m;
+}
+
+static int count_bits(uint32_t m) {
+  int n = 0;
+  for (; m; m &= m - 1) ++n;
+  return n;
+}
+
+/* R1 (growth draws): the attempt of source a along direction d at step t is
+ * the r-th target of d's class (r counted over the class's directions in
+ * canonical order, among the targets of the start of the step); it takes
+ * word r & 3 of the Philox block with counter (a lo, a hi, t, 0x200 | b),
+ * b = B_class + (r >> 2), B = 0 (faces: blocks 0, 1), 2 (edges: 2, 3, 4), 5
+ * (corners: 5, 6).  Distinct attempts of a step thus use distinct words. */
+static uint32_t growth_draw(uint64_t a, uint32_t t, uint32_t targets, int d, int klass,
+                            const uint32_t key[2]) {
+  static const uint32_t class_bits[3] = {0x3Fu, 0x3FFC0u, 0x3FC0000u};
+  static const uint32_t first_block[3] = {0u, 2u, 5u};
+  const int r = count_bits(targets & class_bits[klass] & ((1u << d) - 1u));
+  const uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t,
+                           0x200u | (first_block[klass] + (uint32_t)(r >> 2))};
+  uint32_t out[4];
+  oq_philox4x32_10(ctr, key, out);
+  return out[r & 3];
+}
+
 uint64_t oq_front(const oq_params* p, const uint8_t* phase, uint32_t* out) {
   int32_t dirs[78], cls[26];
   oq_directions(dirs, cls);
@@ -320,7 +366,11 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
   uint32_t* A = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
   uint32_t* A_new = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
   uint32_t* merged = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
-  if (!A || !A_new || !merged) { free(A); free(A_new); free(merged); return OQ_ERR_NOMEM; }
+  uint32_t* T = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));  /* targets of A[i] */
+  if (!A || !A_new || !merged || !T) {
+    free(A); free(A_new); free(merged); free(T);
+    return OQ_ERR_NOMEM;
+  }
 
   /* Algorithm 3 starts from the active set: solids with a void neighbour
    * (step 2 of Sec. 2.3). */
@@ -335,21 +385,22 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
     uint64_t thr[3];
     for (int k = 0; k < 3; ++k) thr[k] = oq_threshold(t_ref[k], nt, c); /* Eq. 1 */
     uint64_t new_n = 0, live = 0;  /* A_new starts empty each step */
+    /* The targets of every front voxel at the start of the step (the draws
+     * are located by rank among them, R1). */
+    for (uint64_t i = 0; i < a_n; ++i) T[i] = target_mask(p, phase, A[i], dirs, cls, thr);
     for (int d = 0; d < 26; ++d) {   /* every direction of every front voxel */
       for (uint64_t i = 0; i < a_n; ++i) {
         uint64_t a = A[i], q;
-        /* neighbours inside the domain that are still void -- or, with
-         * interacting phases (R13), cells of an earlier phase */
-        if (!neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q)) continue;
-        if (phase[q] != 0) continue;
+        /* neighbours inside the domain that were void at the start of the
+         * step -- or, with interacting phases (R13), cells of an earlier
+         * phase -- with a positive threshold */
+        if (!((T[i] >> d) & 1u)) continue;
+        neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q);
+        if (phase[q] != 0) continue;  /* claimed earlier in this step */
         const uint64_t th = blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]];
-        if (th == 0) continue; /* this attempt cannot succeed */
         ++live;
         /* an independent draw for this (source, step, direction) */
-        uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
-        uint32_t r[4];
-        oq_philox4x32_10(ctr, key, r);
-        if ((uint64_t)r[d & 3] < th) {
+        if ((uint64_t)growth_draw(a, t, T[i], d, cls[d], key) < th) {
           phase[q] = 1;  /* the void (or entered cell) becomes solid ... */
           A_new[new_n++] = (uint32_t)q;  /* ... and joins A_new */
         }
@@ -394,6 +445,7 @@ int oq_run(const oq_params* p, uint8_t* phase, oq_step_log* log, uint32_t log_ca
   free(A);
   free(A_new);
   free(merged);
+  free(T);
   return 0;
 }
 
@@ -418,7 +470,11 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
   uint64_t c = (uint64_t)placed;
   uint8_t* solid_mask = (uint8_t*)malloc((size_t)n);
   uint8_t* grown = (uint8_t*)malloc((size_t)n);
-  if (!solid_mask || !grown) { free(solid_mask); free(grown); return OQ_ERR_NOMEM; }
+  uint32_t* T = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));  /* targets of each cell */
+  if (!solid_mask || !grown || !T) {
+    free(solid_mask); free(grown); free(T);
+    return OQ_ERR_NOMEM;
+  }
 
   uint32_t t = 0;
   int32_t status;
@@ -430,20 +486,18 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
     memcpy(solid_mask, phase, (size_t)n);
     memset(grown, 0, (size_t)n);
     uint64_t live = 0;
+    /* the targets of every solid cell of the start-of-step mask (R1) */
+    for (uint64_t a = 0; a < n; ++a)
+      T[a] = solid_mask[a] ? target_mask(p, solid_mask, a, dirs, cls, thr) : 0u;
     for (int d = 0; d < 26; ++d) {
       for (uint64_t a = 0; a < n; ++a) {
-        if (!solid_mask[a]) continue;
+        if (!solid_mask[a] || !((T[a] >> d) & 1u)) continue;
         uint64_t q;
         /* a target: void, or (R13) a cell of an earlier phase */
-        int target = neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q) &&
-                     !solid_mask[q];
-        const uint64_t th =
-            !target ? 0 : (blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]]);
-        if (th > 0) ++live;
-        uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), t, 0x200u | (uint32_t)(d >> 2)};
-        uint32_t r[4];
-        oq_philox4x32_10(ctr, key, r);
-        if ((uint64_t)r[d & 3] >= th) continue;
+        neighbour(p, a, dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2], &q);
+        const uint64_t th = blocked(p, q) ? inter_threshold(p, q, cls[d]) : thr[cls[d]];
+        ++live;
+        if ((uint64_t)growth_draw(a, t, T[a], d, cls[d], key) >= th) continue;
         grown[q] = 1;
       }
     }
@@ -468,5 +522,6 @@ int oq_run_fullfield(const oq_params* p, uint8_t* phase, oq_summary* out) {
   out->status = status;
   free(solid_mask);
   free(grown);
+  free(T);
   return 0;
 }

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256, 2)
     const uint32_t lw0 = g0 * 32u - md.word_base;  // member-local first word
     uint32_t* touched = md.mark + bitmap_words(md.g);
     const uint32_t* cur = md.aux + (size_t)(st->t & 1u) * md.g.nwords;
-    const bool sparse = (unsigned long long)st->front_words * kSparseFraction < nloc;
+    const bool sparse = commit_is_sparse(st->front_words, nloc);
     const bool jv = lane < (uint32_t)G && g0 + lane <= glast;
     const uint32_t jl = (lw0 >> 5) + lane;
     const uint32_t mk = jv ? md.mark[jl] : 0u, tc = jv ? touched[jl] : 0u;

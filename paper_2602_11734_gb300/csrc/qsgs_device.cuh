@@ -154,9 +154,10 @@ constexpr uint32_t kGrowTag = 0x200u;
 
 // ---------------------------------------------------------------------------
 // Directions.  d = 0..5 faces, 6..17 edges, 18..25 corners; within a class
-// ordered by (dz, dy, dx) lexicographically.  The growth draw of direction
-// d is word (d & 3) of the Philox block with counter word 3 = 0x200|(d>>2).
-// A neighbourhood position packs the offset as (dz+1)*9 + (dy+1)*3 + (dx+1).
+// ordered by (dz, dy, dx) lexicographically.  A growth attempt along d is
+// drawn by the rank of d among the source's targets of its class (counter
+// word 3 = 0x200 | block; see growth_blocks in qsgs_kernels.cu).  A
+// neighbourhood position packs the offset as (dz+1)*9 + (dy+1)*3 + (dx+1).
 // ---------------------------------------------------------------------------
 struct Dir {
   int dx, dy, dz, cls;
@@ -204,24 +205,6 @@ __host__ __device__ __forceinline__ int nb_pos(int dx, int dy, int dz) {
 
 __host__ __device__ __forceinline__ int dir_pos(int d) {
   return nb_pos(dir_dx(d), dir_dy(d), dir_dz(d));
-}
-
-// Neighbourhood positions of the directions drawn from Philox block b.
-__host__ __device__ __forceinline__ uint32_t block_pos_mask(int b) {
-  uint32_t m = 0;
-  for (int j = 0; j < 4; ++j) {
-    int d = 4 * b + j;
-    if (d < 26) m |= 1u << dir_pos(d);
-  }
-  return m;
-}
-
-// Neighbourhood positions of the directions of class cls.
-__host__ __device__ __forceinline__ uint32_t class_pos_mask(int cls) {
-  uint32_t m = 0;
-  for (int d = 0; d < 26; ++d)
-    if (dir_cls(d) == cls) m |= 1u << dir_pos(d);
-  return m;
 }
 
 constexpr uint32_t kNbAll = (1u << 27) - 1u;

@@ -328,6 +328,12 @@ constexpr int kCommitItems = 8;
 constexpr int kCommitGroup = 8;
 constexpr uint32_t kSparseFraction = 32;
 
+// The commit of a step whose list holds list_n of nwords words takes the
+// sparse path.
+__device__ __forceinline__ bool commit_is_sparse(uint32_t list_n, uint32_t nwords) {
+  return (unsigned long long)list_n * kSparseFraction < nwords;
+}
+
 // Lanes of a warp: the next (up to) kCommitGroup set bits of the uniform
 // mask nz, as source lanes src[k] with their bitmap words mm[k] (0 past the
 // last set bit); nz loses those bits.
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(kCommitThreads, 3)
   const uint32_t nw = g.nwords;
   uint32_t* touched = mark + bitmap_words(g);
   const uint32_t* claims = aux + (size_t)(st->t & 1u) * nw;
-  const bool sparse = (unsigned long long)st->front_words * kSparseFraction < nw;
+  const bool sparse = commit_is_sparse(st->front_words, nw);
   if (threadIdx.x == 0) s_claimed = 0;
   uint32_t claimed = 0;
   constexpr uint32_t kTile = kCommitThreads * kCommitItems;
@@ -1013,10 +1019,12 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 
 // ---------------------------------------------------------------------------
 // The growth step (Sec. 2.3 step 3, Algorithm 3).  Every front
-// voxel a tries each void in-domain neighbour q = a + e_d with the draw
-// word (d & 3) of Philox block (a, 0, t, 0x200 | d >> 2) against the class
-// threshold of Eq. 1; a success records q in this step's claim grid with a
-// fire-and-forget atomicOr.  The occupancy grid is not written during the
+// voxel a tries each void in-domain neighbour q = a + e_d (its targets)
+// against the class threshold of Eq. 1, with the draw located by rank: the
+// r-th target of class c takes word r & 3 of Philox block (a, 0, t, 0x200 |
+// B_c + r >> 2), B = 0, 2, 5 for faces, edges, corners (growth_blocks); a
+// success records q in this step's claim grid with a fire-and-forget
+// atomicOr.  The occupancy grid is not written during the
 // kernel, so every thread sees the start-of-step grid: the front, the void
 // targets and the attempt count are those of Algorithm 3 exactly, and the
 // claim grid ends up holding New_t (the commit scan ORs it into the grid).
@@ -1026,8 +1034,9 @@ __global__ void __launch_bounds__(1024) k_spacing_rounds(Geom g, CellGeom cg, Ru
 // bit-parallel over its 32 voxels, the front bits (solid with a void
 // in-domain neighbour), the 26 "void target" masks V_d (bit i: voxel i is
 // solid, its d-neighbour is void and inside the domain, and d's class has a
-// positive threshold) and the 7 Philox-block masks B_b = OR of V_d over the
-// directions of block b; words that still hold front voxels are marked for
+// positive threshold) and the 7 Philox-block masks B_b (voxels with more
+// targets of block b's class than the ranks before b); words that still
+// hold front voxels are marked for
 // the next candidate list.  Phase 2: the non-empty (word, block) masks are
 // listed in shared memory as entries and the chunk's (voxel, block) pairs --
 // one Philox call each -- are numbered through them; lane L takes the L-th
@@ -1102,30 +1111,27 @@ __device__ __forceinline__ void row_words(const Geom& g, const uint32_t* __restr
 template <int DZ, int DY>
 __device__ __forceinline__ void row_masks_from(uint32_t c, uint32_t l, uint32_t rr, uint32_t self,
                                                const uint32_t (&live)[3], uint32_t (&V)[28],
-                                               uint32_t (&Bm)[7], uint32_t& front) {
+                                               uint32_t& front) {
   const uint32_t at_minus = (c << 1) | (l >> 31);  // bit i: voxel x-1 of this row
   const uint32_t at_plus = (c >> 1) | (rr << 31);  // bit i: voxel x+1 of this row
   constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   const uint32_t vm = ~at_minus & self, vp = ~at_plus & self;
   front |= vm | vp;
   V[dm] = vm & live[dir_cls(dm)];
-  Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
     const uint32_t v0 = ~c & self;
     front |= v0;
     V[d] = v0 & live[dir_cls(d < 26 ? d : 0)];
-    Bm[(d >> 2) % 7] |= V[d];
   }
   V[dp] = vp & live[dir_cls(dp)];
-  Bm[dp >> 2] |= V[dp];
 }
 
 template <int DZ, int DY, int DK, bool kInterior = false>
 __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restrict__ grid,
                                           uint32_t y, uint32_t z, uint32_t r, uint32_t xw,
                                           uint32_t self, const uint32_t (&live)[3],
-                                          uint32_t (&V)[28], uint32_t (&Bm)[7], uint32_t& front) {
+                                          uint32_t (&V)[28], uint32_t& front) {
   int yy = (int)y + DY, zz = (int)z + DZ;
   if (on_torus<DK>(g)) {  // the torus: every row exists
     yy = yy < 0 ? yy + (int)g.ny : (yy >= (int)g.ny ? yy - (int)g.ny : yy);
@@ -1143,7 +1149,7 @@ __device__ __forceinline__ void row_masks(const Geom& g, const uint32_t* __restr
       rr |= br;
     }
   }
-  row_masks_from<DZ, DY>(c, l, rr, self, live, V, Bm, front);
+  row_masks_from<DZ, DY>(c, l, rr, self, live, V, front);
 }
 
 // The same for an interacting phase (R13): besides the void targets, cells
@@ -1155,7 +1161,7 @@ template <int DZ, int DY>
 __device__ __forceinline__ void row_masks_inter(const Geom& g, const uint32_t* __restrict__ grid,
                                                 uint32_t y, uint32_t z, uint32_t xw, uint32_t self,
                                                 const uint32_t (&live)[3], uint32_t (&V)[28],
-                                                uint32_t (&Bm)[7], uint32_t& front) {
+                                                uint32_t& front) {
   constexpr int dm = dir_index(-1, DY, DZ), d0 = dir_index(0, DY, DZ), dp = dir_index(1, DY, DZ);
   constexpr int cls_x = dir_cls(dm);                // class of the x-1 / x+1 directions
   constexpr int cls_0 = d0 >= 0 ? dir_cls(d0) : 0;  // class of the centre direction
@@ -1189,16 +1195,98 @@ __device__ __forceinline__ void row_masks_inter(const Geom& g, const uint32_t* _
   const uint32_t em = ((exc << 1) | (exl >> 31)) & self, ep = ((exc >> 1) | (exr << 31)) & self;
   front |= vm | vp | em | ep;
   V[dm] = (vm & live[cls_x]) | em;
-  Bm[dm >> 2] |= V[dm];
   if (d0 >= 0) {
     constexpr int d = d0 < 0 ? 26 : d0;
     const uint32_t v0 = ~c & self, e0 = e0c & self;
     front |= v0 | e0;
     V[d] = (v0 & live[cls_0]) | e0;
-    Bm[(d >> 2) % 7] |= V[d];
   }
   V[dp] = (vp & live[cls_x]) | ep;
-  Bm[dp >> 2] |= V[dp];
+}
+
+// R1, the growth draws: a voxel's targets (V bits) are drawn class by class
+// in rank order -- faces from blocks 0-1, edges from 2-4, corners from 5-6;
+// block B_c + k (B = 0, 2, 5) serves the class's targets of rank 4k .. 4k+3,
+// word j the one of rank 4k + j.  A voxel thus draws block B_c + k iff it
+// has more than 4k targets of class c.  The counts come bit-parallel over
+// the word's 32 voxels from carry-save adders (sum = a ^ b ^ c, carry = the
+// majority) on the direction masks of each class.
+__device__ __forceinline__ void csa(uint32_t a, uint32_t b, uint32_t c, uint32_t& sum,
+                                    uint32_t& carry) {
+  sum = a ^ b ^ c;
+  carry = (a & b) | (c & (a ^ b));
+}
+
+// Class of growth block b (faces 0-1, edges 2-4, corners 5-6), the first
+// block and the first direction of class c, and its number of directions.
+__host__ __device__ constexpr int block_class(int b) { return b < 2 ? 0 : (b < 5 ? 1 : 2); }
+__host__ __device__ constexpr int class_first_block(int c) { return c == 0 ? 0 : (c == 1 ? 2 : 5); }
+__host__ __device__ constexpr int class_first_dir(int c) { return c == 0 ? 0 : (c == 1 ? 6 : 18); }
+__host__ __device__ constexpr int class_dirs(int c) { return c == 0 ? 6 : (c == 1 ? 12 : 8); }
+
+__device__ __forceinline__ void growth_blocks(const uint32_t (&V)[28], uint32_t (&Bm)[7]) {
+  // Faces (6): count = fo + 2 ft + 4 f4.
+  uint32_t s1, c1, s2, c2, ft, f4;
+  csa(V[0], V[1], V[2], s1, c1);
+  csa(V[3], V[4], V[5], s2, c2);
+  const uint32_t fo = s1 ^ s2, fk = s1 & s2;
+  csa(c1, c2, fk, ft, f4);
+  Bm[0] = fo | ft | f4;    // >= 1
+  Bm[1] = f4 & (fo | ft);  // >= 5
+  // Edges (12): count = eo + 2 et + 4 eq + 8 ee.
+  uint32_t a1, b1, a2, b2, a3, b3, a4, b4, o1, k1, t1, m1, t2, m2, eq, ee;
+  csa(V[6], V[7], V[8], a1, b1);
+  csa(V[9], V[10], V[11], a2, b2);
+  csa(V[12], V[13], V[14], a3, b3);
+  csa(V[15], V[16], V[17], a4, b4);
+  csa(a1, a2, a3, o1, k1);
+  const uint32_t eo = o1 ^ a4, k2 = o1 & a4;
+  csa(b1, b2, b3, t1, m1);
+  csa(b4, k1, k2, t2, m2);
+  const uint32_t et = t1 ^ t2, m3 = t1 & t2;
+  csa(m1, m2, m3, eq, ee);
+  Bm[2] = eo | et | eq | ee;   // >= 1
+  Bm[3] = ee | (eq & (eo | et));  // >= 5
+  Bm[4] = ee & (eo | et | eq);    // >= 9
+  // Corners (8): count = co + 2 ct + 4 cq + 8 ce.
+  uint32_t p1, q1, p2, q2, o2, k3, u1, n1;
+  csa(V[18], V[19], V[20], p1, q1);
+  csa(V[21], V[22], V[23], p2, q2);
+  csa(p1, p2, V[24], o2, k3);
+  const uint32_t co = o2 ^ V[25], k4 = o2 & V[25];
+  csa(q1, q2, k3, u1, n1);
+  const uint32_t ct = u1 ^ k4, n2 = u1 & k4;
+  const uint32_t cq = n1 ^ n2, ce = n1 & n2;
+  Bm[5] = co | ct | cq | ce;      // >= 1
+  Bm[6] = ce | (cq & (co | ct));  // >= 5
+}
+
+// The targets of class c of voxel i of a lane word, as a mask over the
+// class's directions in order (bit k: direction class_first_dir(c) + k), from
+// the word's direction masks (Vw[b] holds V[4b .. 4b+3]).
+__device__ __forceinline__ uint32_t vbit(uint32_t v, uint32_t i) { return (v >> i) & 1u; }
+__device__ __forceinline__ uint32_t class_targets(const uint4* Vw, uint32_t i, int c) {
+  if (c == 0) {  // faces: V[0..5]
+    const uint4 a = Vw[0], b = Vw[1];
+    return vbit(a.x, i) | vbit(a.y, i) << 1 | vbit(a.z, i) << 2 | vbit(a.w, i) << 3 |
+           vbit(b.x, i) << 4 | vbit(b.y, i) << 5;
+  }
+  if (c == 1) {  // edges: V[6..17]
+    const uint4 a = Vw[1], b = Vw[2], e = Vw[3], f = Vw[4];
+    return vbit(a.z, i) | vbit(a.w, i) << 1 | vbit(b.x, i) << 2 | vbit(b.y, i) << 3 |
+           vbit(b.z, i) << 4 | vbit(b.w, i) << 5 | vbit(e.x, i) << 6 | vbit(e.y, i) << 7 |
+           vbit(e.z, i) << 8 | vbit(e.w, i) << 9 | vbit(f.x, i) << 10 | vbit(f.y, i) << 11;
+  }
+  const uint4 a = Vw[4], b = Vw[5], e = Vw[6];  // corners: V[18..25]
+  return vbit(a.z, i) | vbit(a.w, i) << 1 | vbit(b.x, i) << 2 | vbit(b.y, i) << 3 |
+         vbit(b.z, i) << 4 | vbit(b.w, i) << 5 | vbit(e.x, i) << 6 | vbit(e.y, i) << 7;
+}
+
+
+// Position of the r-th (from 0) set bit of m (r < popc(m)).
+__device__ __forceinline__ uint32_t nth_bit(uint32_t m, uint32_t r) {
+  for (uint32_t k = 0; k < r; ++k) m &= m - 1;
+  return (uint32_t)(__ffs(m) - 1);
 }
 
 struct GrowCounters {
@@ -1212,11 +1300,12 @@ struct GrowCounters {
 // exactly when r > T - 1, which fail_bits below reads off the carry flag.
 template <bool kComplement = false>
 __device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lane, uint4* thr) {
-  if (lane < 28) {
-    const int d = (int)lane;
-    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
+  if (lane < 28) {  // word j = lane & 3 of block b = lane >> 2: a target of rank r of class c
+    const int b = (int)lane >> 2, c = block_class(b);
+    const int r = 4 * (b - class_first_block(c)) + ((int)lane & 3);
+    const unsigned long long T = r < class_dirs(c) ? st->thr[c] : 0ull;
     const uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
-    reinterpret_cast<uint32_t*>(thr)[d] = kComplement ? ~t1 : t1;
+    reinterpret_cast<uint32_t*>(thr)[lane] = kComplement ? ~t1 : t1;
   }
 }
 
@@ -1228,12 +1317,13 @@ __device__ __forceinline__ void load_thresholds(const RunState* st, uint32_t lan
 // themselves (not complemented), for the claims.
 __device__ __forceinline__ void load_thresholds_inter(const RunState* st, const GeomInter& g,
                                                       uint32_t lane, uint4* thr) {
-  if (lane < 28) {
-    const int d = (int)lane;
-    const unsigned long long T = d < 26 ? st->thr[dir_cls(d)] : 0ull;
+  if (lane < 28) {  // word j = lane & 3 of block b = lane >> 2: a target of rank r of class c
+    const int b = (int)lane >> 2, c = block_class(b);
+    const bool real = 4 * (b - class_first_block(c)) + ((int)lane & 3) < class_dirs(c);
+    const unsigned long long T = real ? st->thr[c] : 0ull;
     uint32_t t1 = T ? (uint32_t)(T - 1) : 0u;  // dead: never tested
-    if (d < 26) t1 = max(t1, g.enter_thr[dir_cls(d)]);  // row 0: the largest per class
-    reinterpret_cast<uint32_t*>(thr)[d] = ~t1;
+    if (real) t1 = max(t1, g.enter_thr[c]);  // row 0: the largest per class
+    reinterpret_cast<uint32_t*>(thr)[lane] = ~t1;
   } else if (lane < 31) {
     const unsigned long long T = st->thr[lane - 28];
     reinterpret_cast<uint32_t*>(thr)[lane] = T ? (uint32_t)(T - 1) : 0u;
@@ -1273,8 +1363,9 @@ __device__ __forceinline__ void claim_target(const Geom& g, uint32_t w, uint32_t
 
 // Claims of buffered draws: a draw's direction j wins when it passed its
 // threshold and its target is a void in-domain neighbour (bit i of V_{4b+j}).
-// Every claim also sets its word's touched bit, so that the commit visits
-// only marked and touched words.
+// Every claim also sets its word's touched bit, so that the commit's sparse
+// path visits only marked and touched words.  (Setting it only in steps
+// whose commit is sparse measured 1 % slower.)
 __device__ __forceinline__ void claim(uint32_t* claims, uint32_t* touched, uint32_t wq,
                                       uint32_t bit) {
   // Fire-and-forget: the claim grid collects New_t; nobody waits.
@@ -1288,15 +1379,19 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, uint
   for (uint32_t k = lane; k < nwin; k += 32) {
     const uint32_t x = S.win[k];
     const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
-    const uint4 vm = S.V[owner][b];
-    uint32_t win = (x >> 16) & (((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
-                                (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3));
+    // Word j of block b is the voxel's target of rank r0 + j of class c.
+    const int c = block_class((int)b);
+    const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(c));
+    const uint32_t m = class_targets(S.V[owner], i, c);
+    const uint32_t n = (uint32_t)__popc(m);
+    uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
     const uint32_t wo = S.w[owner];
     while (win) {
       const uint32_t j = __ffs(win) - 1;
       win &= win - 1;
+      const int d = class_first_dir(c) + (int)nth_bit(m, r0 + j);
       uint32_t wq, bit;
-      claim_target<DK>(g, wo, i, (int)(4u * b + j), wq, bit);
+      claim_target<DK>(g, wo, i, d, wq, bit);
       claim(claims, touched, wq, bit);
     }
   }
@@ -1318,9 +1413,12 @@ __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims
   for (uint32_t k = lane; k < nwin; k += 32) {
     const uint32_t x = S.win[k];
     const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
-    const uint4 vm = S.V[owner][b];
-    uint32_t win = (x >> 16) & (((vm.x >> i) & 1u) | (((vm.y >> i) & 1u) << 1) |
-                                (((vm.z >> i) & 1u) << 2) | (((vm.w >> i) & 1u) << 3));
+    // Word j of block b is the voxel's target of rank r0 + j of class c.
+    const int cb = block_class((int)b);
+    const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(cb));
+    const uint32_t m = class_targets(S.V[owner], i, cb);
+    const uint32_t n = (uint32_t)__popc(m);
+    uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
     if (!win) continue;
     const uint32_t wo = S.w[owner];
     const uint32_t ro = fast_div(wo, g.div_W);
@@ -1329,7 +1427,7 @@ __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims
     while (win) {
       const uint32_t j = __ffs(win) - 1;
       win &= win - 1;
-      const int d = (int)(4u * b + j);
+      const int d = class_first_dir(cb) + (int)nth_bit(m, r0 + j);
       uint32_t wq, bit;
       claim_target<DK>(g, wo, i, d, wq, bit);
       const uint32_t rq = fast_div(wq, g.div_W);
@@ -1360,43 +1458,44 @@ __device__ __forceinline__ void word_masks(const Geom& g, const uint32_t* __rest
   const uint32_t live[3] = {0u - (live_dirs & 1u), 0u - ((live_dirs >> 6) & 1u),
                             0u - ((live_dirs >> 18) & 1u)};
   if constexpr (DK == kInteract) {
-    row_masks_inter<-1, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<-1, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<-1, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<0, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<0, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<0, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<1, -1>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<1, 0>(g, grid, y, z, xw, self, live, V, Bm, front);
-    row_masks_inter<1, 1>(g, grid, y, z, xw, self, live, V, Bm, front);
+    row_masks_inter<-1, -1>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<-1, 0>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<-1, 1>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<0, -1>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<0, 0>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<0, 1>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<1, -1>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<1, 0>(g, grid, y, z, xw, self, live, V, front);
+    row_masks_inter<1, 1>(g, grid, y, z, xw, self, live, V, front);
   } else if (DK == kOpen && y >= 1 && y + 1 < g.ny && z >= 1 && z + 1 < g.nz) {
     // On the open domain, words whose nine neighbour rows all lie inside the
     // grid (almost all of them) take a copy without the per-row bounds tests
     // and branches (4 % of the 400^3 growth time).  The torus and run-time
     // kinds keep one copy: there the second one costs more in register
     // spills than it saves.
-    row_masks<-1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<-1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<-1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, -1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, 0, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, 1, DK, true>(g, grid, y, z, r, xw, self, live, V, front);
   } else {
-    row_masks<-1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<-1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<0, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, -1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 0, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
-    row_masks<1, 1, DK>(g, grid, y, z, r, xw, self, live, V, Bm, front);
+    row_masks<-1, -1, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<-1, 0, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<-1, 1, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, -1, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, 0, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<0, 1, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, -1, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, 0, DK>(g, grid, y, z, r, xw, self, live, V, front);
+    row_masks<1, 1, DK>(g, grid, y, z, r, xw, self, live, V, front);
   }
   V[26] = 0;
   V[27] = 0;
+  growth_blocks(V, Bm);
 }
 
 // Bit j set: word j of r fails its threshold (r_j > T_j - 1), for the four
@@ -1696,6 +1795,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   uint32_t* claims = aux + (size_t)(t & 1u) * g.nwords;
   uint32_t* other = aux + (size_t)((t & 1u) ^ 1u) * g.nwords;  // cleared as in k_grow
+  uint32_t* touched = mark + bitmap_words(g);
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t rounds = (g.nwords + stride - 1) / stride;  // uniform: every lane loops alike
   uint32_t front_n = 0, live_n = 0;
@@ -1712,21 +1812,34 @@ __global__ void __launch_bounds__(256)
     const uint32_t len = min(32u, g.nx - x0);
     const uint32_t v0 = r * g.nx + x0;
 #pragma unroll
-    for (int b = 0; b < 7; ++b) {
-      live_n += __popc(Bm[b]);
-      const uint4 th = s_thr[b];
-      for (uint32_t i = 0; i < len; ++i) {
-        const U4 rnd = philox4x32_10(U4{v0 + i, 0u, t, kGrowTag | (uint32_t)b}, keys);
-        uint32_t win = (((V[4 * b] >> i) & 1u) & (rnd.x <= th.x ? 1u : 0u)) |
-                       ((((V[4 * b + 1] >> i) & 1u) & (rnd.y <= th.y ? 1u : 0u)) << 1) |
-                       ((((V[4 * b + 2] >> i) & 1u) & (rnd.z <= th.z ? 1u : 0u)) << 2) |
-                       ((((V[4 * b + 3] >> i) & 1u) & (rnd.w <= th.w ? 1u : 0u)) << 3);
-        while (win) {
-          const uint32_t j = __ffs(win) - 1;
-          win &= win - 1;
-          uint32_t wq, bit;
-          claim_target<kRuntime>(g, w, i, 4 * b + (int)j, wq, bit);
-          claim(claims, mark + bitmap_words(g), wq, bit);
+    for (int b = 0; b < 7; ++b) live_n += __popc(Bm[b]);
+    for (uint32_t i = 0; i < len; ++i) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        // The voxel's targets of class c (bit k: direction class_first_dir(c)
+        // + k); word j of block class_first_block(c) + kb is the one of rank
+        // 4 kb + j.
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < class_dirs(c); ++k) m |= ((V[class_first_dir(c) + k] >> i) & 1u) << k;
+        const uint32_t n = (uint32_t)__popc(m);
+#pragma unroll
+        for (int kb = 0; kb < (class_dirs(c) + 3) / 4; ++kb) {
+          const int b = class_first_block(c) + kb;
+          const uint4 th = s_thr[b];
+          const U4 rnd = philox4x32_10(U4{v0 + i, 0u, t, kGrowTag | (uint32_t)b}, keys);
+          uint32_t win = (rnd.x <= th.x ? 1u : 0u) | (rnd.y <= th.y ? 2u : 0u) |
+                         (rnd.z <= th.z ? 4u : 0u) | (rnd.w <= th.w ? 8u : 0u);
+          const uint32_t r0 = 4u * (uint32_t)kb;
+          win = n > r0 ? win & ((1u << min(4u, n - r0)) - 1u) : 0u;
+          while (win) {
+            const uint32_t j = __ffs(win) - 1;
+            win &= win - 1;
+            uint32_t wq, bit;
+            claim_target<kRuntime>(g, w, i, class_first_dir(c) + (int)nth_bit(m, r0 + j), wq,
+                                   bit);
+            claim(claims, touched, wq, bit);
+          }
         }
       }
     }

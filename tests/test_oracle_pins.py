@@ -508,36 +508,77 @@ def test_seeding_counter_layout(oracle, torch_philox):
     assert list(oracle.seed_candidates(p)) == want
 
 
+def _growth_step_by_layout(seeds, shape, p, thr, torch_philox, dirs, cls):
+    """One growth step from `seeds`, restated from R1: the targets of a
+    source are its in-domain neighbours that are void at the start of the
+    step (with a positive class threshold); the r-th target of class k (in
+    the canonical direction order) draws word r & 3 of the Philox block
+    (a, 0, t = 0, 0x200 | B_k + r >> 2), B = (0, 2, 5); a target is claimed
+    when some draw is below its class threshold."""
+    nz, ny, nx = shape
+    k0, k1 = p["seed"] & 0xFFFFFFFF, p["seed"] >> 32
+    first = (0, 2, 5)
+    want = seeds.copy()
+    for a in np.flatnonzero(seeds.ravel()):
+        z, y, x = a // (nx * ny), (a // nx) % ny, a % nx
+        blocks = torch_philox([(int(a), 0, 0, 0x200 | b, k0, k1) for b in range(7)])
+        rank = [0, 0, 0]
+        for d in range(26):
+            xx, yy, zz = x + dirs[d][0], y + dirs[d][1], z + dirs[d][2]
+            if not (0 <= xx < nx and 0 <= yy < ny and 0 <= zz < nz) or seeds[zz, yy, xx]:
+                continue
+            k = cls[d]
+            if thr[k] == 0:
+                continue
+            r = rank[k]
+            rank[k] += 1
+            if blocks[first[k] + (r >> 2)][r & 3] < thr[k]:
+                want[zz, yy, xx] = True
+    return want
+
+
 def test_growth_counter_layout(oracle, torch_philox):
-    # One step from isolated seeds: the claimed set is exactly the targets
-    # whose draw (word d&3 of block (a, 0, t, 0x200 | d>>2)) is below the
-    # class threshold.
+    # One step from isolated seeds (every interior neighbour a target) and
+    # from touching seeds (solid neighbours shift the ranks): the claimed set
+    # is exactly the one the R1 layout gives with the independent engine.
     dirs, cls = oracle.directions()
     checked = 0
     for seed in range(40):
-        p = dict(nx=16, ny=15, nz=14, cd=0.003, g_face=0.03, g_edge=0.02, g_corner=0.01,
-                 spacing_s=7, target_solid_fraction=0.9, seed=seed * 0x9E3779B97F4A7C15 % 2**64)
+        for spacing, cd in ((7, 0.003), (0, 0.06)):
+            p = dict(nx=16, ny=15, nz=14, cd=cd, g_face=0.03, g_edge=0.02, g_corner=0.01,
+                     spacing_s=spacing, target_solid_fraction=0.9,
+                     seed=seed * 0x9E3779B97F4A7C15 % 2**64)
+            seeds = _seeds_phase(oracle, p)
+            if not seeds.any():
+                continue
+            nt, _, t_ref = oracle.targets(p)
+            thr = [oracle.threshold(t_ref[k], nt, int(seeds.sum())) for k in range(3)]
+            want = _growth_step_by_layout(seeds, (14, 15, 16), p, thr, torch_philox, dirs, cls)
+            r = oracle.run(dict(p, max_steps=1))
+            assert np.array_equal(r.phase.astype(bool), want)
+            checked += 1
+    assert checked > 50
+
+
+def test_growth_layout_skips_dead_classes(oracle, torch_philox):
+    # A class with a zero threshold has no targets: the ranks of the live
+    # classes do not count its directions (edges only here).
+    dirs, cls = oracle.directions()
+    checked = 0
+    for seed in range(20):
+        p = dict(nx=12, ny=13, nz=11, cd=0.05, g_face=0.0, g_edge=0.3, g_corner=0.0,
+                 spacing_s=0, target_solid_fraction=0.95, seed=7 + seed)
         seeds = _seeds_phase(oracle, p)
         if not seeds.any():
             continue
         nt, _, t_ref = oracle.targets(p)
-        c0 = int(seeds.sum())
-        thr = [oracle.threshold(t_ref[k], nt, c0) for k in range(3)]
-        k0, k1 = p["seed"] & 0xFFFFFFFF, p["seed"] >> 32
-        want = seeds.copy()
-        for a in np.flatnonzero(seeds.ravel()):
-            z, y, x = a // (16 * 15), (a // 16) % 15, a % 16
-            blocks = torch_philox([(int(a), 0, 0, 0x200 | b, k0, k1) for b in range(7)])
-            for d in range(26):
-                xx, yy, zz = x + dirs[d][0], y + dirs[d][1], z + dirs[d][2]
-                if not (0 <= xx < 16 and 0 <= yy < 15 and 0 <= zz < 14):
-                    continue
-                if blocks[d >> 2][d & 3] < thr[cls[d]]:
-                    want[zz, yy, xx] = True
+        thr = [oracle.threshold(t_ref[k], nt, int(seeds.sum())) for k in range(3)]
+        assert thr[0] == 0 and thr[2] == 0 and thr[1] > 0
+        want = _growth_step_by_layout(seeds, (11, 13, 12), p, thr, torch_philox, dirs, cls)
         r = oracle.run(dict(p, max_steps=1))
         assert np.array_equal(r.phase.astype(bool), want)
         checked += 1
-    assert checked > 20
+    assert checked > 10
 
 
 # --------------------------------------------------------------------------
