@@ -208,9 +208,10 @@ int qsgs_query(qsgs_handle* h, qsgs_stats* out);
 /* Checkpoint and resume of a realization (Sec. 2.3, Algorithm 3: what one
  * growth step carries to the next is the phase array, the active front, the
  * step counter t and the solid count c_t; the front is a function of the
- * phase array, and every draw is keyed by (seed, voxel, t, direction), so a
- * realization resumed from a snapshot takes exactly the steps it would
- * have taken uninterrupted).
+ * phase array, and every draw is keyed by (seed, voxel, t) and the rank of
+ * its direction among the voxel's start-of-step targets, all of which the
+ * snapshot restores, so a realization resumed from a snapshot takes
+ * exactly the steps it would have taken uninterrupted).
  *
  * qsgs_snapshot_bytes: bytes of a snapshot of a realization with these
  * params (256-byte header, 256-byte run state, the packed grid: 512 + 4
