@@ -417,8 +417,8 @@ int qsgs_time_grow(qsgs_handle* h, uint32_t grow_blocks, uint32_t reps, double* 
  * the device.  The first call on a device does the set-up: it looks up the
  * scratch address with that device current (this may load the library's
  * device code), so make that first call before any stream capture.  Each
- * call zeroes the scratch
- * it uses (run state and tile status words) on the stream before the count.
+ * call zeroes the scratch it uses (run state and tile status words) on the
+ * stream before the count.
  * Calls share the one scratch per device: overlapping calls (other streams
  * or host threads) race and must be serialised by the caller.  The call
  * copies the count to the host and synchronises cuda_stream before it
