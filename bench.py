@@ -319,7 +319,7 @@ def bench_sweep(Q, torch, dev, tune_on: bool) -> dict:
 
 def bench_fullfield(Q, torch, dev, shape: dict) -> dict:
     """Comparator on the same 400^3 workload: the full-field sweep of
-    Algorithm 2 (every voxel draws every direction block each step) against
+    Algorithm 2 (every voxel draws all seven growth blocks each step) against
     the list-driven step, same realization bit for bit.  Device time of
     seeding through the exact target, L2 flushed before each run."""
     from paper_2602_11734_gb300 import tune
@@ -731,7 +731,7 @@ def main():
 
     # Kernel-level pass with the library's event profiler (not timed above).
     # k_grow is bound by integer ALU work: one Philox4x32-10 block per
-    # (front voxel, direction block) pair.  Its ceiling is the integer
+    # front voxel and four targets of a direction class.  Its ceiling is the integer
     # multiply rate derived from the SM count and the sampled clock; the
     # rate the library's Philox-only probe reaches on this GPU is reported
     # beside it.  The L2 roof of the method's per-step byte model is set

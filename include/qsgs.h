@@ -257,7 +257,8 @@ int qsgs_profile(qsgs_handle* h, qsgs_profile_entry* out, int max_entries);
 
 /* Calibration probe: times Philox4x32-10 blocks drawn as fast as the GPU
  * can, with no memory traffic -- the ALU ceiling of the growth step, whose
- * work is one Philox block per (front voxel, direction block) pair.
+ * work is one Philox block per front voxel and four targets of a direction
+ * class.
  *   n_blocks   blocks to time (rounded up to whole threads)
  *   dev_out    device, 8 bytes: receives a checksum (keeps the work live)
  *   cuda_stream  stream to run on (NULL = legacy default stream)
