@@ -908,49 +908,81 @@ __global__ void k_conflict_fill(Geom g, CellGeom cg, const RunState* st, const u
 // Rounds over the conflict lists (one block).  Each round settles at least
 // the lowest undecided candidate, so cand_n + 1 rounds always suffice.  The
 // decisions live in shared memory while they fit (kSpacingSmem candidates),
-// else in the global array; they are copied out at the end.
+// else in the global array; they are copied out at the end.  Thread t owns
+// candidates t + 1024 q; while there are at most 64 per thread (every
+// candidate count that fits in shared memory) it keeps its undecided ones
+// as a bit mask over q, so a round visits only undecided candidates, and
+// one barrier per round both orders the decisions and tells whether any
+// candidate is left.
 constexpr uint32_t kSpacingSmem = 64 * 1024;
+constexpr uint32_t kSpacingThreads = 1024;
 
-__global__ void __launch_bounds__(1024) k_spacing_rounds_csr(const RunState* st,
-                                                            const uint32_t* off,
-                                                            const uint32_t* adj,
-                                                            uint8_t* decision,
-                                                            unsigned long long cap) {
+// Settles candidate i if its earlier conflicts allow: 1 accepted (no
+// earlier conflict accepted or pending), 2 rejected (one accepted);
+// returns false while one is still pending.
+__device__ __forceinline__ bool spacing_settle(uint32_t i, uint32_t n, const uint32_t* off,
+                                               const uint32_t* adj, unsigned long long cap,
+                                               uint8_t* dec) {
+  bool pending = false;
+  const unsigned long long k_end = off[i + 1] < cap ? off[i + 1] : cap;
+  for (unsigned long long k = off[i]; k < k_end; ++k) {
+    const uint32_t j = adj[k];
+    if (j >= n) continue;  // only after a timed-out scan (reported)
+    const uint8_t dj = ((volatile uint8_t*)dec)[j];
+    if (dj == 1) {
+      dec[i] = 2;
+      return true;
+    }
+    if (dj == 0) pending = true;
+  }
+  if (pending) return false;
+  dec[i] = 1;
+  return true;
+}
+
+__global__ void __launch_bounds__(kSpacingThreads) k_spacing_rounds_csr(const RunState* st,
+                                                                       const uint32_t* off,
+                                                                       const uint32_t* adj,
+                                                                       uint8_t* decision,
+                                                                       unsigned long long cap) {
   extern __shared__ uint8_t s_decision[];
-  __shared__ uint32_t s_undecided;
   if (st->adj_n > cap) return;
   const uint32_t n = st->cand_n;
   const bool in_smem = n <= kSpacingSmem;
   uint8_t* dec = in_smem ? s_decision : decision;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dec[i] = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += kSpacingThreads) dec[i] = 0;
   __syncthreads();
-  for (uint32_t round = 0; round <= n; ++round) {
-    if (threadIdx.x == 0) s_undecided = 0;
-    __syncthreads();
-    uint32_t mine = 0;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      if (((volatile uint8_t*)dec)[i] != 0) continue;
-      bool pending = false, rejected = false;
-      const unsigned long long k_end = off[i + 1] < cap ? off[i + 1] : cap;
-      for (unsigned long long k = off[i]; k < k_end; ++k) {
-        const uint32_t j = adj[k];
-        if (j >= n) continue;  // only after a timed-out scan (reported)
-        const uint8_t dj = ((volatile uint8_t*)dec)[j];
-        if (dj == 1) { rejected = true; break; }
-        if (dj == 0) pending = true;
-      }
-      if (rejected) dec[i] = 2;
-      else if (!pending) dec[i] = 1;
-      else ++mine;
+  if (n <= 64u * kSpacingThreads) {
+    // und[h] bit q: candidate threadIdx.x + 1024 (32 h + q) is undecided.
+    const uint32_t mine = threadIdx.x < n ? (n - 1u - threadIdx.x) / kSpacingThreads + 1u : 0u;
+    uint32_t und[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t cnt = mine > 32u * h ? min(mine - 32u * h, 32u) : 0u;
+      und[h] = cnt == 32u ? 0xFFFFFFFFu : (1u << cnt) - 1u;
     }
-    if (mine) atomicAdd(&s_undecided, mine);
-    __syncthreads();
-    const uint32_t left = s_undecided;
-    __syncthreads();
-    if (left == 0) break;
+    for (uint32_t round = 0; round <= n; ++round) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        for (uint32_t m = und[h]; m; m &= m - 1) {
+          const uint32_t q = (uint32_t)__ffs(m) - 1u;
+          if (spacing_settle(threadIdx.x + kSpacingThreads * (32u * h + q), n, off, adj, cap, dec))
+            und[h] &= ~(1u << q);
+        }
+      }
+      if (!__syncthreads_or((und[0] | und[1]) != 0u)) break;
+    }
+  } else {
+    for (uint32_t round = 0; round <= n; ++round) {
+      bool left = false;
+      for (uint32_t i = threadIdx.x; i < n; i += kSpacingThreads)
+        if (((volatile uint8_t*)dec)[i] == 0 && !spacing_settle(i, n, off, adj, cap, dec))
+          left = true;
+      if (!__syncthreads_or(left)) break;
+    }
   }
   if (in_smem)
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) decision[i] = s_decision[i];
+    for (uint32_t i = threadIdx.x; i < n; i += kSpacingThreads) decision[i] = s_decision[i];
 }
 
 // Fallback when the conflict lists exceed their buffer: one block runs all
