@@ -554,14 +554,19 @@ def bench_batch(Q, torch, dev, tune_on: bool, repeats: int = 2) -> dict:
 
 SERVE_QUANTA = (2, 4, 8)           # growth steps per scheduling round
 SERVE_LOADS = (0.75, 1.0)          # Poisson arrival rates, fractions of saturation
+# The served configuration's full arrival-rate sweep, run at the default
+# quantum (the last of SERVE_QUANTA); the other quanta take SERVE_LOADS.
+SERVE_LOADS_SWEEP = (0.25, 0.5, 0.75, 0.9, 1.0, 1.2)
 SERVE_STREAMS = 8                  # concurrent single instances of the stream arm
 
 
-def bench_serve(torch, dev, n_requests: int, loads=SERVE_LOADS, quanta=SERVE_QUANTA) -> dict:
+def bench_serve(torch, dev, n_requests: int, loads=SERVE_LOADS, quanta=SERVE_QUANTA,
+                sweep=SERVE_LOADS_SWEEP) -> dict:
     """Continuous batching on the request mix (edge 64..512 with weights
     0.3/0.3/0.2/0.15/0.05, porosity U[0.08,0.30], spacing U{0..40}, cd 1e-4):
     per step quantum K, the closed-loop saturation rate (all requests at
-    t = 0), then Poisson arrivals at the given fractions of it.  Latency =
+    t = 0), then Poisson arrivals at fractions of it (`sweep` at the last,
+    default quantum, `loads` at the others).  Latency =
     arrival to the uint8 phase map in pinned host memory.  Beside it, the
     same requests on the plain single-instance path, one after another, and
     as single instances on SERVE_STREAMS concurrent streams (host threads),
@@ -591,7 +596,7 @@ def bench_serve(torch, dev, n_requests: int, loads=SERVE_LOADS, quanta=SERVE_QUA
     for k in quanta:
         sat = run([0.0] * n_requests, k)
         points = []
-        for f in loads:
+        for f in (sweep if k == quanta[-1] else loads):
             rate = f * sat["requests_per_s"]
             pt = run(workloads.poisson_arrivals(n_requests, rate), k)
             pt.update({"load": f, "arrival_rate_per_s": rate})
@@ -666,7 +671,7 @@ def main():
     if a.serve:
         build.build()
         Q.load_library()
-        res = bench_serve(torch, dev, 2000, (0.25, 0.5, 0.75, 0.9, 1.0, 1.2), (8,))
+        res = bench_serve(torch, dev, 2000, quanta=(8,))
         if rank == 0:
             sat = res["by_quantum"][0]["saturation"]
             print(json.dumps({"metric": "requests/s", "value": sat["requests_per_s"],
