@@ -121,24 +121,15 @@ inline PhiloxKeys make_philox_keys(uint64_t seed) {
   return k;
 }
 
-// Philox4x32-10 with precomputed round keys.  QSGS_PHILOX_HILO selects
-// separate 32-bit high and low products instead of 64-bit multiplies.
-#ifndef QSGS_PHILOX_HILO
-#define QSGS_PHILOX_HILO 0
-#endif
+// Philox4x32-10 with precomputed round keys (each round's two products as
+// 64-bit multiplies; separate 32-bit high and low products measured slower).
 __device__ __forceinline__ U4 philox4x32_10(U4 c, const PhiloxKeys& key) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-#if QSGS_PHILOX_HILO
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = U4{hi1 ^ c.y ^ key.k0[i], lo1, hi0 ^ c.w ^ key.k1[i], lo0};
-#else
     const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
     const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
     c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ key.k0[i], (uint32_t)p1,
            (uint32_t)(p0 >> 32) ^ c.w ^ key.k1[i], (uint32_t)p0};
-#endif
   }
   return c;
 }

@@ -1083,9 +1083,6 @@ constexpr int kGrowWarps = kGrowThreads / 32;
 #define QSGS_GROW_MIN_BLOCKS 3  // resident blocks per SM the register budget aims for
 #endif
 constexpr int kGrowEntries = 7 * 32 + 1;  // non-empty masks of a chunk, plus one spare
-#ifndef QSGS_GROW_THR_CURSOR
-#define QSGS_GROW_THR_CURSOR 0
-#endif
 constexpr int kGrowWins = 256;            // deferred claims buffered per warp
 
 struct GrowWarpSmem {
@@ -1641,10 +1638,6 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
   uint4 E = S.E[k];
   uint32_t m = E.x;
   for (uint32_t j = S.P[k]; j < s; ++j) m ^= bit_at(top_bit(m));  // pairs before s
-#if QSGS_GROW_THR_CURSOR
-  // The complemented thresholds of the cursor's entry, loaded once per entry.
-  uint4 th = nthr[E.z & 7u];
-#endif
   // Each lane draws two pairs per iteration (two independent Philox chains
   // in flight hide the multiply latency).  After a lane's pair empties the
   // cursor's mask the cursor moves to the next entry (index at most n_ent:
@@ -1658,38 +1651,21 @@ __device__ __forceinline__ void grow_chunk(const Geom& g, const uint32_t* __rest
     const uint32_t ia = top_bit(m);
     m ^= bit_at(ia);
     const uint32_t xa = E.y + ia, cwa = E.z, ta = E.w | ia;
-#if QSGS_GROW_THR_CURSOR
-    const uint4 tha = th;
-#endif
     if (va && m == 0) {
       E = S.E[++k];
       m = E.x;
-#if QSGS_GROW_THR_CURSOR
-      th = nthr[E.z & 7u];
-#endif
     }
     const uint32_t ib = top_bit(m);
     m ^= bit_at(ib);
     const uint32_t xb = E.y + ib, cwb = E.z, tb = E.w | ib;
-#if QSGS_GROW_THR_CURSOR
-    const uint4 thb = th;
-#endif
     if (vb && m == 0) {
       E = S.E[++k];
       m = E.x;
-#if QSGS_GROW_THR_CURSOR
-      th = nthr[E.z & 7u];
-#endif
     }
     const U4 ra = philox4x32_10(U4{xa, 0u, t, cwa}, keys);
     const U4 rb = philox4x32_10(U4{xb, 0u, t, cwb}, keys);
-#if QSGS_GROW_THR_CURSOR
-    const uint32_t pa = va ? fail_bits(ra, tha) ^ 0xFu : 0u;  // passing words
-    const uint32_t pb = vb ? fail_bits(rb, thb) ^ 0xFu : 0u;
-#else
     const uint32_t pa = va ? fail_bits(ra, nthr[cwa & 7u]) ^ 0xFu : 0u;  // passing words
     const uint32_t pb = vb ? fail_bits(rb, nthr[cwb & 7u]) ^ 0xFu : 0u;
-#endif
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t bala = __ballot_sync(0xffffffffu, pa != 0);
     const uint32_t balb = __ballot_sync(0xffffffffu, pb != 0);
