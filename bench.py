@@ -829,6 +829,11 @@ def main():
         cpu = finish_cpu_baseline(cpu_handle, p)
     batched = served = sweep = sizes = fullfield = fontainebleau = phases = None
     del g
+    # The single-GPU reports below run at N = 1 only: under torchrun they
+    # would hold every rank's GPU for minutes and repeat the same figures.
+    if world > 1:
+        a.no_phases = a.no_fontainebleau = a.no_fullfield = a.no_sweep = True
+        a.no_sizes = a.no_batch = a.no_serve = True
     if not a.no_phases and a.edge == 400:
         phases = bench_phases(Q, torch, dev)
     if not a.no_fontainebleau and a.edge == 400:
