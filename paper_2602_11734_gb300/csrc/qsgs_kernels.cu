@@ -612,6 +612,26 @@ struct FrontCountInterPolicy {
   __device__ void total(unsigned long long) const {}
 };
 
+// A count policy's side sum without the ordered scan: nothing is emitted,
+// so no tile waits on its predecessors.  Each warp takes 32 consecutive
+// items per iteration (the front policies' neighbour shuffles need
+// consecutive words in consecutive lanes) and adds its warp total with one
+// atomic.
+template <class Policy>
+__global__ void __launch_bounds__(256) k_side_sum(Policy pol) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = pol.n_items();
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long sum = 0;
+  for (uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; w0 < n;
+       w0 += nwarps * 32u) {
+    const uint32_t w = w0 + lane;
+    sum += pol.side(pol.load(w, w < n), 0);
+  }
+  const unsigned long long ws = __reduce_add_sync(0xffffffffu, (uint32_t)sum);
+  if (lane == 0 && ws) atomicAdd(pol.side_sum(0), ws);
+}
+
 // The exact-target trim, once, after the step that overshot Nt.  The claim
 // grid of that step holds exactly New_t (every success targets a voxel that
 // was void when the step began); of New_t in ascending order only the first
@@ -2057,6 +2077,12 @@ static uint32_t scan_grid(uint64_t max_items) {
   return (uint32_t)(blocks ? blocks : 1);
 }
 
+static uint32_t side_sum_grid(uint64_t nwords) {
+  const uint64_t need = (nwords + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 4;
+  return (uint32_t)(need < cap ? (need ? need : 1) : cap);
+}
+
 static uint32_t seed_bits_grid(uint64_t nwords) {
   const uint64_t need = (nwords + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 8;  // 8 blocks of 256 threads per SM
@@ -2269,16 +2295,16 @@ cudaError_t launch_epilogue(const Geom& g, const StepBuffers& b, uint32_t spin_l
   QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<TrimPolicy>, scan_grid(g.nwords), kScanThreads, tp,
               ctl);
   QSGS_LAUNCH(tr, kClsTrim, s, k_zero_front, 1, 1, b.st);
+  // The final front count (a statistic): an unordered sum over all words.
   if (b.enter) {  // an interacting phase counts enterable neighbours too
     FrontCountInterPolicy fi{geom_inter(g, b), b.st, b.grid};
-    QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontCountInterPolicy>, scan_grid(g.nwords),
-                kScanThreads, fi, ctl);
+    QSGS_LAUNCH(tr, kClsTrim, s, k_side_sum<FrontCountInterPolicy>, side_sum_grid(g.nwords), 256,
+                fi);
     QSGS_LAUNCH(tr, kClsTrim, s, k_trim_done, 1, 1, b.st);
     return cudaSuccess;
   }
   FrontCountPolicy fp{g, b.st, b.grid};
-  QSGS_LAUNCH(tr, kClsTrim, s, k_lookback_scan<FrontCountPolicy>, scan_grid(g.nwords),
-              kScanThreads, fp, ctl);
+  QSGS_LAUNCH(tr, kClsTrim, s, k_side_sum<FrontCountPolicy>, side_sum_grid(g.nwords), 256, fp);
   QSGS_LAUNCH(tr, kClsTrim, s, k_trim_done, 1, 1, b.st);
   return cudaSuccess;
 }
