@@ -9,6 +9,11 @@
         Per growth step of one realization: the front, the solid count and
         the event-timed device time of the growth and commit kernels (the
         library's event profiler, one step per call), as one JSON line.
+    python -m paper_2602_11734_gb300.probe batch [--start 20] [--steps 2]
+        The 96-member batch workload seeded, then advanced `start` steps and
+        `steps` more with direct launches (one batched growth launch per
+        step): a profiler capture of the batched growth kernel skips `start`
+        launches (e.g. ncu -k regex:k_grow_batch -s 20 -c 2).
 
 Both run the CUDA library only; nothing here computes voxels.
 """
@@ -32,6 +37,25 @@ def grow(edge: int, start: int, steps: int) -> dict:
         return {"steps": st.steps, "front": st.front_size, "solid": st.solid_count}
     finally:
         g.close()
+
+
+def batch(start: int, steps: int) -> dict:
+    params = W.batch_96()
+    gens = [Q.Generator(p) for p in params]
+    b = Q.Batch(len(params), sum(Q.word_count(p) for p in params))
+    try:
+        b.set_members(gens)
+        b.seed()
+        b.set_profiling(True)  # direct launches: every batch step is one growth launch
+        b.advance(start)
+        b.advance(steps)
+        st = b.query()
+        return {"members": len(st), "steps": max(x.steps for x in st),
+                "solid": sum(x.solid_count for x in st)}
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
 
 
 def steps(params: dict) -> dict:
@@ -60,7 +84,7 @@ def steps(params: dict) -> dict:
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=("grow", "steps"))
+    ap.add_argument("mode", choices=("grow", "steps", "batch"))
     ap.add_argument("--edge", type=int, default=400)
     ap.add_argument("--start", type=int, default=30)
     ap.add_argument("--steps", type=int, default=2)
@@ -72,6 +96,8 @@ def main() -> int:
     Q.load_library()
     if a.mode == "grow":
         out = grow(a.edge, a.start, a.steps)
+    elif a.mode == "batch":
+        out = batch(a.start, a.steps)
     else:
         params = W.fig3_size(a.fig3, True) if a.fig3 else getattr(W, a.workload)()
         out = dict(steps(params), workload=f"fig3_{a.fig3}" if a.fig3 else a.workload)
