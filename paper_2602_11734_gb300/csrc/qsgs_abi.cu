@@ -299,7 +299,7 @@ cudaError_t build_graph(qsgs_handle* h) {
 constexpr uint32_t kSeedStreams = 8;  // members seeded concurrently
 
 struct BatchLayout {
-  size_t state, descs, list, total;
+  size_t state, descs, states, list, total;
 };
 
 BatchLayout make_batch_layout(uint32_t max_members, uint64_t max_words) {
@@ -307,6 +307,7 @@ BatchLayout make_batch_layout(uint32_t max_members, uint64_t max_words) {
   size_t off = 0;
   L.state = off; off = align_up(off + sizeof(BatchState));
   L.descs = off; off = align_up(off + (size_t)max_members * sizeof(MemberDesc));
+  L.states = off; off = align_up(off + (size_t)max_members * sizeof(RunState));
   L.list = off; off = align_up(off + (max_words ? max_words : 1) * 4);
   L.total = off;
   return L;
@@ -1051,10 +1052,13 @@ int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n) {
   if (!b || (n && !per_member)) return QSGS_ERR_INVALID;
   const size_t nm = b->members.size();
   b->host_states.resize(nm);
+  // Every member's run state, gathered on the device, in one copy.
+  RunState* gathered = reinterpret_cast<RunState*>(b->ws + b->L.states);
   auto read_all = [&]() -> cudaError_t {
-    cudaError_t e = cudaSuccess;
-    for (size_t m = 0; m < nm && e == cudaSuccess; ++m)
-      e = cudaMemcpyAsync(&b->host_states[m], b->members[m]->st, sizeof(RunState),
+    cudaError_t e = launch_batch_gather_states(b->buf, (uint32_t)nm, gathered, b->stream,
+                                               b->tracer);
+    if (e == cudaSuccess && nm)
+      e = cudaMemcpyAsync(b->host_states.data(), gathered, nm * sizeof(RunState),
                           cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e;

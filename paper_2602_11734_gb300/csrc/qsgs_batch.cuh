@@ -235,6 +235,14 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+// Block per member: its run state into out[m] (16 threads, 16 bytes each),
+// so that the host reads every member's state with one copy.
+__global__ void __launch_bounds__(16) k_batch_gather_states(const MemberDesc* d, RunState* out) {
+  const uint4* src = reinterpret_cast<const uint4*>(d[blockIdx.x].st);
+  reinterpret_cast<uint4*>(out + blockIdx.x)[threadIdx.x] = src[threadIdx.x];
+}
+static_assert(sizeof(RunState) == 16 * sizeof(uint4), "one uint4 per gather thread");
+
 // Thread per member: per-member step budget of this advance.
 __global__ void k_batch_limits(MemberDesc* d, BatchState* bs) {
   for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < bs->n_members;

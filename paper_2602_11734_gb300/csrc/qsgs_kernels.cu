@@ -2516,6 +2516,12 @@ cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cu
   return cudaSuccess;
 }
 
+cudaError_t launch_batch_gather_states(const BatchBuffers& b, uint32_t n, RunState* out,
+                                       cudaStream_t s, Tracer& tr) {
+  if (n) QSGS_LAUNCH(tr, kClsStepCtl, s, k_batch_gather_states, n, 16, b.d, out);
+  return cudaSuccess;
+}
+
 cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowShape shape,
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,
                               int use_cond) {

@@ -195,6 +195,9 @@ struct BatchBuffers {
 // use_cond is set).
 cudaError_t launch_batch_prologue(const BatchBuffers& b, uint32_t spin_limit, cudaStream_t s,
                                   Tracer& tr, cudaGraphConditionalHandle cond, int use_cond);
+// Run states of members 0 .. n-1 into out[0 .. n) (device).
+cudaError_t launch_batch_gather_states(const BatchBuffers& b, uint32_t n, RunState* out,
+                                       cudaStream_t s, Tracer& tr);
 // One step of every member that runs: batched growth, commit and control.
 cudaError_t launch_batch_step(const BatchBuffers& b, uint32_t spin_limit, GrowShape shape,
                               cudaStream_t s, Tracer& tr, cudaGraphConditionalHandle cond,

@@ -142,6 +142,7 @@ class Server:
                 self._admit(r, clock())
                 joined.append(r)
                 qi += 1
+            finished = []
             if in_flight:
                 stats = self.batch.query()        # waits for the round
                 in_flight = False
@@ -150,7 +151,7 @@ class Server:
                     if st.status == Q.QSGS_RUNNING:
                         still.append(r)
                     else:
-                        self._retire(r, st, clock)
+                        finished.append((r, st))
                 running = still
             if joined or len(running) != len(self.batch.members):
                 running = running + joined
@@ -159,7 +160,11 @@ class Server:
                 self.batch.advance(self.step_quantum)
                 in_flight = True
                 self.rounds += 1
-            elif qi < len(pending):
+            # The finished requests left the batch above; their maps are
+            # fetched on their own streams while the next round runs.
+            for r, st in finished:
+                self._retire(r, st, clock)
+            if not running and not finished and qi < len(pending):
                 time.sleep(max(0.0, min(0.001, pending[qi].arrival - clock())))
         return requests
 
