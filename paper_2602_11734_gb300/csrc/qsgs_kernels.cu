@@ -1422,28 +1422,32 @@ __device__ __forceinline__ void claim(uint32_t* claims, uint32_t* touched, uint3
   atomicOr(touched + (wq >> 5), 1u << (wq & 31u));
 }
 
+// The claims of one buffered draw x (tag | bit | pass bits << 16).
+template <int DK>
+__device__ __forceinline__ void claim_entry(const Geom& g, uint32_t* claims, uint32_t* touched,
+                                            const GrowWarpSmem& S, uint32_t x) {
+  const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
+  // Word j of block b is the voxel's target of rank r0 + j of class c.
+  const int c = block_class((int)b);
+  const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(c));
+  const uint32_t m = class_targets(S.V[owner], i, c);
+  const uint32_t n = (uint32_t)__popc(m);
+  uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
+  const uint32_t wo = S.w[owner];
+  while (win) {
+    const uint32_t j = __ffs(win) - 1;
+    win &= win - 1;
+    const int d = class_first_dir(c) + (int)nth_bit(m, r0 + j);
+    uint32_t wq, bit;
+    claim_target<DK>(g, wo, i, d, wq, bit);
+    claim(claims, touched, wq, bit);
+  }
+}
+
 template <int DK>
 __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, uint32_t* touched,
                                            const GrowWarpSmem& S, uint32_t nwin, uint32_t lane) {
-  for (uint32_t k = lane; k < nwin; k += 32) {
-    const uint32_t x = S.win[k];
-    const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
-    // Word j of block b is the voxel's target of rank r0 + j of class c.
-    const int c = block_class((int)b);
-    const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(c));
-    const uint32_t m = class_targets(S.V[owner], i, c);
-    const uint32_t n = (uint32_t)__popc(m);
-    uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
-    const uint32_t wo = S.w[owner];
-    while (win) {
-      const uint32_t j = __ffs(win) - 1;
-      win &= win - 1;
-      const int d = class_first_dir(c) + (int)nth_bit(m, r0 + j);
-      uint32_t wq, bit;
-      claim_target<DK>(g, wo, i, d, wq, bit);
-      claim(claims, touched, wq, bit);
-    }
-  }
+  for (uint32_t k = lane; k < nwin; k += 32) claim_entry<DK>(g, claims, touched, S, S.win[k]);
 }
 
 // Claims of an interacting phase (R13).  The draw loop tested a block's
@@ -1452,42 +1456,48 @@ __device__ __forceinline__ void claim_wins(const Geom& g, uint32_t* claims, uint
 // cent of the pairs) and each candidate direction is tested against its own
 // target's threshold: Eq. 1 for a void cell, I^{n,m} for a cell of phase m.
 template <int DK>
+__device__ __forceinline__ void claim_entry_inter(const Geom& g, uint32_t* claims,
+                                                  uint32_t* touched, const GrowWarpSmem& S,
+                                                  uint32_t x, uint32_t t, const PhiloxKeys& keys,
+                                                  const uint4* nthr) {
+  const GeomInter& gi = static_cast<const GeomInter&>(g);  // the kind's own geometry
+  const uint4 eq1 = nthr[7];  // Eq. 1 thresholds T - 1 per class (load_thresholds_inter)
+  const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
+  // Word j of block b is the voxel's target of rank r0 + j of class c.
+  const int cb = block_class((int)b);
+  const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(cb));
+  const uint32_t m = class_targets(S.V[owner], i, cb);
+  const uint32_t n = (uint32_t)__popc(m);
+  uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
+  if (!win) return;
+  const uint32_t wo = S.w[owner];
+  const uint32_t ro = fast_div(wo, g.div_W);
+  const uint32_t v = ro * g.nx + (wo - ro * g.W) * 32u + i;
+  const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
+  while (win) {
+    const uint32_t j = __ffs(win) - 1;
+    win &= win - 1;
+    const int d = class_first_dir(cb) + (int)nth_bit(m, r0 + j);
+    uint32_t wq, bit;
+    claim_target<DK>(g, wo, i, d, wq, bit);
+    const uint32_t rq = fast_div(wq, g.div_W);
+    const uint32_t q = rq * g.nx + (wq - rq * g.W) * 32u + (uint32_t)(__ffs(bit) - 1);
+    const uint32_t lab = gi.labels[q];
+    const int c = dir_cls(d);
+    const uint32_t th = lab ? gi.enter_thr[lab * 3u + (uint32_t)c]
+                            : (c == 0 ? eq1.x : (c == 1 ? eq1.y : eq1.z));
+    if (u4_word(rnd, (int)j) <= th) claim(claims, touched, wq, bit);
+  }
+}
+
+template <int DK>
 __device__ __forceinline__ void claim_wins_inter(const Geom& g, uint32_t* claims,
                                                  uint32_t* touched, const GrowWarpSmem& S,
                                                  uint32_t nwin,
                                                  uint32_t lane, uint32_t t,
                                                  const PhiloxKeys& keys, const uint4* nthr) {
-  const GeomInter& gi = static_cast<const GeomInter&>(g);  // the kind's own geometry
-  const uint4 eq1 = nthr[7];  // Eq. 1 thresholds T - 1 per class (load_thresholds_inter)
-  for (uint32_t k = lane; k < nwin; k += 32) {
-    const uint32_t x = S.win[k];
-    const uint32_t owner = (x >> 8) & 31u, b = (x >> 5) & 7u, i = x & 31u;
-    // Word j of block b is the voxel's target of rank r0 + j of class c.
-    const int cb = block_class((int)b);
-    const uint32_t r0 = 4u * (b - (uint32_t)class_first_block(cb));
-    const uint32_t m = class_targets(S.V[owner], i, cb);
-    const uint32_t n = (uint32_t)__popc(m);
-    uint32_t win = n > r0 ? (x >> 16) & ((1u << min(4u, n - r0)) - 1u) : 0u;
-    if (!win) continue;
-    const uint32_t wo = S.w[owner];
-    const uint32_t ro = fast_div(wo, g.div_W);
-    const uint32_t v = ro * g.nx + (wo - ro * g.W) * 32u + i;
-    const U4 rnd = philox4x32_10(U4{v, 0u, t, kGrowTag | b}, keys);
-    while (win) {
-      const uint32_t j = __ffs(win) - 1;
-      win &= win - 1;
-      const int d = class_first_dir(cb) + (int)nth_bit(m, r0 + j);
-      uint32_t wq, bit;
-      claim_target<DK>(g, wo, i, d, wq, bit);
-      const uint32_t rq = fast_div(wq, g.div_W);
-      const uint32_t q = rq * g.nx + (wq - rq * g.W) * 32u + (uint32_t)(__ffs(bit) - 1);
-      const uint32_t lab = gi.labels[q];
-      const int c = dir_cls(d);
-      const uint32_t th = lab ? gi.enter_thr[lab * 3u + (uint32_t)c]
-                              : (c == 0 ? eq1.x : (c == 1 ? eq1.y : eq1.z));
-      if (u4_word(rnd, (int)j) <= th) claim(claims, touched, wq, bit);
-    }
-  }
+  for (uint32_t k = lane; k < nwin; k += 32)
+    claim_entry_inter<DK>(g, claims, touched, S, S.win[k], t, keys, nthr);
 }
 
 // Bit-parallel over the 32 voxels of word w: the 26 void-target masks V_d
