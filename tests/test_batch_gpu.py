@@ -59,6 +59,27 @@ def test_batch_of_uneven_small_realizations(oracle, Q):
             g.close()
 
 
+def test_batch_at_the_member_limit(oracle, Q):
+    # 1024 members (the most a batch takes): one control thread and one
+    # state-gather block per member.  Each member must match the oracle, and
+    # the batch's gathered statistics must equal each handle's own query.
+    rng = np.random.default_rng(4242)
+    params = [workloads.random_small(rng, max_edge=12) for _ in range(1024)]
+    b, gens = make_batch(Q, params)
+    try:
+        stats = b.run()
+        assert len(stats) == 1024
+        for g, st, p in zip(gens, stats, params):
+            check_member(oracle, g, st, p)
+            own = g.query()
+            assert (own.solid_count, own.steps, own.status, own.front_size, own.sum_front) == \
+                   (st.solid_count, st.steps, st.status, st.front_size, st.sum_front), p
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
+
+
 def test_batch_equals_single_path(Q):
     params = [dict(workloads.single_400(), nx=e, ny=e - 3, nz=e + 5, seed=s,
                    target_solid_fraction=0.7 + 0.02 * s)
