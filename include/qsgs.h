@@ -479,7 +479,9 @@ int qsgs_batch_advance(qsgs_batch* b, uint32_t max_steps);
 
 /* Waits for the batch stream, runs the exact-target trim and the final
  * front count of members whose run has ended, and fills per_member[0..n)
- * (host array, may be NULL if n = 0) in member order.  Returns QSGS_OK,
+ * (host array, may be NULL if n = 0) in member order.  The members' run
+ * states are gathered into the batch workspace on the batch stream and read
+ * with one copy.  Returns QSGS_OK,
  * QSGS_ERR_TIMEOUT, QSGS_ERR_INVALID or QSGS_ERR_CUDA. */
 int qsgs_batch_query(qsgs_batch* b, qsgs_stats* per_member, uint32_t n);
 
