@@ -104,83 +104,40 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-// Step commit of the batch (the work of k_commit, per member) over the
-// batch word space: a warp takes 8 consecutive 32-word groups per
-// iteration.  When they belong to one member (all but the groups at member
-// boundaries) their loads are issued together and list space is reserved
-// with one atomic; as in k_commit, a member whose step list is under
+// Step commit of the batch (the work of k_commit, per member): a warp
+// takes one super-group of 8 consecutive 32-word groups of one member per
+// iteration, over the super-groups of the members that run the step only
+// (laid out by k_batch_control: member m's start at commit_base(m)).  The
+// group loads are issued together and list space is reserved with one
+// atomic; as in k_commit, a member whose step list is under
 // 1/kSparseFraction of its words takes the sparse path (bitmaps first, then
 // only marked or touched words), the others the dense one (everything at
 // once).  Member m's list entries (member-local word indices, any order) go
 // to the batch list from word_base(m) on, counted by its list_next.
-
-// One 32-word group of member md (the slow path, at member boundaries).
-__device__ __forceinline__ void batch_commit_group(const MemberDesc& md, uint32_t gs,
-                                                   uint32_t* list) {
-  const uint32_t lane = threadIdx.x & 31u;
-  RunState* st = md.st;
-  if (!st->active) return;  // uniform
-  const uint32_t w = gs + lane - md.word_base;
-  const bool in = gs + lane < md.word_end;
-  const uint32_t jl = (gs - md.word_base) >> 5;
-  uint32_t* touched = md.mark + bitmap_words(md.g);
-  uint32_t mk = 0;
-  if (lane == 0) {
-    mk = md.mark[jl];
-    const uint32_t tc = touched[jl];
-    if (mk) md.mark[jl] = 0u;
-    if (tc) touched[jl] = 0u;
-  }
-  mk = __shfl_sync(0xffffffffu, mk, 0);
-  const uint32_t* claims = md.aux + (size_t)(st->t & 1u) * md.g.nwords;
-  const uint32_t c = in ? claims[w] : 0u;
-  const uint32_t old = in ? md.grid[w] : 0u;
-  if (c) md.grid[w] = old | c;
-  const bool keep = in && (((mk >> lane) & 1u) || c != 0);  // touched = claimed
-  const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(c));
-  if (lane == 0 && wc) atomicAdd(&st->claimed, (unsigned long long)wc);
-  const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-  uint32_t base = 0;
-  if (lane == 0 && bal) base = atomicAdd(&st->list_next, (uint32_t)__popc(bal));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (keep) list[md.word_base + base + __popc(bal & ((1u << lane) - 1u))] = w;
-}
-
 __global__ void __launch_bounds__(256, 2)
     k_batch_commit(const MemberDesc* __restrict__ d, const BatchState* bs, uint32_t* list) {
   constexpr int G = kBatchCommitGroups;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = bs->n_members;
   if (n == 0) return;
-  const uint32_t ngroups = bs->total_words / 32u;  // member ranges are 32-aligned
-  const uint32_t nsuper = (ngroups + G - 1) / G;
+  const uint32_t nsuper = bs->total_supers;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nsuper; sg += nwarps) {
-    const uint32_t g0 = sg * G;
-    const uint32_t glast = min(g0 + G, ngroups) - 1;
+    // The member whose super-groups hold sg: the last one starting at or
+    // before it (members that do not run have none, so never end there).
     uint32_t mm = 0;
-    if (lane < 2)
-      mm = find_member(d, n, (lane ? glast : g0) * 32u,
-                       [](const MemberDesc& x) { return x.word_base; });
+    if (lane == 0) mm = find_member(d, n, sg, [](const MemberDesc& x) { return x.commit_base; });
     const uint32_t m0 = __shfl_sync(0xffffffffu, mm, 0);
-    const uint32_t m1 = __shfl_sync(0xffffffffu, mm, 1);
-    if (m0 != m1) {
-      uint32_t m = m0;
-      for (uint32_t gi = g0; gi <= glast; ++gi) {
-        while (m + 1 < n && d[m + 1].word_base <= gi * 32u) ++m;  // uniform
-        batch_commit_group(d[m], gi * 32u, list);
-      }
-      continue;
-    }
     const MemberDesc& md = d[m0];
     RunState* st = md.st;
-    if (!st->active) continue;
     const uint32_t nloc = md.word_end - md.word_base;
-    const uint32_t lw0 = g0 * 32u - md.word_base;  // member-local first word
+    const uint32_t ngl = (nloc + 31u) / 32u;                  // the member's groups
+    const uint32_t lg0 = (sg - md.commit_base) * (uint32_t)G;  // its first group here
+    const uint32_t lw0 = lg0 * 32u;                           // member-local first word
     uint32_t* touched = md.mark + bitmap_words(md.g);
     const uint32_t* cur = md.aux + (size_t)(st->t & 1u) * md.g.nwords;
     const bool sparse = commit_is_sparse(st->front_words, nloc);
-    const bool jv = lane < (uint32_t)G && g0 + lane <= glast;
+    const bool jv = lane < (uint32_t)G && lg0 + lane < ngl;
     const uint32_t jl = (lw0 >> 5) + lane;
     const uint32_t mk = jv ? md.mark[jl] : 0u, tc = jv ? touched[jl] : 0u;
     uint32_t c[G], old[G], bal[G];
@@ -200,7 +157,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t w = lw0 + j * 32u + lane;
-        const bool in = g0 + j <= glast && w < nloc;
+        const bool in = w < nloc;  // groups past the member's last hold no words
         c[j] = in ? cur[w] : 0u;
         old[j] = in ? md.grid[w] : 0u;
       }
@@ -256,14 +213,14 @@ __global__ void k_batch_limits(MemberDesc* d, BatchState* bs) {
 __global__ void __launch_bounds__(kMaxBatchMembers)
     k_batch_control(MemberDesc* d, BatchState* bs, cudaGraphConditionalHandle cond, int use_cond,
                     int prologue) {
-  __shared__ uint32_t s_warp[kMaxBatchMembers / 32];
+  __shared__ unsigned long long s_warp[kMaxBatchMembers / 32];
   __shared__ uint32_t s_active;
   const uint32_t n = bs->n_members;
   const uint32_t m = threadIdx.x;
   const uint32_t lane = m & 31u, warp = m >> 5;
   if (m == 0) s_active = 0;
   __syncthreads();
-  uint32_t chunks = 0;
+  uint32_t chunks = 0, supers = 0;
   if (m < n) {
     RunState* st = d[m].st;
     const uint32_t list_n = st->list_next;  // appended by the commit just before
@@ -279,31 +236,42 @@ __global__ void __launch_bounds__(kMaxBatchMembers)
     d[m].list_n = list_n;
     if (st->active) {
       chunks = (list_n + 31u) / 32u;
+      const uint32_t groups = (d[m].word_end - d[m].word_base + 31u) / 32u;
+      supers = (groups + kBatchCommitGroups - 1u) / kBatchCommitGroups;
       s_active = 1;  // benign race: every writer stores 1
     }
   }
-  // Block-wide exclusive scan of the chunk counts.
-  uint32_t incl = chunks;
+  // Block-wide exclusive scan of the growth chunk counts (low half) and the
+  // commit super-group counts (high half) of the members that run the step.
+  const unsigned long long mine = chunks | ((unsigned long long)supers << 32);
+  unsigned long long incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= (uint32_t)o) incl += y;
   }
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t x = s_warp[lane];
+    unsigned long long x = s_warp[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= (uint32_t)o) x += y;
     }
     s_warp[lane] = x;  // inclusive warp totals
   }
   __syncthreads();
-  const uint32_t excl = (warp ? s_warp[warp - 1] : 0u) + incl - chunks;
-  if (m < n) d[m].chunk_base = excl;
-  if (m == kMaxBatchMembers - 1) bs->total_chunks = s_warp[kMaxBatchMembers / 32 - 1];
+  const unsigned long long excl = (warp ? s_warp[warp - 1] : 0ull) + incl - mine;
+  if (m < n) {
+    d[m].chunk_base = (uint32_t)excl;
+    d[m].commit_base = (uint32_t)(excl >> 32);
+  }
+  if (m == kMaxBatchMembers - 1) {
+    const unsigned long long tot = s_warp[kMaxBatchMembers / 32 - 1];
+    bs->total_chunks = (uint32_t)tot;
+    bs->total_supers = (uint32_t)(tot >> 32);
+  }
   if (m == 0) {
     bs->scan.iters += 1;  // control launches of this batch (launch accounting)
     bs->any_active = s_active;

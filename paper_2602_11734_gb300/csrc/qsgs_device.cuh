@@ -265,7 +265,8 @@ struct alignas(16) MemberDesc {
   uint32_t list_base;   // first entry in the batch candidate list
   uint32_t list_n;      // entries of this member
   uint32_t chunk_base;  // first growth chunk (32 entries) of this member
-  uint32_t pad_[3];
+  uint32_t commit_base; // first commit super-group of this member (0 groups if it does not run)
+  uint32_t pad_[2];
 };
 
 struct BatchState {
@@ -275,7 +276,8 @@ struct BatchState {
   uint32_t total_chunks;  // growth chunks of this step
   uint32_t any_active;    // some member runs the next step
   uint32_t step_extra;    // per-member step budget of the current advance (0: none)
-  uint32_t pad_[3];
+  uint32_t total_supers;  // commit super-groups of the members that run this step
+  uint32_t pad_[2];
 };
 
 }  // namespace qsgs
