@@ -154,3 +154,47 @@ def test_summary_when_every_request_is_rejected(monkeypatch):
     s = S.summarize(reqs)
     assert s["requests"] == 0 and s["rejected"] == 3
     assert s["p50_ms"] is None and s["p99_ms"] is None and s["requests_per_s"] is None
+
+
+def test_next_round_starts_before_finished_maps_are_fetched(monkeypatch):
+    # After a round, requests that finished leave the batch and the next
+    # round is launched first; their maps are fetched while it runs.  So
+    # between the query that found a request done and its fetch there is an
+    # advance whenever other requests were still running.
+    log = Log()
+    events = []
+    gen_cls, batch_cls = make_fakes(log, 8, 1 << 20, 1 << 40)
+
+    class Gen(gen_cls):
+        def fetch(self, fmt="u8", out=None):
+            super().fetch(fmt, out)
+            events.append(("fetch", id(self)))
+
+    class Batch(batch_cls):
+        def advance(self, k):
+            super().advance(k)
+            events.append(("advance", None))
+
+        def query(self):
+            out = super().query()
+            running = sum(1 for s in out if s.status == Q.QSGS_RUNNING)
+            events.append(("query", running))
+            return out
+
+    monkeypatch.setattr(Q, "Generator", Gen)
+    monkeypatch.setattr(Q, "Batch", Batch)
+    srv = S.Server(device="cuda:0", max_members=8, max_words=1 << 20, hbm_budget=1 << 40,
+                   step_quantum=1, keep_results=False)
+    # different step counts (1 + seed % 7), all present from the start
+    reqs = [S.Request(rid=i, params=params(i, 32), arrival=0.0) for i in range(6)]
+    srv.serve(reqs, timeout_s=30.0)
+    assert all(r.finished is not None for r in reqs)
+    checked = 0
+    for i, (kind, _) in enumerate(events):
+        if kind != "fetch":
+            continue
+        q = max(j for j in range(i) if events[j][0] == "query")
+        if events[q][1] > 0:  # others still running after that round
+            assert any(events[j][0] == "advance" for j in range(q + 1, i)), events[q:i + 1]
+            checked += 1
+    assert checked > 0
