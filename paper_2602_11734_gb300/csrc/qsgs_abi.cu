@@ -1006,7 +1006,8 @@ int qsgs_batch_set_members(qsgs_batch* b, qsgs_handle* const* members, uint32_t 
 namespace {
 
 // Seeding of every member, forked from the batch stream onto the seed
-// streams and joined back (the same launches as the direct path below).
+// streams and joined back: launched directly, or captured into the seeding
+// graph.
 cudaError_t enqueue_batch_seeding(qsgs_batch* b) {
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
   for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k)
@@ -1072,20 +1073,10 @@ int qsgs_batch_seed(qsgs_batch* b) {
     }
     return QSGS_OK;
   }
-  cudaError_t e = cudaEventRecord(b->fork, b->stream);
-  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k)
-    e = cudaStreamWaitEvent(b->seed_streams[k], b->fork, 0);
+  // Direct launches (the profiler is on, the legacy stream, or no graph).
+  const cudaError_t e = enqueue_batch_seeding(b);
   if (e != cudaSuccess) return batch_fail(b, e);
-  for (size_t m = 0; m < b->members.size(); ++m) {
-    const int rc = seed_on_stream(b->members[m], b->seed_streams[m % kSeedStreams]);
-    if (rc != QSGS_OK) return rc;
-    b->members[m]->list_stale = true;
-  }
-  for (uint32_t k = 0; k < kSeedStreams && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(b->seed_events[k], b->seed_streams[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->seed_events[k], 0);
-  }
-  if (e != cudaSuccess) return batch_fail(b, e);
+  for (qsgs_handle* h : b->members) h->list_stale = true;
   return QSGS_OK;
 }
 
