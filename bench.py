@@ -265,8 +265,8 @@ def run_reference(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample_edge": REF_SAMPLE_EDGE},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1,
+                         "host_cores": host_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
     return 0
