@@ -209,11 +209,15 @@ def start_cpu_baseline(p: dict):
     by side; ``finish_cpu_baseline`` collects it."""
     code = ("import json, sys, time; sys.path.insert(0, %r)\n"
             "from oracle import oracle as O\n"
-            "p = json.loads(%r)\n"
+            "p = json.loads(%r); q = json.loads(%r)\n"
             "O.lib()\n"
+            "ts = []\n"
+            "for _ in range(3):\n"
+            "    t0 = time.perf_counter(); O.run(q); ts.append(time.perf_counter() - t0)\n"
             "t0 = time.perf_counter(); r = O.run(p); dt = time.perf_counter() - t0\n"
             "print(json.dumps({'seconds': dt, 'solid': int(r.solid_count), "
-            "'steps': int(r.steps)}))\n") % (ROOT, json.dumps(p))
+            "'steps': int(r.steps), 'small_seconds': sorted(ts)[1]}))\n") % (
+                ROOT, json.dumps(p), json.dumps(workloads.small_64()))
     return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
                             stderr=subprocess.PIPE, text=True), time.perf_counter()
 
@@ -234,8 +238,12 @@ def finish_cpu_baseline(handle, p: dict):
         return {"value": None, "unit": METRIC, "cores": 1, "host_cores": host_cores(),
                 "kind": "oracle", "sample": "oracle failed: " + err.strip()[-200:]}
     r = json.loads(out.strip().splitlines()[-1])
+    q = workloads.small_64()
     return {"value": n / r["seconds"], "unit": METRIC, "cores": 1, "host_cores": host_cores(),
             "kind": "oracle",
+            "small_64": {"value": q["nx"] * q["ny"] * q["nz"] / r["small_seconds"],
+                         "unit": METRIC, "seconds": r["small_seconds"],
+                         "what": "the 64^3 workload (cd 0.002, s 0, solid 0.70), median of 3"},
             "sample": (f"one full realization of the timed workload itself ({p['nx']}^3, "
                        f"{r['seconds']:.1f} s, {r['steps']} steps; the single-threaded C "
                        f"oracle on one of the {host_cores()} host cores, run beside the GPU "
